@@ -1,0 +1,229 @@
+/*
+ * mts.h -- C ABI of the GB300 (sm_103a) library for the differentiable forward map
+ * from tuning capacitances C to the normal field Bz of capacitively loaded loop arrays,
+ * and for its adjoint gradient.
+ *
+ * Method (paper: "Differentiable Cosimulator for Electrically Reconfigurable Structures",
+ * Mueller, Philipp, Guenther):
+ *   (a) field basis  H[p][k] = Bz at point p per ampere in loop k, from the Biot-Savart
+ *       law over straight wire segments (Sec. I-A: circuit model plus Biot-Savart for
+ *       structures small against the wavelength); coupling M[k][l] = self and mutual
+ *       inductances (Eq. 12-13, here from Neumann partial inductances).
+ *   (b) port solve   (diag(R) + j w M + diag(1/(j w C))) I = V per configuration and
+ *       frequency (Eq. 2 and Eq. 11 give the loaded-loop impedance; Eq. 6 is the same
+ *       linear network solve in scattering form).
+ *   (c) superposition B = H I (Eq. 7).
+ *   (d) objective    mean over frequencies and loss points of (|Bz| - t)^2 (Eq. 1; the
+ *       paper optimises |Hz| at collocation points, Sec. IV-C), or of |Bz - t|^2.
+ *   (adj) gradient   dloss/dC_k = sum_f Im(mu_k I_k)/(w C_k^2), mu = A^-1 H^T conj(G),
+ *       from d(A^-1) = -A^-1 dA A^-1 (Eq. 8-9); A is complex symmetric so the stored
+ *       factorisation serves the adjoint solve.
+ *
+ * Conventions
+ *   - SI units; time dependence e^{+j w t} (Eq. 2, Eq. 11); mu0 = 4 pi 1e-7 H/m.
+ *   - Complex arrays are interleaved (re, im) pairs of double (complex128) unless stated.
+ *   - Every pointer marked "device" must point to device memory of the current CUDA
+ *     device; "host" pointers to host memory. All buffers are caller-owned. The library
+ *     allocates no device memory and never synchronises the stream, except the
+ *     mts_*_status readers, which say so.
+ *   - Every entry point validates its host-visible arguments before any launch and
+ *     returns MTS_EINVAL (nothing launched) on a violation. Device-side table contents
+ *     are trusted to match their host copies.
+ *   - Work is enqueued on `stream` (a cudaStream_t; NULL means the legacy default
+ *     stream). Results are valid after the stream reaches that point.
+ *   - Thread safety: calls on different streams with disjoint output buffers may run
+ *     concurrently; calls that write the same tape or basis buffer must be ordered.
+ */
+#ifndef MTS_H
+#define MTS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* mts_stream; /* cudaStream_t */
+
+typedef enum {
+  MTS_OK = 0,
+  MTS_EINVAL = 1,       /* invalid argument; nothing was launched */
+  MTS_EWORKSPACE = 2,   /* basis or tape buffer smaller than the *_bytes query */
+  MTS_ECUDA = 3,        /* a CUDA launch or runtime call failed */
+  MTS_ENOCONV = 4,      /* (status readers) a system missed the refinement tolerance */
+  MTS_EUNSUPPORTED = 5  /* geometry or size the kernels do not handle */
+} mts_status;
+
+typedef enum {
+  /* FP64 everywhere: basis, FP64 LU with partial pivoting, FP64 superposition;
+     B_out is complex128. Target error against the FP64 oracle <= 1e-10. */
+  MTS_FP64 = 0,
+  /* FP32 basis with FP64 near-field terms; FP32 complex LU with partial pivoting and
+     iterative refinement on residuals taken in FP64-equivalent precision; superposition
+     on the tensor cores with three-way bf16 operand splitting and FP32 accumulation;
+     B_out is complex64. Target error <= 1e-6. */
+  MTS_MIXED = 1,
+  /* As MTS_MIXED but the superposition uses single bf16 operands (one tensor-core pass);
+     B_out is complex64. Target error <= 1e-2 on B. */
+  MTS_BF16 = 2
+} mts_precision;
+
+typedef enum {
+  MTS_LOSS_ABS = 0,     /* (|Bz| - t)^2, t real: the paper's magnitude objective */
+  MTS_LOSS_COMPLEX = 1  /* |Bz - t|^2, t complex (re, im) */
+} mts_loss_mode;
+
+/*
+ * A batch of independent structures (n_struct >= 1). Structure s owns
+ *   ports      port_off[s]  .. port_off[s+1]-1    (port k = loop k, closed by one capacitor)
+ *   points     point_off[s] .. point_off[s+1]-1   (field points, metres)
+ *   freqs      freq_off[s]  .. freq_off[s+1]-1    (angular frequencies in mts_eval.omega)
+ *   loss pts   loss_off[s]  .. loss_off[s+1]-1    (entries of loss_idx; global point
+ *                                                   indices inside structure s)
+ * Loop k is the closed polyline of vertices loop_vtx_off[k] .. loop_vtx_off[k+1]-1, the
+ * last joined back to the first; its orientation fixes the sign of its current. Each
+ * structure is coupled only within itself. Off-diagonal inductances, and diagonal ones
+ * when L_self is NULL, need every segment pair to be parallel or perpendicular
+ * (rectilinear loops); other pairs give MTS_EUNSUPPORTED from mts_basis_status.
+ * Offset tables are given twice, identical: host copies (h_*) plan launches, device
+ * copies are read by the kernels. Limits: 1 <= ports per structure <= 128.
+ */
+typedef struct mts_problem {
+  int32_t n_struct;
+  int32_t n_ports;     /* total over structures */
+  int32_t n_vertices;  /* total */
+  int32_t n_freq;      /* total frequencies, sum over structures */
+  int64_t n_points;    /* total */
+  int32_t n_loss;      /* total loss points (0: no objective possible) */
+  double wire_radius;  /* metres, > 0 */
+  const int32_t* h_port_off;   /* host   [n_struct+1] */
+  const int64_t* h_point_off;  /* host   [n_struct+1] */
+  const int32_t* h_freq_off;   /* host   [n_struct+1] */
+  const int32_t* h_loss_off;   /* host   [n_struct+1] */
+  const int32_t* port_off;     /* device [n_struct+1] */
+  const int64_t* point_off;    /* device [n_struct+1] */
+  const int32_t* freq_off;     /* device [n_struct+1] */
+  const int32_t* loss_off;     /* device [n_struct+1] */
+  const int32_t* loop_vtx_off; /* device [n_ports+1] */
+  const double* vx;            /* device [n_vertices] */
+  const double* vy;
+  const double* vz;
+  const double* px;            /* device [n_points] */
+  const double* py;
+  const double* pz;
+  const int64_t* loss_idx;     /* device [n_loss] */
+  const double* R;             /* device [n_ports], ohm, > 0 */
+  const double* L_self;        /* device [n_ports] henry, or NULL (partial inductances) */
+} mts_problem;
+
+/*
+ * Per-call inputs. Layouts, with FN = sum_s F_s N_s and FL = sum_s F_s L_s:
+ *   C       device [n_cfg][n_ports]             farad, finite, nonzero (Eq. 1 leaves C
+ *                                                unbounded, so negative C is accepted)
+ *   omega   device [n_freq]                      rad/s, > 0
+ *   V       device complex [FN]: structure s at sum_{s'<s} F_s' N_s', as [F_s][N_s] volt
+ *   target  device, NULL = no objective; real [FL] (MTS_LOSS_ABS) or complex [FL]
+ *           (MTS_LOSS_COMPLEX), structure s at sum_{s'<s} F_s' L_s' as [F_s][L_s];
+ *           with target_per_cfg != 0 one such block per configuration ([n_cfg][...]).
+ * refine_tol: stop refining a system when max|dx| <= refine_tol * max|x| (MTS_MIXED,
+ *   MTS_BF16; 0 selects 1e-12). max_refine: refinement steps per solve (0 selects 8).
+ */
+typedef struct mts_eval {
+  int64_t n_cfg;
+  const double* C;
+  const double* omega;
+  const double* V;
+  const double* target;
+  int32_t target_per_cfg;
+  int32_t loss_mode; /* mts_loss_mode */
+  double refine_tol;
+  int32_t max_refine;
+} mts_eval;
+
+/* Human-readable name of a status code (static string). */
+const char* mts_status_string(mts_status s);
+
+/* Library version string (static). */
+const char* mts_version(void);
+
+/* Number of kernels this library has launched in this process (all threads). */
+uint64_t mts_launch_count(void);
+
+/* ---------------------------------------------------------------------------------
+ * (a) basis: H, M and derived tables, in a library-defined layout inside a caller
+ * buffer of mts_basis_bytes(...) bytes (device, 256-byte aligned). Built once per
+ * geometry and precision; read-only afterwards. Returns MTS_EWORKSPACE if
+ * basis_bytes is too small.
+ * --------------------------------------------------------------------------------- */
+size_t mts_basis_bytes(const mts_problem* pb, mts_precision prec);
+mts_status mts_build_basis(const mts_problem* pb, mts_precision prec, void* basis,
+                           size_t basis_bytes, mts_stream stream);
+
+/* Copy of the field basis as FP64 [P_s][N_s] blocks (structure s at sum P N), and of
+ * the inductance matrix as FP64 [N_s][N_s] blocks (at sum N^2); either output may be
+ * NULL. Device outputs. For testing and for callers that want the basis itself. */
+mts_status mts_basis_export(const mts_problem* pb, mts_precision prec, const void* basis,
+                            double* H_out, double* M_out, mts_stream stream);
+
+/* Synchronises `stream`, then reports MTS_EUNSUPPORTED if a segment pair needed for M
+ * was neither parallel nor perpendicular (or two collinear segments overlapped). */
+mts_status mts_basis_status(const mts_problem* pb, mts_precision prec, const void* basis,
+                            mts_stream stream);
+
+/* ---------------------------------------------------------------------------------
+ * Tape: the per-call state written by the forward calls and read by mts_backward
+ * (currents I, tensor-core operand copies of I, per-system objective and gradient
+ * partials, per-system status, backward scratch). Device buffer of
+ * mts_tape_bytes(...) bytes, 256-byte aligned.
+ * --------------------------------------------------------------------------------- */
+size_t mts_tape_bytes(const mts_problem* pb, int64_t n_cfg, mts_precision prec);
+
+/* ---------------------------------------------------------------------------------
+ * (b)+(d)+(adj) mts_solve: for every configuration b and frequency f of every
+ * structure, assemble A = diag(R) + j w M + diag(1/(j w C_b)) (Eq. 2, 11), solve A I = V
+ * (Eq. 6 in impedance form) with partial pivoting, and store I in the tape (and in
+ * I_out, device complex [n_cfg][FN], if not NULL). If ev->target is not NULL it also
+ * evaluates the objective at the loss points (Eq. 1) and the adjoint gradient
+ * dloss/dC (Eq. 8-9) while the factors are resident; the loss is written to loss_out
+ * (device [n_cfg][n_struct], may be NULL) and the gradient kept in the tape.
+ * --------------------------------------------------------------------------------- */
+mts_status mts_solve(const mts_problem* pb, mts_precision prec, const void* basis,
+                     const mts_eval* ev, double* I_out, double* loss_out, void* tape,
+                     size_t tape_bytes, mts_stream stream);
+
+/* (c) mts_superpose: B = H I for the currents in the tape (Eq. 7). B_out is device
+ * [n_cfg][sum_s F_s P_s] complex, structure s at sum_{s'<s} F_s' P_s' as [F_s][P_s]:
+ * complex128 for MTS_FP64, complex64 (interleaved float re, im) otherwise. */
+mts_status mts_superpose(const mts_problem* pb, mts_precision prec, const void* basis,
+                         const mts_eval* ev, const void* tape, void* B_out,
+                         mts_stream stream);
+
+/* mts_forward = mts_solve followed by mts_superpose (B_out may be NULL: loss only). */
+mts_status mts_forward(const mts_problem* pb, mts_precision prec, const void* basis,
+                       const mts_eval* ev, void* B_out, double* I_out, double* loss_out,
+                       void* tape, size_t tape_bytes, mts_stream stream);
+
+/* (adj) mts_backward: grad_C (device [n_cfg][n_ports], overwritten) =
+ *     grad_loss[b][s] * dloss_{b,s}/dC            (grad_loss device [n_cfg][n_struct];
+ *                                                   needs a forward with a target)
+ *   + dL/dC from a field cotangent grad_B         (device, same layout and element type
+ *                                                   as B_out; torch convention
+ *                                                   dL/dRe B + j dL/dIm B)
+ * Either input may be NULL (both NULL gives zeros). `ev` must be the forward's. The
+ * field-cotangent term re-solves A mu = H^T conj(grad_B) per system. */
+mts_status mts_backward(const mts_problem* pb, mts_precision prec, const void* basis,
+                        const mts_eval* ev, void* tape, size_t tape_bytes,
+                        const void* grad_B, const double* grad_loss, double* grad_C,
+                        mts_stream stream);
+
+/* Synchronises `stream` and summarises the per-system status of the last forward on
+ * this tape: MTS_OK, or MTS_ENOCONV if any system missed the refinement tolerance or
+ * met a non-finite value. If n_bad is not NULL it receives the number of such systems. */
+mts_status mts_tape_status(const mts_problem* pb, int64_t n_cfg, mts_precision prec,
+                           const void* tape, int64_t* n_bad, mts_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MTS_H */

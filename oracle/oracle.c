@@ -105,6 +105,7 @@ double oracle_segment_bz(double x1, double y1, double z1, double x2, double y2, 
 void oracle_basis(int32_t n_loops, const int32_t* loop_vtx_off, const double* vx,
                   const double* vy, const double* vz, int64_t n_points, const double* px,
                   const double* py, const double* pz, double rw, double* H) {
+#pragma omp parallel for schedule(static)
   for (int64_t p = 0; p < n_points; ++p) {
     for (int32_t k = 0; k < n_loops; ++k) {
       int32_t a = loop_vtx_off[k], b = loop_vtx_off[k + 1];

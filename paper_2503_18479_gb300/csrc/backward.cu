@@ -1,0 +1,140 @@
+// backward.cu -- pieces of the adjoint path (paper Eq. 8-10 through d(A^-1) = -A^-1 dA A^-1)
+// for a field cotangent grad_B = dL/dRe B + j dL/dIm B:
+//   field_adjoint_kernel  u[b][f][k] = sum_p H[p][k] conj(grad_B[b][f][p])   (u = H^T conj(gB))
+//   grad_combine_kernel   grad_C = grad_loss * dloss/dC + (field term)
+//   count_bad_kernel      number of systems with a nonzero status word
+// The solve kernels (solve.cu) then compute mu = A^-1 u and Im(mu_k I_k)/(w C_k^2).
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace mts {
+
+constexpr int kFaSys = 8;     // systems per CTA (share the H reads)
+constexpr int kFaChunk = 128; // points per staged chunk
+
+// CTA = 128 threads (one per port k, N <= 128), kFaSys configurations of one frequency g.
+// Inner sums over a chunk of points in the working precision, outer sums in FP64.
+template <typename HT, typename GT>
+__global__ void __launch_bounds__(128) field_adjoint_kernel(FieldAdjArgs a) {
+  __shared__ GT sg[kFaSys][kFaChunk];
+  const int g = blockIdx.x;
+  const int64_t b0 = (int64_t)blockIdx.y * kFaSys;
+  const int s = a.t.freq_struct[g];
+  const int f = g - a.freq_off[s];
+  const int N = a.port_off[s + 1] - a.port_off[s];
+  const int64_t P = a.point_off[s + 1] - a.point_off[s];
+  const int k = threadIdx.x;
+  const HT* H = static_cast<const HT*>(a.H) + a.t.pn_off[s];
+  const GT* gB = static_cast<const GT*>(a.grad_B);
+  double accx[kFaSys], accy[kFaSys];
+#pragma unroll
+  for (int i = 0; i < kFaSys; ++i) accx[i] = accy[i] = 0.0;
+  for (int64_t p0 = 0; p0 < P; p0 += kFaChunk) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < kFaSys * kFaChunk; e += blockDim.x) {
+      int i = e / kFaChunk, q = e % kFaChunk;
+      int64_t b = b0 + i;
+      GT v;
+      v.x = 0;
+      v.y = 0;
+      if (b < a.n_cfg && p0 + q < P) v = gB[b * a.sumFP + a.t.fp_off[s] + (int64_t)f * P + p0 + q];
+      sg[i][q] = v;
+    }
+    __syncthreads();
+    if (k < N) {
+      HT cx[kFaSys], cy[kFaSys];
+#pragma unroll
+      for (int i = 0; i < kFaSys; ++i) cx[i] = cy[i] = 0;
+      int qn = (int)min((int64_t)kFaChunk, P - p0);
+      for (int q = 0; q < qn; ++q) {
+        HT h = H[(p0 + q) * N + k];
+#pragma unroll
+        for (int i = 0; i < kFaSys; ++i) {
+          cx[i] += h * sg[i][q].x;
+          cy[i] -= h * sg[i][q].y;  // conj
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < kFaSys; ++i) {
+        accx[i] += (double)cx[i];
+        accy[i] += (double)cy[i];
+      }
+    }
+  }
+  if (k < N) {
+#pragma unroll
+    for (int i = 0; i < kFaSys; ++i) {
+      int64_t b = b0 + i;
+      if (b < a.n_cfg) {
+        double* up = a.u + 2 * (b * a.sumFN + a.t.fn_off[s] + (int64_t)f * N + k);
+        up[0] = accx[i];
+        up[1] = accy[i];
+      }
+    }
+  }
+}
+
+cudaError_t launch_field_adjoint_rhs(const FieldAdjArgs& a, mts_precision prec, int max_ports,
+                                     cudaStream_t st) {
+  if (max_ports > 128) return cudaErrorNotSupported;
+  dim3 grid((unsigned)a.n_freq, (unsigned)((a.n_cfg + kFaSys - 1) / kFaSys));
+  if (prec == MTS_FP64)
+    field_adjoint_kernel<double, double2><<<grid, 128, 0, st>>>(a);
+  else
+    field_adjoint_kernel<float, float2><<<grid, 128, 0, st>>>(a);
+  note_launch();
+  return cudaGetLastError();
+}
+
+__global__ void grad_combine_kernel(int64_t n_cfg, int n_struct, int n_ports,
+                                    const int32_t* __restrict__ port_off,
+                                    const double* __restrict__ grad_loss,
+                                    const double* __restrict__ dldc,
+                                    const double* __restrict__ gfield, double* __restrict__ grad_C) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_cfg * n_ports) return;
+  int64_t b = i / n_ports;
+  int port = (int)(i - b * n_ports);
+  double v = 0.0;
+  if (grad_loss) {
+    int s = find_struct_i32(port_off, n_struct, port);
+    v = grad_loss[b * n_struct + s] * dldc[i];
+  }
+  if (gfield) v += gfield[i];
+  grad_C[i] = v;
+}
+
+cudaError_t launch_grad_combine(int64_t n_cfg, int n_struct, int n_ports,
+                                const int32_t* port_off, const double* grad_loss,
+                                const double* dldc, const double* gfield, double* grad_C,
+                                cudaStream_t st) {
+  int64_t n = n_cfg * n_ports;
+  if (n == 0) return cudaSuccess;
+  grad_combine_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n_cfg, n_struct, n_ports,
+                                                                   port_off, grad_loss, dldc,
+                                                                   gfield, grad_C);
+  note_launch();
+  return cudaGetLastError();
+}
+
+__global__ void count_bad_kernel(const int32_t* __restrict__ status, int64_t n, int32_t* out) {
+  int c = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    c += status[i] != 0;
+  for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+cudaError_t launch_count_bad(const int32_t* status, int64_t n, int32_t* out, cudaStream_t st) {
+  cudaMemsetAsync(out, 0, sizeof(int32_t), st);
+  if (n > 0) {
+    count_bad_kernel<<<64, 256, 0, st>>>(status, n, out);
+    note_launch();
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace mts

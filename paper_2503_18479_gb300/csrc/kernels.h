@@ -1,0 +1,117 @@
+// kernels.h -- internal launcher interface between the C ABI layer and the kernels.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace mts {
+
+// Everything the per-system solve kernels read and write.
+struct SolveArgs {
+  int n_struct, n_freq, n_ports;
+  const int32_t* port_off;
+  const int32_t* freq_off;
+  const int32_t* loss_off;
+  const double* R;
+  DevTables t;
+  const double* M64;
+  const float* M32hi;
+  const float* M32lo;
+  const double* Hl64;
+  const float* Hl32;
+  int64_t n_cfg;
+  const double* C;
+  const double* omega;
+  const double* V;
+  const double* target;
+  int target_per_cfg;
+  int loss_mode;
+  double tol;
+  int max_refine;
+  int64_t sumFN, sumFL;
+  double* I;          // tape
+  double* I_out;      // optional copy
+  double* loss_part;  // [n_cfg][n_freq]
+  double* grad_part;  // [n_cfg][sumFN]
+  int32_t* status;    // [n_cfg][n_freq]
+  __nv_bfloat16* Bop;      // tensor-core operand of I (nullptr for FP64)
+  const int64_t* bop_off;  // per-structure element base of Bop (plan table)
+  int npieces;
+  int max_loss;  // max loss points of one structure (uniform trip count for group loops)
+  // backward (field cotangent) mode: solve A mu = rhs_in and write grad terms only
+  const double* rhs_in;  // [n_cfg][sumFN] complex, or nullptr for the forward
+};
+
+struct ReduceArgs {
+  int n_struct, n_freq, n_ports;
+  const int32_t* port_off;
+  const int32_t* freq_off;
+  const int32_t* loss_off;
+  DevTables t;
+  int64_t n_cfg, sumFN;
+  const double* loss_part;
+  const double* grad_part;
+  double* dldc;      // [n_cfg][n_ports]
+  double* lossv;     // [n_cfg][n_struct]
+  double* loss_out;  // optional
+  int normalise;     // 1: divide by F_s L_s (objective), 0: plain sum over frequencies
+};
+
+cudaError_t launch_build_basis(const mts_problem* pb, mts_precision prec, void* basis,
+                               const BasisLayout& bl, const ProblemSums& ps, cudaStream_t st);
+cudaError_t launch_export_basis(const mts_problem* pb, mts_precision prec, const void* basis,
+                                const BasisLayout& bl, const ProblemSums& ps, double* H_out,
+                                double* M_out, cudaStream_t st);
+
+// Per-call plan tables in the tape (bases of the B operand, GEMM unit prefixes).
+cudaError_t launch_plan(const mts_problem* pb, int64_t n_cfg, int npieces, int64_t* bop_off,
+                        int64_t* unit_off, cudaStream_t st);
+
+cudaError_t launch_solve(const SolveArgs& a, mts_precision prec, int max_ports, cudaStream_t st);
+cudaError_t launch_reduce(const ReduceArgs& a, cudaStream_t st);
+
+struct SuperposeArgs {
+  int n_struct, n_freq, n_ports;
+  const int32_t* port_off;
+  const int32_t* freq_off;
+  const int64_t* point_off;
+  DevTables t;
+  int64_t n_cfg, sumFN, sumFP;
+  int64_t total_units;      // GEMM work units (host-computed)
+  const int64_t* unit_off;  // per-structure prefix of GEMM units (plan table)
+  const void* H;            // FP64 (MTS_FP64) basis
+  const double* I;          // tape currents
+  const __nv_bfloat16* Aop;
+  const __nv_bfloat16* Bop;
+  const int64_t* bop_off;
+  int npieces;
+  void* B_out;
+  int32_t* err;  // device error word (bounded-wait timeouts)
+};
+
+cudaError_t launch_superpose(const SuperposeArgs& a, mts_precision prec, cudaStream_t st);
+
+struct FieldAdjArgs {
+  int n_struct, n_freq, n_ports;
+  const int32_t* port_off;
+  const int32_t* freq_off;
+  const int64_t* point_off;
+  DevTables t;
+  int64_t n_cfg, sumFN, sumFP;
+  const void* H;       // FP64 or FP32 basis
+  const void* grad_B;  // complex128 (FP64) or complex64
+  double* u;           // out: [n_cfg][sumFN] complex, u = H^T conj(grad_B)
+};
+
+cudaError_t launch_field_adjoint_rhs(const FieldAdjArgs& a, mts_precision prec, int max_ports,
+                                     cudaStream_t st);
+
+cudaError_t launch_grad_combine(int64_t n_cfg, int n_struct, int n_ports,
+                                const int32_t* port_off, const double* grad_loss,
+                                const double* dldc, const double* gfield, double* grad_C,
+                                cudaStream_t st);
+
+cudaError_t launch_count_bad(const int32_t* status, int64_t n, int32_t* out, cudaStream_t st);
+
+}  // namespace mts

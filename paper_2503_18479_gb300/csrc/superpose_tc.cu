@@ -1,0 +1,409 @@
+// superpose_tc.cu -- (c) B = H I (paper Eq. 7) on the 5th-generation tensor cores.
+//
+// Real GEMM per structure: rows = field points p (A operand: H, bf16 pieces), columns =
+// (configuration, frequency, re/im) (B operand: I, bf16 pieces), K = ports. With
+// x = x0 + x1 + x2 (bf16 pieces, exact for FP32 data) the product keeps the six piece
+// pairs of order >= 2^-16 (x0y0, x0y1, x1y0, x0y2, x1y1, x2y0) accumulated in FP32 in
+// tensor memory: relative error ~2^-24 per product (MTS_MIXED). MTS_BF16 uses x0 y0 only.
+//
+// Persistent kernel, one CTA per SM, 192 threads:
+//   warp 0      producer: cp.async.bulk copies of the pre-swizzled 16 KB operand tiles
+//               (global images already in the 128-byte-swizzled K-major layout) into a
+//               ring of shared-memory stages, completion via mbarrier transaction counts
+//   warp 1      allocates 256 TMEM columns (two 128x128 FP32 accumulators); lane 0
+//               issues tcgen05.mma (M=128, N=128, K=16, kind::f16 with bf16 inputs) and
+//               tcgen05.commit to release stages and hand accumulators to the epilogue
+//   warps 2..5  epilogue: tcgen05.ld of the accumulator (warp w reads lanes 32*(w%4)..),
+//               release of the accumulator, then streaming complex64 stores: lane = point,
+//               so each warp store writes 32 consecutive points (256 contiguous bytes)
+// Every mbarrier wait is bounded; on timeout the kernel records an error word, stops
+// issuing work, waits (bounded) for its own copies, frees TMEM and returns.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace mts {
+
+namespace tc {
+
+constexpr int kThreads = 192;
+constexpr uint32_t kTileBytes = kTileP * kChunkK * 2;  // 16 KB (also kTileN x 64 x 2)
+constexpr uint32_t kTmemCols = 256;
+constexpr uint64_t kWaitNs = 2000000000ull;  // bound of every mbarrier wait: 2 s
+
+__device__ inline uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ inline void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ inline void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ inline void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ inline bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ inline uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait (kWaitNs of wall time); returns false and records `code` in *err on timeout.
+__device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity, int32_t* err, int code) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > kWaitNs) {
+      atomicCAS(err, 0, code);
+      return false;
+    }
+  }
+}
+
+__device__ inline void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ inline void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ inline void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ inline uint64_t make_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);  // start address
+  d |= (uint64_t)1u << 16;                  // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024u >> 4) << 32;        // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1u << 46;                  // descriptor version (sm_100 family)
+  d |= (uint64_t)2u << 61;                  // layout: 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: kind::f16, A = B = bf16, D = f32, both K-major, M = 128, N = 128.
+constexpr uint32_t kIdesc = (1u << 4)            // D format f32
+                            | (1u << 7)          // A bf16
+                            | (1u << 10)         // B bf16
+                            | ((128u >> 3) << 17)  // N
+                            | ((128u >> 4) << 24); // M
+
+__device__ inline void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accum)
+      : "memory");
+}
+
+__device__ inline void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ inline void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t* r = reinterpret_cast<uint32_t*>(v);
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+}
+
+__device__ inline void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ inline void st_cs_f2(float2* p, float x, float y) {
+  asm volatile("st.global.cs.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(x), "f"(y) : "memory");
+}
+
+struct Unit {
+  int s, N, F, nkc;
+  int64_t P, pt, nt, nptile, nntile;
+};
+
+__device__ inline Unit unit_info(const SuperposeArgs& a, int64_t u) {
+  Unit x;
+  x.s = find_struct_i64(a.unit_off, a.n_struct, u);
+  x.N = a.port_off[x.s + 1] - a.port_off[x.s];
+  x.F = a.freq_off[x.s + 1] - a.freq_off[x.s];
+  x.P = a.point_off[x.s + 1] - a.point_off[x.s];
+  x.nkc = (x.N + kChunkK - 1) / kChunkK;
+  x.nptile = (x.P + kTileP - 1) / kTileP;
+  x.nntile = (2 * a.n_cfg * x.F + kTileN - 1) / kTileN;
+  int64_t lu = u - a.unit_off[x.s];
+  x.pt = lu % x.nptile;
+  x.nt = lu / x.nptile;
+  return x;
+}
+
+template <int NPIECE>
+__global__ void __launch_bounds__(kThreads, 1) superpose_tc_kernel(SuperposeArgs a, int32_t* err) {
+  constexpr int NSTAGE = NPIECE == 3 ? 2 : 4;
+  constexpr uint32_t kStageBytes = 2u * NPIECE * kTileBytes;
+  constexpr int NPAIR = NPIECE == 3 ? 6 : 1;
+  // piece pairs (A piece, B piece), smallest products first
+  constexpr int pa[6] = {2, 1, 0, 1, 0, 0};
+  constexpr int pb[6] = {0, 1, 2, 0, 1, 0};
+
+  extern __shared__ __align__(1024) unsigned char smem_dyn[];
+  // 1024-byte aligned operand area
+  uintptr_t sbase = (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023);
+  unsigned char* stages = reinterpret_cast<unsigned char*>(sbase);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stages + NSTAGE * kStageBytes);
+  uint64_t* full = bars;                 // [NSTAGE]
+  uint64_t* empty = bars + NSTAGE;       // [NSTAGE]
+  uint64_t* tfull = bars + 2 * NSTAGE;   // [2]
+  uint64_t* tempty = tfull + 2;          // [2]
+  uint64_t* mdone = tempty + 2;          // [1] all issued MMAs complete
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mdone + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t G = gridDim.x;
+  const int64_t u_begin = a.total_units * blockIdx.x / G;
+  const int64_t u_end = a.total_units * (blockIdx.x + 1) / G;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NSTAGE; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&tfull[i], 1);
+      mbar_init(&tempty[i], 128);
+    }
+    mbar_init(mdone, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------- producer ----------------
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      uint32_t last_phase[NSTAGE];
+      bool used[NSTAGE];
+      for (int i = 0; i < NSTAGE; ++i) {
+        used[i] = false;
+        last_phase[i] = 0;
+      }
+      for (int64_t u = u_begin; u < u_end && ok; ++u) {
+        Unit x = unit_info(a, u);
+        const unsigned char* Ab = reinterpret_cast<const unsigned char*>(a.Aop + a.t.aop_off[x.s]);
+        const unsigned char* Bb = reinterpret_cast<const unsigned char*>(a.Bop + a.bop_off[x.s]);
+        for (int kc = 0; kc < x.nkc && ok; ++kc) {
+          if (!mbar_wait(&empty[stage], phase ^ 1u, err, 1)) {
+            ok = false;
+            break;
+          }
+          unsigned char* sA = stages + stage * kStageBytes;
+          unsigned char* sB = sA + NPIECE * kTileBytes;
+          mbar_arrive_expect_tx(&full[stage], kStageBytes);
+          for (int q = 0; q < NPIECE; ++q) {
+            const unsigned char* ga =
+                Ab + ((size_t)(q * x.nptile + x.pt) * x.nkc + kc) * kTileBytes;
+            const unsigned char* gb =
+                Bb + ((size_t)(q * x.nntile + x.nt) * x.nkc + kc) * kTileBytes;
+            bulk_g2s(sA + q * kTileBytes, ga, kTileBytes, &full[stage]);
+            bulk_g2s(sB + q * kTileBytes, gb, kTileBytes, &full[stage]);
+          }
+          used[stage] = true;
+          last_phase[stage] = phase;
+          if (++stage == NSTAGE) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      // no copy may still be in flight when the CTA exits
+      for (int i = 0; i < NSTAGE; ++i)
+        if (used[i]) mbar_wait(&full[i], last_phase[i], err, 5);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int acc = 0;
+      uint32_t aphase = 0;
+      bool ok = true;
+      for (int64_t u = u_begin; u < u_end && ok; ++u) {
+        Unit x = unit_info(a, u);
+        if (!mbar_wait(&tempty[acc], aphase ^ 1u, err, 2)) break;
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + (uint32_t)acc * 128u;
+        for (int kc = 0; kc < x.nkc; ++kc) {
+          if (!mbar_wait(&full[stage], phase, err, 3)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sA = smem_u32(stages + stage * kStageBytes);
+          const uint32_t sB = sA + NPIECE * kTileBytes;
+#pragma unroll
+          for (int pp = 0; pp < NPAIR; ++pp) {
+            const int qa = NPIECE == 3 ? pa[pp] : 0, qb = NPIECE == 3 ? pb[pp] : 0;
+            const uint64_t da = make_desc(sA + qa * kTileBytes);
+            const uint64_t db = make_desc(sB + qb * kTileBytes);
+#pragma unroll
+            for (int kk = 0; kk < kChunkK / 16; ++kk) {
+              // advance 16 elements (32 bytes) along K inside the swizzle atom
+              mma_bf16(d_tmem, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2),
+                       (kc > 0 || pp > 0 || kk > 0) ? 1u : 0u);
+            }
+          }
+          mma_commit(&empty[stage]);
+          if (++stage == NSTAGE) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+        mma_commit(&tfull[acc]);
+        if (++acc == 2) {
+          acc = 0;
+          aphase ^= 1u;
+        }
+      }
+      // every MMA issued by this thread has finished before TMEM is released
+      mma_commit(mdone);
+      mbar_wait(mdone, 0, err, 6);
+    }
+  } else {
+    // ---------------- epilogue (warps 2..5) ----------------
+    const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
+    int acc = 0;
+    uint32_t aphase = 0;
+    float2* Bout = static_cast<float2*>(a.B_out);
+    for (int64_t u = u_begin; u < u_end; ++u) {
+      Unit x = unit_info(a, u);
+      if (!mbar_wait(&tfull[acc], aphase, err, 4)) break;
+      tc_fence_after();
+      float v[128];
+      const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)acc * 128u;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) tmem_ld32(taddr + c * 32, v + c * 32);
+      tmem_wait_ld();
+      tc_fence_before();
+      mbar_arrive(&tempty[acc]);
+      if (++acc == 2) {
+        acc = 0;
+        aphase ^= 1u;
+      }
+      const int64_t p = x.pt * kTileP + quarter * 32 + lane;
+      if (p < x.P) {
+        const int64_t nsys = a.n_cfg * x.F;
+        int64_t sys0 = x.nt * (kTileN / 2);
+        int64_t b = sys0 / x.F;
+        int f = (int)(sys0 - b * x.F);
+        const int64_t fpo = a.t.fp_off[x.s];
+#pragma unroll
+        for (int i = 0; i < kTileN / 2; ++i) {
+          if (sys0 + i < nsys) {
+            float2* dst = Bout + (b * a.sumFP + fpo + (int64_t)f * x.P + p);
+            st_cs_f2(dst, v[2 * i], v[2 * i + 1]);
+          }
+          if (++f == x.F) {
+            f = 0;
+            ++b;
+          }
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(kTmemCols)
+                 : "memory");
+  }
+}
+
+template <int NPIECE>
+size_t smem_bytes() {
+  constexpr int NSTAGE = NPIECE == 3 ? 2 : 4;
+  return 1024 + (size_t)NSTAGE * 2 * NPIECE * kTileBytes + 8 * (2 * NSTAGE + 5) + 16;
+}
+
+}  // namespace tc
+
+static int g_num_sms = 0;
+
+cudaError_t launch_superpose_tc(const SuperposeArgs& a, mts_precision prec, cudaStream_t st) {
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 1;
+  }
+  int64_t grid = a.total_units < g_num_sms ? a.total_units : g_num_sms;
+  int32_t* err = a.err;
+  if (err == nullptr) return cudaErrorInvalidValue;
+  if (prec == MTS_MIXED) {
+    size_t sm = tc::smem_bytes<3>();
+    cudaError_t e = cudaFuncSetAttribute(tc::superpose_tc_kernel<3>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    tc::superpose_tc_kernel<3><<<(unsigned)grid, tc::kThreads, sm, st>>>(a, err);
+  } else {
+    size_t sm = tc::smem_bytes<1>();
+    cudaError_t e = cudaFuncSetAttribute(tc::superpose_tc_kernel<1>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    tc::superpose_tc_kernel<1><<<(unsigned)grid, tc::kThreads, sm, st>>>(a, err);
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace mts

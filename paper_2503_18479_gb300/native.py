@@ -1,0 +1,277 @@
+"""ctypes binding of libmts.so (include/mts.h): same names, argument marshalling only.
+
+Device buffers are torch tensors (PyTorch supplies device memory and streams); every step
+of the method runs in the library's CUDA kernels. If the library is missing this module
+raises ImportError on use: there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libmts.so")
+
+MTS_OK, MTS_EINVAL, MTS_EWORKSPACE, MTS_ECUDA, MTS_ENOCONV, MTS_EUNSUPPORTED = range(6)
+MTS_FP64, MTS_MIXED, MTS_BF16 = 0, 1, 2
+MTS_LOSS_ABS, MTS_LOSS_COMPLEX = 0, 1
+PRECISIONS = {"fp64": MTS_FP64, "mixed": MTS_MIXED, "bf16": MTS_BF16}
+
+# symbols declared in include/mts.h
+EXPORTED = ["mts_status_string", "mts_version", "mts_launch_count", "mts_basis_bytes",
+            "mts_build_basis", "mts_basis_export", "mts_basis_status", "mts_tape_bytes",
+            "mts_solve", "mts_superpose", "mts_forward", "mts_backward", "mts_tape_status"]
+
+
+class MtsProblem(ct.Structure):
+    _fields_ = [
+        ("n_struct", ct.c_int32), ("n_ports", ct.c_int32), ("n_vertices", ct.c_int32),
+        ("n_freq", ct.c_int32), ("n_points", ct.c_int64), ("n_loss", ct.c_int32),
+        ("wire_radius", ct.c_double),
+        ("h_port_off", ct.c_void_p), ("h_point_off", ct.c_void_p), ("h_freq_off", ct.c_void_p),
+        ("h_loss_off", ct.c_void_p),
+        ("port_off", ct.c_void_p), ("point_off", ct.c_void_p), ("freq_off", ct.c_void_p),
+        ("loss_off", ct.c_void_p),
+        ("loop_vtx_off", ct.c_void_p), ("vx", ct.c_void_p), ("vy", ct.c_void_p),
+        ("vz", ct.c_void_p), ("px", ct.c_void_p), ("py", ct.c_void_p), ("pz", ct.c_void_p),
+        ("loss_idx", ct.c_void_p), ("R", ct.c_void_p), ("L_self", ct.c_void_p),
+    ]
+
+
+class MtsEval(ct.Structure):
+    _fields_ = [
+        ("n_cfg", ct.c_int64), ("C", ct.c_void_p), ("omega", ct.c_void_p), ("V", ct.c_void_p),
+        ("target", ct.c_void_p), ("target_per_cfg", ct.c_int32), ("loss_mode", ct.c_int32),
+        ("refine_tol", ct.c_double), ("max_refine", ct.c_int32),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load libmts.so (raises ImportError if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"{LIB_PATH} is missing: build it with "
+                                  "`python -m paper_2503_18479_gb300.build_lib` (needs nvcc)")
+            L = ct.CDLL(LIB_PATH)
+            p, i32, i64, sz = ct.c_void_p, ct.c_int32, ct.c_int64, ct.c_size_t
+            PP, PE = ct.POINTER(MtsProblem), ct.POINTER(MtsEval)
+            L.mts_status_string.restype = ct.c_char_p
+            L.mts_status_string.argtypes = [ct.c_int]
+            L.mts_version.restype = ct.c_char_p
+            L.mts_version.argtypes = []
+            L.mts_launch_count.restype = ct.c_uint64
+            L.mts_launch_count.argtypes = []
+            L.mts_basis_bytes.restype = sz
+            L.mts_basis_bytes.argtypes = [PP, ct.c_int]
+            L.mts_build_basis.restype = ct.c_int
+            L.mts_build_basis.argtypes = [PP, ct.c_int, p, sz, p]
+            L.mts_basis_export.restype = ct.c_int
+            L.mts_basis_export.argtypes = [PP, ct.c_int, p, p, p, p]
+            L.mts_basis_status.restype = ct.c_int
+            L.mts_basis_status.argtypes = [PP, ct.c_int, p, p]
+            L.mts_tape_bytes.restype = sz
+            L.mts_tape_bytes.argtypes = [PP, i64, ct.c_int]
+            L.mts_solve.restype = ct.c_int
+            L.mts_solve.argtypes = [PP, ct.c_int, p, PE, p, p, p, sz, p]
+            L.mts_superpose.restype = ct.c_int
+            L.mts_superpose.argtypes = [PP, ct.c_int, p, PE, p, p, p]
+            L.mts_forward.restype = ct.c_int
+            L.mts_forward.argtypes = [PP, ct.c_int, p, PE, p, p, p, p, sz, p]
+            L.mts_backward.restype = ct.c_int
+            L.mts_backward.argtypes = [PP, ct.c_int, p, PE, p, sz, p, p, p, p]
+            L.mts_tape_status.restype = ct.c_int
+            L.mts_tape_status.argtypes = [PP, i64, ct.c_int, p, ct.POINTER(ct.c_int64), p]
+            _lib = L
+    return _lib
+
+
+class MtsError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {mts_status_string(code)}")
+        self.code = code
+
+
+def _check(code: int, where: str):
+    if code != MTS_OK:
+        raise MtsError(code, where)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ct.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> ct.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ct.c_void_p(stream.cuda_stream)
+
+
+def _prec(p) -> int:
+    return PRECISIONS[p] if isinstance(p, str) else int(p)
+
+
+# ---------------------------------------------------------------------------------------
+# problem / eval holders (keep the tensors that the ctypes structs point to alive)
+# ---------------------------------------------------------------------------------------
+class Problem:
+    """Device and host copies of a batch of structures (mts_problem)."""
+
+    def __init__(self, flat: dict, wire_radius: float, device="cuda"):
+        def dev(a, dt):
+            return torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).to(device)
+        self.h_port_off = np.ascontiguousarray(flat["port_off"], np.int32)
+        self.h_point_off = np.ascontiguousarray(flat["point_off"], np.int64)
+        self.h_freq_off = np.ascontiguousarray(flat["freq_off"], np.int32)
+        self.h_loss_off = np.ascontiguousarray(flat["loss_off"], np.int32)
+        self.d = {
+            "port_off": dev(flat["port_off"], np.int32), "point_off": dev(flat["point_off"], np.int64),
+            "freq_off": dev(flat["freq_off"], np.int32), "loss_off": dev(flat["loss_off"], np.int32),
+            "loop_vtx_off": dev(flat["loop_vtx_off"], np.int32),
+            "vx": dev(flat["vx"], np.float64), "vy": dev(flat["vy"], np.float64),
+            "vz": dev(flat["vz"], np.float64), "px": dev(flat["px"], np.float64),
+            "py": dev(flat["py"], np.float64), "pz": dev(flat["pz"], np.float64),
+            "loss_idx": dev(flat["loss_idx"], np.int64), "R": dev(flat["R"], np.float64),
+        }
+        if flat.get("L_self") is not None:
+            self.d["L_self"] = dev(flat["L_self"], np.float64)
+        n_struct = len(self.h_port_off) - 1
+        c = MtsProblem()
+        c.n_struct = n_struct
+        c.n_ports = int(self.h_port_off[-1])
+        c.n_vertices = len(flat["vx"])
+        c.n_freq = int(self.h_freq_off[-1])
+        c.n_points = int(self.h_point_off[-1])
+        c.n_loss = int(self.h_loss_off[-1])
+        c.wire_radius = float(wire_radius)
+        c.h_port_off = self.h_port_off.ctypes.data
+        c.h_point_off = self.h_point_off.ctypes.data
+        c.h_freq_off = self.h_freq_off.ctypes.data
+        c.h_loss_off = self.h_loss_off.ctypes.data
+        for k in ("port_off", "point_off", "freq_off", "loss_off", "loop_vtx_off", "vx", "vy",
+                  "vz", "px", "py", "pz", "loss_idx", "R"):
+            setattr(c, k, self.d[k].data_ptr() if self.d[k].numel() else None)
+        c.L_self = self.d["L_self"].data_ptr() if "L_self" in self.d else None
+        self.c = c
+        self.n_struct = n_struct
+
+    @property
+    def ref(self):
+        return ct.byref(self.c)
+
+
+class Eval:
+    """Per-call inputs (mts_eval): C [n_cfg, n_ports], omega, V (complex), target."""
+
+    def __init__(self, C: torch.Tensor, omega: torch.Tensor, V: torch.Tensor,
+                 target: Optional[torch.Tensor] = None, target_per_cfg: bool = False,
+                 loss_mode: int = MTS_LOSS_ABS, refine_tol: float = 0.0, max_refine: int = 0):
+        self.C = C.contiguous()
+        self.omega = omega.contiguous()
+        self.V = V.contiguous()
+        self.target = None if target is None else target.contiguous()
+        e = MtsEval()
+        e.n_cfg = self.C.shape[0]
+        e.C = self.C.data_ptr()
+        e.omega = self.omega.data_ptr()
+        e.V = self.V.data_ptr()
+        e.target = None if self.target is None else self.target.data_ptr()
+        e.target_per_cfg = int(target_per_cfg)
+        e.loss_mode = int(loss_mode)
+        e.refine_tol = float(refine_tol)
+        e.max_refine = int(max_refine)
+        self.c = e
+
+    @property
+    def n_cfg(self) -> int:
+        return int(self.c.n_cfg)
+
+    @property
+    def ref(self):
+        return ct.byref(self.c)
+
+
+# ---------------------------------------------------------------------------------------
+# the C ABI, one Python function per entry point
+# ---------------------------------------------------------------------------------------
+def mts_status_string(code: int) -> str:
+    return lib().mts_status_string(int(code)).decode()
+
+
+def mts_version() -> str:
+    return lib().mts_version().decode()
+
+
+def mts_launch_count() -> int:
+    return int(lib().mts_launch_count())
+
+
+def mts_basis_bytes(pb: Problem, prec) -> int:
+    return int(lib().mts_basis_bytes(pb.ref, _prec(prec)))
+
+
+def mts_build_basis(pb: Problem, prec, basis: torch.Tensor, stream=None):
+    _check(lib().mts_build_basis(pb.ref, _prec(prec), _ptr(basis), basis.numel() * basis.element_size(),
+                                 _stream(stream)), "mts_build_basis")
+
+
+def mts_basis_export(pb: Problem, prec, basis: torch.Tensor, H_out=None, M_out=None, stream=None):
+    _check(lib().mts_basis_export(pb.ref, _prec(prec), _ptr(basis), _ptr(H_out), _ptr(M_out),
+                                  _stream(stream)), "mts_basis_export")
+
+
+def mts_basis_status(pb: Problem, prec, basis: torch.Tensor, stream=None) -> int:
+    return int(lib().mts_basis_status(pb.ref, _prec(prec), _ptr(basis), _stream(stream)))
+
+
+def mts_tape_bytes(pb: Problem, n_cfg: int, prec) -> int:
+    return int(lib().mts_tape_bytes(pb.ref, int(n_cfg), _prec(prec)))
+
+
+def mts_solve(pb, prec, basis, ev: Eval, I_out=None, loss_out=None, tape=None, stream=None):
+    _check(lib().mts_solve(pb.ref, _prec(prec), _ptr(basis), ev.ref, _ptr(I_out), _ptr(loss_out),
+                           _ptr(tape), tape.numel() * tape.element_size(), _stream(stream)),
+           "mts_solve")
+
+
+def mts_superpose(pb, prec, basis, ev: Eval, tape, B_out, stream=None):
+    _check(lib().mts_superpose(pb.ref, _prec(prec), _ptr(basis), ev.ref, _ptr(tape), _ptr(B_out),
+                               _stream(stream)), "mts_superpose")
+
+
+def mts_forward(pb, prec, basis, ev: Eval, B_out=None, I_out=None, loss_out=None, tape=None,
+                stream=None):
+    _check(lib().mts_forward(pb.ref, _prec(prec), _ptr(basis), ev.ref, _ptr(B_out), _ptr(I_out),
+                             _ptr(loss_out), _ptr(tape), tape.numel() * tape.element_size(),
+                             _stream(stream)), "mts_forward")
+
+
+def mts_backward(pb, prec, basis, ev: Eval, tape, grad_B=None, grad_loss=None, grad_C=None,
+                 stream=None):
+    _check(lib().mts_backward(pb.ref, _prec(prec), _ptr(basis), ev.ref, _ptr(tape),
+                              tape.numel() * tape.element_size(), _ptr(grad_B), _ptr(grad_loss),
+                              _ptr(grad_C), _stream(stream)), "mts_backward")
+
+
+def mts_tape_status(pb, n_cfg: int, prec, tape, stream=None):
+    n_bad = ct.c_int64(0)
+    code = lib().mts_tape_status(pb.ref, int(n_cfg), _prec(prec), _ptr(tape), ct.byref(n_bad),
+                                 _stream(stream))
+    return int(code), int(n_bad.value)
+
+
+def alloc_bytes(nbytes: int, device="cuda") -> torch.Tensor:
+    """A device byte buffer; torch's allocator returns 512-byte aligned blocks."""
+    t = torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+    assert t.data_ptr() % 256 == 0
+    return t

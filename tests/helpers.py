@@ -1,0 +1,116 @@
+"""Test helpers: run the FP64 oracle over a (possibly ragged) workload, in the layouts of
+the C ABI, and relative-error metrics. Expected values come only from oracle/."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+from paper_2503_18479_gb300 import workloads as W
+
+
+def rel(a, b) -> float:
+    a = np.asarray(a)
+    b = np.asarray(b)
+    den = np.linalg.norm(b.ravel())
+    return float(np.linalg.norm((a - b).ravel()) / (den if den > 0 else 1.0))
+
+
+def cosine(a, b) -> float:
+    a = np.asarray(a, float).ravel()
+    b = np.asarray(b, float).ravel()
+    return float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))
+
+
+def structure_basis(wl: W.Workload, s: int):
+    st = wl.structures[s]
+    H = oracle.basis(st.loop_vtx_off, st.vx, st.vy, st.vz, st.px, st.py, st.pz, wl.wire_radius)
+    status, M = oracle.inductance(st.loop_vtx_off, st.vx, st.vy, st.vz, wl.wire_radius, st.L_self)
+    assert status == 0
+    return H, M
+
+
+def apply_target_rule(wl: W.Workload, bases=None) -> W.Workload:
+    """Targets |Bz| at a fixed capacitance (the 'field at C = X' rule), from the oracle."""
+    if wl.target is not None or wl.target_rule is None:
+        return wl
+    kind, c0 = wl.target_rule
+    assert kind == "field_at_C"
+    blocks = []
+    for s, st in enumerate(wl.structures):
+        H, M = bases[s] if bases is not None else structure_basis(wl, s)
+        C0 = np.full((1, st.n_ports), c0)
+        out = oracle.forward(H, M, st.R, C0, st.omega, st.V, want_loss=False)
+        blocks.append(np.abs(out["B"][0][:, st.loss_idx]).ravel())
+    wl.target = np.concatenate(blocks)
+    return wl
+
+
+def oracle_reference(wl: W.Workload, want_B: bool = True, want_grad: bool = True, cfg=None,
+                     gB=None, bases=None):
+    """Per-structure oracle results. cfg: optional index array of configurations."""
+    res = []
+    for s, st in enumerate(wl.structures):
+        H, M = bases[s] if bases is not None else structure_basis(wl, s)
+        C = wl.structure_C(s)
+        if cfg is not None:
+            C = C[cfg]
+        t = None
+        if wl.target is not None:
+            t = wl.structure_target(s)
+            if wl.target_per_cfg and cfg is not None:
+                t = t[cfg]
+            if wl.loss_mode == 1:
+                t = np.ascontiguousarray(t)
+        out = oracle.forward(H, M, st.R, C, st.omega, st.V, st.loss_idx if t is not None else None,
+                             t, mode=wl.loss_mode, target_per_cfg=wl.target_per_cfg,
+                             want_B=want_B, want_loss=t is not None)
+        r = {"H": H, "M": M, "I": out["I"], "B": out["B"], "loss": out["loss"]}
+        if want_grad and t is not None:
+            r["grad"] = oracle.gradient(H, M, st.R, C, st.omega, st.V, st.loss_idx, t,
+                                        mode=wl.loss_mode, target_per_cfg=wl.target_per_cfg)
+        if gB is not None:
+            r["grad_field"] = oracle.gradient_field(H, M, st.R, C, st.omega, st.V, gB[s])
+        res.append(r)
+    return res
+
+
+def split_B(wl: W.Workload, B: np.ndarray):
+    """Concatenated [n_cfg, sum F_s P_s] field -> list of [n_cfg, F_s, P_s]."""
+    out, o = [], 0
+    for st in wl.structures:
+        n = st.n_freq * st.n_points
+        out.append(B[:, o:o + n].reshape(B.shape[0], st.n_freq, st.n_points))
+        o += n
+    return out
+
+
+def split_I(wl: W.Workload, I: np.ndarray):
+    out, o = [], 0
+    for st in wl.structures:
+        n = st.n_freq * st.n_ports
+        out.append(I[:, o:o + n].reshape(I.shape[0], st.n_freq, st.n_ports))
+        o += n
+    return out
+
+
+def split_ports(wl: W.Workload, G: np.ndarray):
+    po = wl.port_off()
+    return [G[:, po[s]:po[s + 1]] for s in range(len(wl.structures))]
+
+
+def small_8x8(n_cfg=200, grid=24, planes=(0.02, 0.04), seed=0):
+    return W.array_8x8(seed=seed, n_cfg=n_cfg, grid=grid, planes=planes)
+
+
+def small_line(n_cfg=96, n_freq=5, grid=20, seed=0):
+    wl = W.line_8x1(seed=seed, n_cfg=n_cfg, n_freq=n_freq, grid=grid)
+    return apply_target_rule(wl)
+
+
+def small_loop(n_cfg=16, n_freq=11, grid=16, seed=0):
+    wl = W.single_loop(seed=seed, n_cfg=n_cfg, n_freq=n_freq, grid=grid)
+    return apply_target_rule(wl)
+
+
+def small_ragged(n_struct=12, seed=3, grid=12, max_freq=4, ports=(1, 8, 16, 32, 64)):
+    return W.ragged(seed=seed, n_struct=n_struct, grid=grid, max_freq=max_freq, port_choices=ports)

@@ -1,0 +1,167 @@
+"""C ABI checks that need no GPU: the library builds, loads, exports every entry point that
+include/mts.h declares, and its host-side validation and size queries behave as documented.
+No call here reaches a CUDA launch."""
+import ctypes as ct
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2503_18479_gb300 import build_lib
+from paper_2503_18479_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def nv():
+    build_lib.build()
+    from paper_2503_18479_gb300 import native
+    native.lib()
+    return native
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "mts.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mts_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_abi():
+    syms = declared_symbols()
+    for name in ("mts_build_basis", "mts_forward", "mts_backward", "mts_solve", "mts_superpose",
+                 "mts_basis_bytes", "mts_tape_bytes", "mts_status_string"):
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol(nv):
+    L = nv.lib()
+    for name in declared_symbols():
+        assert hasattr(L, name), name
+    assert sorted(nv.EXPORTED) == declared_symbols()
+
+
+def test_status_strings_and_version(nv):
+    assert nv.mts_status_string(0) == "MTS_OK"
+    for c in range(1, 6):
+        assert nv.mts_status_string(c).startswith("MTS_E")
+    assert "sm_103a" in nv.mts_version()
+    assert nv.mts_launch_count() == 0  # nothing launched in this process
+
+
+FAKE = 0x10000  # a non-null device address; the calls below never dereference it
+
+
+def fake_problem(nv, wl, **over):
+    flat = wl.flat()
+    keep = {k: np.ascontiguousarray(flat[k]) for k in ("port_off", "point_off", "freq_off", "loss_off")}
+    c = nv.MtsProblem()
+    c.n_struct = len(wl.structures)
+    c.n_ports = int(keep["port_off"][-1])
+    c.n_vertices = len(flat["vx"])
+    c.n_freq = int(keep["freq_off"][-1])
+    c.n_points = int(keep["point_off"][-1])
+    c.n_loss = int(keep["loss_off"][-1])
+    c.wire_radius = wl.wire_radius
+    c.h_port_off = keep["port_off"].ctypes.data
+    c.h_point_off = keep["point_off"].ctypes.data
+    c.h_freq_off = keep["freq_off"].ctypes.data
+    c.h_loss_off = keep["loss_off"].ctypes.data
+    for k in ("port_off", "point_off", "freq_off", "loss_off", "loop_vtx_off", "vx", "vy", "vz",
+              "px", "py", "pz", "loss_idx", "R"):
+        setattr(c, k, FAKE)
+    c.L_self = None
+    for k, v in over.items():
+        setattr(c, k, v)
+    return c, keep
+
+
+def test_size_queries(nv):
+    wl = W.array_8x8(n_cfg=4, grid=8, planes=(0.02,))
+    c, keep = fake_problem(nv, wl)
+    L = nv.lib()
+    b64 = L.mts_basis_bytes(ct.byref(c), nv.MTS_FP64)
+    bmx = L.mts_basis_bytes(ct.byref(c), nv.MTS_MIXED)
+    P, N = wl.n_points, 64
+    assert b64 >= 8 * P * N + 8 * N * N
+    # mixed: FP32 H plus three bf16 pieces of the padded operand
+    assert bmx >= 4 * P * N + 3 * 2 * ((P + 127) // 128 * 128) * 64
+    t1 = L.mts_tape_bytes(ct.byref(c), 1, nv.MTS_MIXED)
+    t2 = L.mts_tape_bytes(ct.byref(c), 4096, nv.MTS_MIXED)
+    assert t2 > t1 > 0
+    assert t2 >= 4096 * 64 * 16  # the currents alone
+    assert L.mts_tape_bytes(ct.byref(c), -1, nv.MTS_MIXED) == 0
+    assert L.mts_basis_bytes(ct.byref(c), 7) == 0
+
+
+def test_validation_rejects_bad_problems(nv):
+    L = nv.lib()
+    wl = W.array_8x8(n_cfg=2, grid=8, planes=(0.02,))
+    cases = [dict(n_struct=0), dict(wire_radius=0.0), dict(wire_radius=float("nan")),
+             dict(n_ports=63), dict(port_off=None), dict(R=None), dict(loss_idx=None)]
+    for over in cases:
+        c, keep = fake_problem(nv, wl, **over)
+        assert L.mts_basis_bytes(ct.byref(c), nv.MTS_MIXED) == 0, over
+        code = L.mts_build_basis(ct.byref(c), nv.MTS_MIXED, ct.c_void_p(FAKE), 1 << 40, None)
+        assert code == nv.MTS_EINVAL, over
+    # too many ports in one structure
+    big = W.ragged(n_struct=1, grid=4, max_freq=1, port_choices=(128,))
+    c, keep = fake_problem(nv, big)
+    assert L.mts_basis_bytes(ct.byref(c), nv.MTS_MIXED) > 0
+    # non-monotonic host offsets
+    wl2 = W.ragged(n_struct=3, grid=4, max_freq=2, port_choices=(8,))
+    c, keep = fake_problem(nv, wl2)
+    keep["port_off"][1], keep["port_off"][2] = keep["port_off"][2], keep["port_off"][1]
+    assert L.mts_basis_bytes(ct.byref(c), nv.MTS_FP64) == 0
+
+
+def test_workspace_and_alignment_checks(nv):
+    L = nv.lib()
+    wl = W.array_8x8(n_cfg=2, grid=8, planes=(0.02,))
+    c, keep = fake_problem(nv, wl)
+    need = L.mts_basis_bytes(ct.byref(c), nv.MTS_MIXED)
+    assert L.mts_build_basis(ct.byref(c), nv.MTS_MIXED, ct.c_void_p(FAKE), need - 1, None) == nv.MTS_EWORKSPACE
+    assert L.mts_build_basis(ct.byref(c), nv.MTS_MIXED, ct.c_void_p(FAKE + 8), need, None) == nv.MTS_EINVAL
+    assert L.mts_build_basis(ct.byref(c), nv.MTS_MIXED, None, need, None) == nv.MTS_EINVAL
+    ev = nv.MtsEval()
+    ev.n_cfg = 2
+    ev.C = ev.omega = ev.V = FAKE
+    ev.target = None
+    ev.loss_mode = 0
+    tneed = L.mts_tape_bytes(ct.byref(c), 2, nv.MTS_MIXED)
+    code = L.mts_solve(ct.byref(c), nv.MTS_MIXED, ct.c_void_p(FAKE), ct.byref(ev), None, None,
+                       ct.c_void_p(FAKE), tneed - 1, None)
+    assert code == nv.MTS_EWORKSPACE
+    ev.loss_mode = 5
+    code = L.mts_solve(ct.byref(c), nv.MTS_MIXED, ct.c_void_p(FAKE), ct.byref(ev), None, None,
+                       ct.c_void_p(FAKE), tneed, None)
+    assert code == nv.MTS_EINVAL
+    ev.loss_mode = 0
+    ev.C = None
+    code = L.mts_forward(ct.byref(c), nv.MTS_MIXED, ct.c_void_p(FAKE), ct.byref(ev), None, None,
+                         None, ct.c_void_p(FAKE), tneed, None)
+    assert code == nv.MTS_EINVAL
+    # a loss output without a target
+    ev.C = FAKE
+    code = L.mts_solve(ct.byref(c), nv.MTS_MIXED, ct.c_void_p(FAKE), ct.byref(ev), None,
+                       ct.c_void_p(FAKE), ct.c_void_p(FAKE), tneed, None)
+    assert code == nv.MTS_EINVAL
+    assert L.mts_backward(ct.byref(c), nv.MTS_MIXED, ct.c_void_p(FAKE), ct.byref(ev),
+                          ct.c_void_p(FAKE), tneed, None, None, None, None) == nv.MTS_EINVAL
+    assert nv.mts_launch_count() == 0
+
+
+def test_solver_size_limit_is_reported(nv):
+    """Structures with more than 64 ports validate, but the solve reports MTS_EUNSUPPORTED
+    (before any launch) until the large-system kernels exist."""
+    L = nv.lib()
+    wl = W.ragged(n_struct=2, grid=4, max_freq=1, port_choices=(128,))
+    c, keep = fake_problem(nv, wl)
+    ev = nv.MtsEval()
+    ev.n_cfg = 1
+    ev.C = ev.omega = ev.V = FAKE
+    tneed = L.mts_tape_bytes(ct.byref(c), 1, nv.MTS_MIXED)
+    code = L.mts_solve(ct.byref(c), nv.MTS_MIXED, ct.c_void_p(FAKE), ct.byref(ev), None, None,
+                       ct.c_void_p(FAKE), tneed, None)
+    assert code == nv.MTS_EUNSUPPORTED

@@ -1,0 +1,162 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on seeded inputs.
+
+Tolerances (relative L2 over the whole tensor): MTS_FP64 <= 1e-10; MTS_MIXED <= 1e-6 on the
+field B, the objective and dloss/dC, with gradient cosine >= 0.9999; MTS_BF16 <= 1e-2 on B.
+Sizes span several 128-point tiles and 64-system column tiles with ragged tails."""
+import numpy as np
+import pytest
+import torch
+
+from helpers import (apply_target_rule, cosine, oracle_reference, rel, small_8x8, small_line,
+                     small_loop, small_ragged, split_B, split_I, split_ports, structure_basis)
+from paper_2503_18479_gb300 import build_lib
+from paper_2503_18479_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL_B = {"fp64": 1e-10, "mixed": 1e-6, "bf16": 1e-2}
+TOL_I = {"fp64": 1e-10, "mixed": 1e-9, "bf16": 1e-9}
+TOL_LOSS = {"fp64": 1e-10, "mixed": 1e-6, "bf16": 1e-6}
+TOL_GRAD = {"fp64": 1e-10, "mixed": 1e-6, "bf16": 1e-6}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build_lib.build()
+
+
+_CASES = {
+    "loop": lambda: small_loop(),
+    "line": lambda: small_line(),
+    "8x8": lambda: small_8x8(),
+    "ragged": lambda: apply_target_rule(small_ragged()),
+}
+_cache = {}
+
+
+def case(name):
+    if name not in _cache:
+        wl = _CASES[name]()
+        bases = [structure_basis(wl, s) for s in range(len(wl.structures))]
+        ref = oracle_reference(wl, bases=bases)
+        _cache[name] = (wl, ref)
+    return _cache[name]
+
+
+def sim_for(wl, prec):
+    from paper_2503_18479_gb300.simulator import Simulator
+    return Simulator(wl, prec)
+
+
+@pytest.mark.parametrize("name", list(_CASES))
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_basis(name, prec):
+    wl, ref = case(name)
+    sim = sim_for(wl, prec)
+    H, M = sim.export_basis()
+    H, M = H.cpu().numpy(), M.cpu().numpy()
+    oh, om = 0, 0
+    for s, st in enumerate(wl.structures):
+        n, p = st.n_ports, st.n_points
+        Hs = H[oh:oh + p * n].reshape(p, n)
+        Ms = M[om:om + n * n].reshape(n, n)
+        oh += p * n
+        om += n * n
+        assert rel(Ms, ref[s]["M"]) < 1e-12, (s, rel(Ms, ref[s]["M"]))
+        tol = 1e-12 if prec == "fp64" else 1e-6
+        assert rel(Hs, ref[s]["H"]) < tol, (s, rel(Hs, ref[s]["H"]))
+
+
+@pytest.mark.parametrize("name", list(_CASES))
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "bf16"])
+def test_forward(name, prec):
+    wl, ref = case(name)
+    sim = sim_for(wl, prec)
+    C = torch.from_numpy(wl.C).cuda()
+    out = sim.forward(C, want_I=True)
+    torch.cuda.synchronize()
+    code, n_bad = sim.status(out["tape"], wl.n_cfg)
+    assert code == 0 and n_bad == 0, (code, n_bad)
+    Bs = split_B(wl, out["B"].cpu().numpy())
+    Is = split_I(wl, out["I"].cpu().numpy())
+    loss = out["loss"].cpu().numpy()
+    for s in range(len(wl.structures)):
+        assert rel(Is[s], ref[s]["I"]) < TOL_I[prec], (s, rel(Is[s], ref[s]["I"]))
+        assert rel(Bs[s], ref[s]["B"]) < TOL_B[prec], (s, rel(Bs[s], ref[s]["B"]))
+        assert rel(loss[:, s], ref[s]["loss"]) < TOL_LOSS[prec], (s, rel(loss[:, s], ref[s]["loss"]))
+
+
+@pytest.mark.parametrize("name", list(_CASES))
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_gradient(name, prec):
+    """dloss/dC through torch.autograd (MtsFunction -> mts_backward) against the oracle."""
+    wl, ref = case(name)
+    sim = sim_for(wl, prec)
+    C = torch.from_numpy(wl.C).cuda().requires_grad_(True)
+    B, loss = sim(C, want_B=False)
+    loss.sum().backward()
+    g = split_ports(wl, C.grad.cpu().numpy())
+    for s in range(len(wl.structures)):
+        assert rel(g[s], ref[s]["grad"]) < TOL_GRAD[prec], (s, rel(g[s], ref[s]["grad"]))
+        assert cosine(g[s], ref[s]["grad"]) >= 0.9999
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_field_cotangent(prec):
+    """Backward with a field cotangent dL/dRe B + j dL/dIm B (and a loss cotangent)."""
+    wl, _ = case("8x8")
+    nc = 40
+    cfg = np.arange(nc)
+    sub = W.Workload(wl.name, wl.structures, wl.C[:nc].copy(), wl.wire_radius, target=wl.target)
+    st = sub.structures[0]
+    gB = W.random_cotangent((nc, st.n_freq, st.n_points), seed=7)
+    bases = [structure_basis(sub, 0)]
+    ref = oracle_reference(sub, want_B=False, gB=[gB], bases=bases)
+    sim = sim_for(sub, prec)
+    C = torch.from_numpy(sub.C).cuda().requires_grad_(True)
+    B, loss = sim(C, want_B=True)
+    gl = torch.linspace(0.5, 2.0, nc, dtype=torch.float64, device="cuda")[:, None]
+    gBt = torch.from_numpy(gB.reshape(nc, -1)).to(B.dtype).cuda()
+    torch.autograd.backward([B, loss], [gBt, gl])
+    want = ref[0]["grad_field"] + gl.cpu().numpy() * ref[0]["grad"]
+    tol = 1e-9 if prec == "fp64" else 1e-5
+    assert rel(C.grad.cpu().numpy(), want) < tol, rel(C.grad.cpu().numpy(), want)
+    assert cosine(C.grad.cpu().numpy(), want) >= 0.9999
+
+
+def test_complex_target_mode():
+    """|B - t|^2 with complex targets per configuration (loss_mode = 1, target_per_cfg)."""
+    wl0 = small_8x8(n_cfg=70)
+    rng = np.random.Generator(np.random.PCG64(5))
+    t = rng.standard_normal((70, 1, 64, 2)) * 1e-6
+    wl = W.Workload(wl0.name, wl0.structures, wl0.C, wl0.wire_radius, loss_mode=1,
+                    target=t.ravel(), target_per_cfg=True)
+    ref = oracle_reference(wl, want_B=False)
+    for prec, tol in (("fp64", 1e-10), ("mixed", 1e-6)):
+        sim = sim_for(wl, prec)
+        C = torch.from_numpy(wl.C).cuda().requires_grad_(True)
+        _, loss = sim(C, want_B=False)
+        loss.sum().backward()
+        assert rel(loss.detach().cpu().numpy()[:, 0], ref[0]["loss"]) < tol
+        assert rel(C.grad.cpu().numpy(), ref[0]["grad"]) < tol
+
+
+def test_single_config_and_launch_count():
+    from paper_2503_18479_gb300 import native as nv
+    wl = small_8x8(n_cfg=1, grid=8, planes=(0.02,))
+    ref = oracle_reference(wl)
+    sim = sim_for(wl, "mixed")
+    n0 = nv.mts_launch_count()
+    out = sim.forward(torch.from_numpy(wl.C).cuda())
+    torch.cuda.synchronize()
+    assert nv.mts_launch_count() > n0
+    assert rel(split_B(wl, out["B"].cpu().numpy())[0], ref[0]["B"]) < 1e-6
+
+
+def test_zero_configurations():
+    wl = small_8x8(n_cfg=3, grid=8, planes=(0.02,))
+    sim = sim_for(wl, "mixed")
+    out = sim.forward(torch.zeros((0, 64), dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+    assert out["B"].shape == (0, wl.n_points)
