@@ -324,7 +324,12 @@ __global__ void __launch_bounds__(kThreads, 1) superpose_tc_kernel(SuperposeArgs
     float2* Bout = static_cast<float2*>(a.B_out);
     for (int64_t u = u_begin; u < u_end; ++u) {
       Unit x = unit_info(a, u);
-      if (!mbar_wait(&tfull[acc], aphase, err, 4)) break;
+      // lane 0 does the bounded wait; the outcome is made warp-uniform before the
+      // warp-collective tcgen05.ld
+      int ok = (lane == 0) ? (int)mbar_wait(&tfull[acc], aphase, err, 4) : 1;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      mbar_wait(&tfull[acc], aphase, err, 4);  // already complete: acquire for every lane
       tc_fence_after();
       float v[128];
       const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)acc * 128u;
