@@ -1,0 +1,426 @@
+"""Benchmark: forward + adjoint of the 8x8 loop metasurface (64 ports, 4096 capacitance
+configurations, 65,536 grid points + 64 loss points, 63.6 MHz) through the C ABI.
+
+One step = mts_solve (port solves, objective, adjoint gradient at the loss points) +
+mts_superpose (the full field B = H I, complex64) + mts_backward (grad_C from the loss
+cotangent) over one batch of 4096 configurations. Inputs are resident in HBM; L2 is flushed
+(256 MB write) between timed steps. Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--precision mixed|bf16|fp64] [--no-cpu-baseline] [--no-fp64-path]
+
+--impl reference times the CPU oracle (the reference implementation of the method for this
+build) on the host cores, on a bounded sample of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "8×8 array forward+adjoint configs/s at rel err ≤1e-6 vs FP64; % of roofline"
+UNIT = "configs/s"
+N_CFG = 4096
+WORKLOAD = ("array_8x8: 8x8 square loops (side 50 mm, pitch 55 mm, 16 segments/side, 64 ports), "
+            "4096 configs C~U[20,200] pF, 1 freq 63.6 MHz, Bz on 4x128x128 points at z=10..40 mm "
+            "+ 64 loss points at z=40 mm, loss |Bz| MSE to N(0,1)e-6 T targets")
+# ncu DRAM traffic of the superposition kernel per launch at the full workload (bytes),
+# with the hash of the kernel source it was taken from; reported as null once the source
+# changes. Filled from profiles/superpose_tc_array_8x8.md.
+TRAFFIC = {"superpose_tc.cu": {"sha256_12": None, "bytes": None}}
+
+
+def sha12(path):
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:12]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "bf16", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-path", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--n-cfg", type=int, default=N_CFG, help="configurations per GPU (profiling runs)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, pw, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                pw.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(pw) if pw else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_uuid(dev):
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(dev.index if dev.index is not None else 0)
+
+
+# ---------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------
+def run_ours(args, rank, world, local):
+    import torch
+    import torch.distributed as tdist
+
+    from paper_2503_18479_gb300 import native as nv
+    from paper_2503_18479_gb300 import workloads as W
+    from paper_2503_18479_gb300.build_lib import build
+    from paper_2503_18479_gb300.simulator import Simulator
+
+    build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        tdist.init_process_group("nccl", device_id=dev)
+    wl = W.array_8x8(seed=rank, n_cfg=args.n_cfg)
+    prec = args.precision
+    sim = Simulator(wl, prec, device=dev)
+    st = torch.cuda.current_stream()
+    n_cfg = wl.n_cfg
+    C = torch.from_numpy(wl.C).to(dev)
+    ev = sim.make_eval(C, True)
+    tape = sim.alloc_tape(n_cfg)
+    B = torch.empty((n_cfg, sim.sumFP), dtype=sim.b_dtype, device=dev)
+    loss = torch.empty((n_cfg, 1), dtype=torch.float64, device=dev)
+    grad_C = torch.empty((n_cfg, sim.n_ports), dtype=torch.float64, device=dev)
+    gl = torch.ones((n_cfg, 1), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step(e_mid1=None, e_mid2=None):
+        nv.mts_solve(sim.pb, sim.prec, sim.basis, ev, None, loss, tape)
+        if e_mid1 is not None:
+            e_mid1.record(st)
+        nv.mts_superpose(sim.pb, sim.prec, sim.basis, ev, tape, B)
+        if e_mid2 is not None:
+            e_mid2.record(st)
+        nv.mts_backward(sim.pb, sim.prec, sim.basis, ev, tape, None, gl, grad_C)
+
+    for _ in range(max(args.warmup, 3)):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+    code, n_bad = sim.status(tape, n_cfg)
+
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    sampler = ClockSampler(gpu_uuid(dev))
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    n0 = nv.mts_launch_count()
+    t_wall = time.perf_counter()
+    for i in range(K):
+        flush.fill_(1)
+        e0, e1, e2, e3 = evs[i]
+        e0.record(st)
+        step(e1, e2)
+        e3.record(st)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        tdist.barrier()
+    launches = nv.mts_launch_count() - n0
+    clocks = sampler.stop()
+    total_ms = sum(e[0].elapsed_time(e[3]) for e in evs)
+    gemm_ms = sum(e[1].elapsed_time(e[2]) for e in evs) / K
+    solve_ms = sum(e[0].elapsed_time(e[1]) for e in evs) / K
+    bwd_ms = sum(e[2].elapsed_time(e[3]) for e in evs) / K
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    value = world * n_cfg * K / (max_ms / 1e3)
+
+    # ---- end to end through the public API, host buffers, copies inside the timed region
+    Ch = torch.from_numpy(wl.C).pin_memory()
+    loss_h = torch.empty((n_cfg, 1), dtype=torch.float64).pin_memory()
+    grad_h = torch.empty((n_cfg, sim.n_ports), dtype=torch.float64).pin_memory()
+    Cd = torch.empty_like(C)
+    ev2 = sim.make_eval(Cd, True)
+    KE = max(1, min(args.e2e_steps, K))
+
+    def e2e_step():
+        Cd.copy_(Ch, non_blocking=True)
+        nv.mts_forward(sim.pb, sim.prec, sim.basis, ev2, B, None, loss, tape)
+        nv.mts_backward(sim.pb, sim.prec, sim.basis, ev2, tape, None, gl, grad_C)
+        loss_h.copy_(loss, non_blocking=True)
+        grad_h.copy_(grad_C, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = 0.0
+    for _ in range(KE):
+        flush.fill_(1)
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(st)
+        e2e_step()
+        a1.record(st)
+        a1.synchronize()  # the host reads the result
+        e2e_ms += a0.elapsed_time(a1)
+    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        tdist.all_reduce(te, op=tdist.ReduceOp.MAX)
+    e2e_value = world * n_cfg * KE / (float(te.item()) / 1e3)
+
+    # ---- roofline of the dominant kernel (superposition): algorithmic bytes per launch
+    P = wl.n_points
+    npc = {"mixed": 3, "bf16": 1, "fp64": 0}[prec]
+    if prec == "fp64":
+        alg_bytes = n_cfg * P * 16 + P * 64 * 8 + n_cfg * 64 * 16
+    else:
+        alg_bytes = n_cfg * P * 8 + npc * 2 * ((P + 127) // 128 * 128) * 64 + npc * 2 * 2 * n_cfg * 64
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        hbm_peak, peak_src = float(peaks["hbm_gbs"]), "measured"
+    except Exception:
+        hbm_peak, peak_src = 6800.0, "fallback"
+    achieved = alg_bytes / (gemm_ms / 1e3) / 1e9
+    src_hash = sha12(os.path.join(ROOT, "paper_2503_18479_gb300", "csrc", "superpose_tc.cu"))
+    tr = TRAFFIC["superpose_tc.cu"]
+    traffic = tr["bytes"] if (tr["sha256_12"] == src_hash and prec != "fp64") else None
+
+    # ---- FP64 GPU path on the same workload (context for the mixed-precision speed-up)
+    fp64_path = None
+    if not args.no_fp64_path and prec != "fp64":
+        sim64 = Simulator(wl, "fp64", device=dev)
+        ev64 = sim64.make_eval(C, True)
+        tape64 = sim64.alloc_tape(n_cfg)
+        B64 = torch.empty((n_cfg, sim64.sumFP), dtype=torch.complex128, device=dev)
+        loss64 = torch.empty((n_cfg, 1), dtype=torch.float64, device=dev)
+        g64 = torch.empty_like(grad_C)
+
+        def step64():
+            nv.mts_forward(sim64.pb, sim64.prec, sim64.basis, ev64, B64, None, loss64, tape64)
+            nv.mts_backward(sim64.pb, sim64.prec, sim64.basis, ev64, tape64, None, gl, g64)
+
+        step64()
+        torch.cuda.synchronize()
+        k64 = 3
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(st)
+        for _ in range(k64):
+            step64()
+        a1.record(st)
+        a1.synchronize()
+        ms64 = a0.elapsed_time(a1) / k64
+        fp64_path = {"value": n_cfg / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64, "steps": k64,
+                     "speedup_of_this_line": (n_cfg * K / (total_ms / 1e3)) / (n_cfg / (ms64 / 1e3))}
+        del B64, sim64
+        torch.cuda.empty_cache()
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": max_ms / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"mixed": "f32 LU + df64 residual + bf16x3 tensor-core (f32 accum)",
+                  "bf16": "f32 LU + df64 residual + bf16 tensor-core (f32 accum)",
+                  "fp64": "f64"}[prec],
+        "data": "synthetic (seeded PCG64 per rank); shapes of the paper's 8x8 metasurface",
+        "config": {"workload": WORKLOAD, "n_cfg_per_gpu": n_cfg, "points": P, "ports": 64,
+                   "precision": prec, "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"replicas x{world} (independent batches, no collective)"},
+        "field_points_per_s": value * P,
+        "breakdown_ms": {"solve_loss_adjoint": solve_ms, "superpose": gemm_ms, "backward": bwd_ms},
+        "e2e": {"value": e2e_value, "unit": UNIT, "steps": KE,
+                "h2d_bytes_per_step": int(Ch.numel() * 8),
+                "d2h_bytes_per_step": int(loss_h.numel() * 8 + grad_h.numel() * 8),
+                "note": "C copied in, loss and grad_C copied out; the field B stays on the device"},
+        "gpu_launches": int(launches),
+        "gpu_launches_per_step": launches / K,
+        "roofline": {"kernel": "superpose_tc_kernel" if prec != "fp64" else "superpose_fp64_kernel",
+                     "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+                     "peak_source": f"{peak_src} hbm_gbs", "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": gemm_ms},
+        "clocks": clocks,
+        "wall_s_timed_loop": t_wall,
+        "status": {"code": code, "systems_flagged": n_bad},
+        "fp64_path": fp64_path,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"], out["accuracy"] = cpu_baseline_and_accuracy(wl, sim, C, B, loss, grad_C, gl, tape, ev)
+    if world > 1:
+        tdist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def cpu_baseline_and_accuracy(wl, sim, C, B, loss, grad_C, gl, tape, ev):
+    """Time the FP64 oracle (as it stands) on a bounded sample of the same workload on the
+    host cores, and compare the GPU outputs of the same configurations with it."""
+    import torch
+
+    import oracle
+    from paper_2503_18479_gb300 import native as nv
+    st = wl.structures[0]
+    H = oracle.basis(st.loop_vtx_off, st.vx, st.vy, st.vz, st.px, st.py, st.pz, wl.wire_radius)
+    _, M = oracle.inductance(st.loop_vtx_off, st.vx, st.vy, st.vz, wl.wire_radius)
+    t = wl.structure_target(0)
+    # calibrate, then size the sample for ~10 s of CPU work
+    t0 = time.perf_counter()
+    oracle.forward(H, M, st.R, wl.C[:8], st.omega, st.V, st.loss_idx, t)
+    oracle.gradient(H, M, st.R, wl.C[:8], st.omega, st.V, st.loss_idx, t)
+    per = (time.perf_counter() - t0) / 8
+    n = int(max(8, min(wl.n_cfg, 10.0 / max(per, 1e-6))))
+    idx = np.arange(n)
+    t0 = time.perf_counter()
+    ref = oracle.forward(H, M, st.R, wl.C[idx], st.omega, st.V, st.loss_idx, t)
+    g = oracle.gradient(H, M, st.R, wl.C[idx], st.omega, st.V, st.loss_idx, t)
+    dt = time.perf_counter() - t0
+    cores = oracle.num_threads()
+    base = {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} of the 4096 configurations, forward (full field at all {wl.n_points} points) "
+                      f"+ loss + adjoint gradient, FP64, {cores} OpenMP threads; basis setup untimed"}
+    # accuracy of the GPU path (last timed step) on the same configurations
+    torch.cuda.synchronize()
+    Bg = B[:n].cpu().numpy().reshape(n, 1, -1)
+    lg = loss[:n, 0].cpu().numpy()
+    gg = grad_C[:n].cpu().numpy()
+    rel = lambda a, b: float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+    ga, gb = gg.ravel(), g.ravel()
+    acc = {"sample_configs": n, "B_rel_l2": rel(Bg, ref["B"]), "loss_rel_l2": rel(lg, ref["loss"]),
+           "grad_rel_l2": rel(gg, g), "grad_cosine": float(ga @ gb / (np.linalg.norm(ga) * np.linalg.norm(gb)))}
+    return base, acc
+
+
+# ---------------------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle on the host cores
+# ---------------------------------------------------------------------------------------
+def run_reference(args, rank, world, local):
+    if rank != 0:
+        return
+    import oracle
+    from paper_2503_18479_gb300 import workloads as W
+    oracle.build()
+    wl = W.array_8x8(seed=0, n_cfg=N_CFG)
+    st = wl.structures[0]
+    H = oracle.basis(st.loop_vtx_off, st.vx, st.vy, st.vz, st.px, st.py, st.pz, wl.wire_radius)
+    _, M = oracle.inductance(st.loop_vtx_off, st.vx, st.vy, st.vz, wl.wire_radius)
+    t = wl.structure_target(0)
+
+    def step(idx):
+        oracle.forward(H, M, st.R, wl.C[idx], st.omega, st.V, st.loss_idx, t)
+        oracle.gradient(H, M, st.R, wl.C[idx], st.omega, st.V, st.loss_idx, t)
+
+    t0 = time.perf_counter()
+    step(np.arange(8))
+    per = (time.perf_counter() - t0) / 8
+    K, Wm = args.steps, max(args.warmup, 3)
+    budget = 150.0 / (K + Wm)  # whole run within a few minutes
+    n = int(max(1, min(N_CFG, budget / max(per, 1e-6))))
+    for i in range(Wm):
+        step(np.arange(i * n, i * n + n) % N_CFG)
+    t0 = time.perf_counter()
+    for i in range(K):
+        step(np.arange(i * n, i * n + n) % N_CFG)
+    dt = time.perf_counter() - t0
+    value = n * K / dt
+    cores = oracle.num_threads()
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": K, "warmup": args.warmup, "ms_per_step": dt / K * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded PCG64)",
+           "config": {"workload": WORKLOAD, "sample_configs_per_step": n},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"{n} configurations per step, forward + loss + adjoint, FP64"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "gpu_launches": 0}
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world, local)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()
