@@ -226,6 +226,33 @@ mts_status mts_backward(const mts_problem* pb, mts_precision prec, const void* b
 mts_status mts_tape_status(const mts_problem* pb, int64_t n_cfg, mts_precision prec,
                            const void* tape, int64_t* n_bad, mts_stream stream);
 
+/* ---------------------------------------------------------------------------------
+ * mts_solve_static: mts_solve without a tape, for callers that cannot allocate device
+ * memory when they solve (a real-time loop that may not call the allocator, a plugin
+ * whose host application owns every device allocation, a process with a fixed memory
+ * budget). The paper has no counterpart; this is a deployment convenience.
+ *
+ * The per-call working state lives in one library-owned device array of
+ * MTS_STATIC_SCRATCH_BYTES bytes, which every GPU that loads the library holds until the
+ * process exits. The caller still passes the problem, the basis, the inputs (ev) and the
+ * outputs, all as for mts_solve:
+ *   I_out        device complex [n_cfg][FN] currents, or NULL
+ *   loss_out     device [n_cfg][n_struct] objective, or NULL (needs ev->target)
+ *   dloss_dC_out device [n_cfg][n_ports] dloss_{b,s}/dC of each port's own structure,
+ *                or NULL (needs ev->target)
+ * Returns MTS_EWORKSPACE, before any launch, when the work would need more than
+ * MTS_STATIC_SCRATCH_BYTES (compare mts_tape_bytes(pb, n_cfg, prec)). Calls no device
+ * allocator. The first call on each device looks up the array's device address with that
+ * device current; make that first call before any stream capture. Every call on a device
+ * shares the one array, so calls whose GPU work overlaps in time (other streams, other
+ * threads) race: order them on one stream. The array keeps the last call's contents; each
+ * call clears what must start at zero and never reads a region it did not write.
+ * --------------------------------------------------------------------------------- */
+#define MTS_STATIC_SCRATCH_BYTES (32u << 20)
+mts_status mts_solve_static(const mts_problem* pb, mts_precision prec, const void* basis,
+                            const mts_eval* ev, double* I_out, double* loss_out,
+                            double* dloss_dC_out, mts_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

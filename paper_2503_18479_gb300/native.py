@@ -25,7 +25,8 @@ PRECISIONS = {"fp64": MTS_FP64, "mixed": MTS_MIXED, "bf16": MTS_BF16}
 # symbols declared in include/mts.h
 EXPORTED = ["mts_status_string", "mts_version", "mts_launch_count", "mts_basis_bytes",
             "mts_build_basis", "mts_basis_export", "mts_basis_status", "mts_tape_bytes",
-            "mts_solve", "mts_superpose", "mts_forward", "mts_backward", "mts_tape_status"]
+            "mts_solve", "mts_superpose", "mts_forward", "mts_backward", "mts_tape_status",
+            "mts_solve_static"]
 
 
 class MtsProblem(ct.Structure):
@@ -90,6 +91,8 @@ def lib():
             L.mts_forward.argtypes = [PP, ct.c_int, p, PE, p, p, p, p, sz, p]
             L.mts_backward.restype = ct.c_int
             L.mts_backward.argtypes = [PP, ct.c_int, p, PE, p, sz, p, p, p, p]
+            L.mts_solve_static.restype = ct.c_int
+            L.mts_solve_static.argtypes = [PP, ct.c_int, p, PE, p, p, p, p]
             L.mts_tape_status.restype = ct.c_int
             L.mts_tape_status.argtypes = [PP, i64, ct.c_int, p, ct.POINTER(ct.c_int64), p]
             _lib = L
@@ -268,6 +271,16 @@ def mts_tape_status(pb, n_cfg: int, prec, tape, stream=None):
     code = lib().mts_tape_status(pb.ref, int(n_cfg), _prec(prec), _ptr(tape), ct.byref(n_bad),
                                  _stream(stream))
     return int(code), int(n_bad.value)
+
+
+def mts_solve_static(pb, prec, basis, ev: Eval, I_out=None, loss_out=None, dloss_dC_out=None,
+                     stream=None):
+    """mts_solve without a tape: the library's own fixed device scratch serves as working
+    memory, for callers that cannot allocate device memory when they solve. Calls on one
+    device share that scratch; keep them on one stream."""
+    _check(lib().mts_solve_static(pb.ref, _prec(prec), _ptr(basis), ev.ref, _ptr(I_out),
+                                  _ptr(loss_out), _ptr(dloss_dC_out), _stream(stream)),
+           "mts_solve_static")
 
 
 def alloc_bytes(nbytes: int, device="cuda") -> torch.Tensor:
