@@ -126,11 +126,12 @@ typedef struct mts_problem {
  *   target  device, NULL = no objective; real [FL] (MTS_LOSS_ABS) or complex [FL]
  *           (MTS_LOSS_COMPLEX), structure s at sum_{s'<s} F_s' L_s' as [F_s][L_s];
  *           with target_per_cfg != 0 one such block per configuration ([n_cfg][...]).
- * refine_tol: a system has converged when its last refinement correction satisfies
- *   max|dx| <= refine_tol * max|x| (MTS_MIXED, MTS_BF16; 0 selects 1e-10). Refinement also
- *   stops early when the correction no longer halves (the residual precision, about
- *   cond(A) * 2^-45 relative, is reached); such a system is flagged if it missed
- *   refine_tol. max_refine: refinement steps per solve (0 selects 8).
+ * refine_tol: a system has converged when the estimated relative error of its solution,
+ *   |d_k|^2 / |d_(k-1)| / |x| for the last two refinement corrections (d_0 = x_0), is at most
+ *   refine_tol (MTS_MIXED, MTS_BF16; 0 selects 1e-8). Refinement also stops early when the
+ *   correction no longer halves (the residual precision, about cond(A) * 2^-45 relative,
+ *   is reached); such a system is flagged if it missed refine_tol. max_refine: refinement
+ *   steps per solve (0 selects 8).
  */
 typedef struct mts_eval {
   int64_t n_cfg;

@@ -207,7 +207,7 @@ static SolveArgs solve_args(const mts_problem* pb, mts_precision prec, const voi
   a.target = ev->target;
   a.target_per_cfg = ev->target_per_cfg;
   a.loss_mode = ev->loss_mode;
-  a.tol = ev->refine_tol > 0.0 ? ev->refine_tol : 1e-10;
+  a.tol = ev->refine_tol > 0.0 ? ev->refine_tol : 1e-8;
   a.max_refine = ev->max_refine > 0 ? ev->max_refine : 8;
   a.sumFN = ps.sumFN;
   a.sumFL = ps.sumFL;
