@@ -393,6 +393,15 @@ mts_status mts_superpose(const mts_problem* pb, mts_precision prec, const void* 
   a.npieces = n_pieces(prec);
   a.B_out = B_out;
   a.err = reinterpret_cast<int32_t*>(const_cast<char*>(T) + tl.err);
+  if (pb->n_struct == 1) {
+    a.uni.on = 1;
+    a.uni.N = pb->h_port_off[1];
+    a.uni.F = pb->h_freq_off[1];
+    a.uni.P = pb->h_point_off[1];
+    a.uni.nkc = (a.uni.N + kChunkK - 1) / kChunkK;
+    a.uni.nptile = (a.uni.P + kTileP - 1) / kTileP;
+    a.uni.nntile = (2 * ev->n_cfg * a.uni.F + kTileN - 1) / kTileN;
+  }
   return cuda_status(launch_superpose(a, prec, (cudaStream_t)stream));
 }
 

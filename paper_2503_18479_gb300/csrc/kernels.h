@@ -71,6 +71,14 @@ cudaError_t launch_plan(const mts_problem* pb, int64_t n_cfg, int npieces, int64
 cudaError_t launch_solve(const SolveArgs& a, mts_precision prec, int max_ports, cudaStream_t st);
 cudaError_t launch_reduce(const ReduceArgs& a, cudaStream_t st);
 
+// Unit geometry of a single-structure problem, passed by value so that the persistent
+// GEMM derives every tile's coordinates without table loads.
+struct UniformUnits {
+  int on;  // 1 when the problem has one structure
+  int N, F, nkc;
+  int64_t P, nptile, nntile;
+};
+
 struct SuperposeArgs {
   int n_struct, n_freq, n_ports;
   const int32_t* port_off;
@@ -88,6 +96,7 @@ struct SuperposeArgs {
   int npieces;
   void* B_out;
   int32_t* err;  // device error word (bounded-wait timeouts)
+  UniformUnits uni;
 };
 
 cudaError_t launch_superpose(const SuperposeArgs& a, mts_precision prec, cudaStream_t st);

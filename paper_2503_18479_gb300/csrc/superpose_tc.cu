@@ -74,7 +74,9 @@ __device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity, int32_t* err, i
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   while (true) {
-    if (mbar_try_wait(bar, parity)) return true;
+#pragma unroll 1
+    for (int i = 0; i < 256; ++i)  // the timer is read once per 256 polls
+      if (mbar_try_wait(bar, parity)) return true;
     if (global_ns() - t0 > kWaitNs) {
       atomicCAS(err, 0, code);
       return false;
@@ -159,6 +161,18 @@ struct Unit {
 
 __device__ inline Unit unit_info(const SuperposeArgs& a, int64_t u) {
   Unit x;
+  if (a.uni.on) {  // one structure: geometry from the arguments, no table loads
+    x.s = 0;
+    x.N = a.uni.N;
+    x.F = a.uni.F;
+    x.P = a.uni.P;
+    x.nkc = a.uni.nkc;
+    x.nptile = a.uni.nptile;
+    x.nntile = a.uni.nntile;
+    x.pt = u % x.nptile;
+    x.nt = u / x.nptile;
+    return x;
+  }
   x.s = find_struct_i64(a.unit_off, a.n_struct, u);
   x.N = a.port_off[x.s + 1] - a.port_off[x.s];
   x.F = a.freq_off[x.s + 1] - a.freq_off[x.s];
@@ -236,8 +250,10 @@ __global__ void __launch_bounds__(kThreads, 1) superpose_tc_kernel(SuperposeArgs
       }
       for (int64_t u = u_begin; u < u_end && ok; ++u) {
         Unit x = unit_info(a, u);
-        const unsigned char* Ab = reinterpret_cast<const unsigned char*>(a.Aop + a.t.aop_off[x.s]);
-        const unsigned char* Bb = reinterpret_cast<const unsigned char*>(a.Bop + a.bop_off[x.s]);
+        const unsigned char* Ab =
+            reinterpret_cast<const unsigned char*>(a.Aop + (a.uni.on ? 0 : a.t.aop_off[x.s]));
+        const unsigned char* Bb =
+            reinterpret_cast<const unsigned char*>(a.Bop + (a.uni.on ? 0 : a.bop_off[x.s]));
         for (int kc = 0; kc < x.nkc && ok; ++kc) {
           if (!mbar_wait(&empty[stage], phase ^ 1u, err, 1)) {
             ok = false;
@@ -345,19 +361,30 @@ __global__ void __launch_bounds__(kThreads, 1) superpose_tc_kernel(SuperposeArgs
       const int64_t p = x.pt * kTileP + quarter * 32 + lane;
       if (p < x.P) {
         const int64_t nsys = a.n_cfg * x.F;
-        int64_t sys0 = x.nt * (kTileN / 2);
-        int64_t b = sys0 / x.F;
-        int f = (int)(sys0 - b * x.F);
-        const int64_t fpo = a.t.fp_off[x.s];
+        const int64_t sys0 = x.nt * (kTileN / 2);
+        const int64_t fpo = a.uni.on ? 0 : a.t.fp_off[x.s];
+        if (x.F == 1 && sys0 + kTileN / 2 <= nsys) {
+          // full tile, one frequency: system i of the tile is row sys0 + i of the output
+          float2* dst = Bout + (sys0 * a.sumFP + fpo + p);
+          const int64_t stride = a.sumFP;
 #pragma unroll
-        for (int i = 0; i < kTileN / 2; ++i) {
-          if (sys0 + i < nsys) {
-            float2* dst = Bout + (b * a.sumFP + fpo + (int64_t)f * x.P + p);
+          for (int i = 0; i < kTileN / 2; ++i) {
             st_cs_f2(dst, v[2 * i], v[2 * i + 1]);
+            dst += stride;
           }
-          if (++f == x.F) {
-            f = 0;
-            ++b;
+        } else {
+          int64_t b = sys0 / x.F;
+          int f = (int)(sys0 - b * x.F);
+#pragma unroll
+          for (int i = 0; i < kTileN / 2; ++i) {
+            if (sys0 + i < nsys) {
+              float2* dst = Bout + (b * a.sumFP + fpo + (int64_t)f * x.P + p);
+              st_cs_f2(dst, v[2 * i], v[2 * i + 1]);
+            }
+            if (++f == x.F) {
+              f = 0;
+              ++b;
+            }
           }
         }
       }
