@@ -82,7 +82,6 @@ struct SmemV3 {
   float prow_im[2][NW][NM];    // imaginary parts
   float2 Wb[NB][8][8];         // inverses of the diagonal blocks of L (unit lower)
   float2 Vb[NB][8][8];         // and of U (upper)
-  float2 Ms[NM * NM];          // M = hi + lo of this system's structure, [j * N + r]
   ulonglong2 xhl[NM];          // x split: ((re_hi, im_hi), (re_lo, im_lo))
   double2 x64[NM];
   float2 Gs[NM];               // conj(G) of a chunk of loss points
@@ -149,6 +148,23 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
+// Objective term of one loss point in FP32 and its cotangent G = de/dRe b + j de/dIm b
+// (targets are read as FP64 and rounded).
+__device__ __forceinline__ float point_loss_f(int mode, float2 b, const double* t, float* gx, float* gy) {
+  if (mode == 0) {
+    const float a = sqrtf(b.x * b.x + b.y * b.y);
+    const float r = a - (float)t[0];
+    const float s = a > 0.0f ? 2.0f * r / a : 0.0f;
+    *gx = s * b.x;
+    *gy = s * b.y;
+    return r * r;
+  }
+  const float ex = b.x - (float)t[0], ey = b.y - (float)t[1];
+  *gx = 2.0f * ex;
+  *gy = 2.0f * ey;
+  return ex * ex + ey * ey;
+}
+
 // column j (a compile-time constant after unrolling) of a block stored as 4 real pairs and
 // 4 imaginary pairs
 __device__ __forceinline__ float2 elem(const u64* re4, const u64* im4, int j) {
@@ -167,7 +183,7 @@ __device__ __forceinline__ void set_elem(u64* re4, u64* im4, int j, float2 v) {
 }
 
 template <int NM>
-__global__ void __launch_bounds__(NM >= 64 ? NM : 128) solve_mixed_v3(SolveArgs a, int64_t n_sys) {
+__global__ void __launch_bounds__(NM >= 64 ? NM : 128, NM >= 64 ? 5 : 1) solve_mixed_v3(SolveArgs a, int64_t n_sys) {
   constexpr int NB = NM / 8;
   constexpr int CT = NM >= 64 ? NM : 128;
   constexpr int G = CT / NM;
@@ -186,11 +202,10 @@ __global__ void __launch_bounds__(NM >= 64 ? NM : 128) solve_mixed_v3(SolveArgs 
   const double Cr = real_row ? a.C[si.b * a.n_ports + si.k0 + r] : 1.0;
   cd Dr = {0.0, 0.0};
   if (real_row) Dr = {a.R[si.k0 + r], -1.0 / (w * Cr)};
-  {
-    const int64_t mo = a.t.nn_off[si.s];
-    for (int e = r; e < N * N; e += NM) sm.Ms[e] = make_float2(a.M32hi[mo + e], a.M32lo[mo + e]);
-  }
-  gsync<NM>();
+  // M = hi + lo of this structure, read through L1 (shared by every system of the structure)
+  const int64_t mo = a.t.nn_off[si.s];
+  const float* __restrict__ Mh = a.M32hi + mo;
+  const float* __restrict__ Ml = a.M32lo + mo;
 
   // ---- row r of A (FP32), identity rows for padding ----
   u64 ReP[NB][4], ImP[NB][4];
@@ -202,12 +217,12 @@ __global__ void __launch_bounds__(NM >= 64 ? NM : 128) solve_mixed_v3(SolveArgs 
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int c = 8 * b + 2 * m + h;
-        float mm = (real_row && c < N) ? w32 * sm.Ms[c * N + r].x : 0.0f;  // M symmetric
+        float mm = (real_row && c < N) ? w32 * __ldg(Mh + c * N + r) : 0.0f;  // M symmetric
         float re = 0.0f;
         if (c == r) {
           if (real_row) {
             re = (float)Dr.x;
-            mm = (float)(w * ((double)sm.Ms[r * N + r].x + (double)sm.Ms[r * N + r].y) + Dr.y);
+            mm = (float)(w * ((double)__ldg(Mh + r * N + r) + (double)__ldg(Ml + r * N + r)) + Dr.y);
           } else {
             re = 1.0f;
           }
@@ -469,7 +484,7 @@ __global__ void __launch_bounds__(NM >= 64 ? NM : 128) solve_mixed_v3(SolveArgs 
       for (int h = 0; h < 2; ++h) {
         const int j = j0 + h;
         if (j < N) {
-          const float2 m = sm.Ms[j * N + r];
+          const float2 m = make_float2(__ldg(Mh + j * N + r), __ldg(Ml + j * N + r));
           const ulonglong2 xj = sm.xhl[j];
           const u64 A = pk(m.x, m.x), Al = pk(m.y, m.y);
           const u64 p = fmul2(A, xj.x);
@@ -498,13 +513,13 @@ __global__ void __launch_bounds__(NM >= 64 ? NM : 128) solve_mixed_v3(SolveArgs 
     u64 S0 = 0ull, S1 = 0ull;
     int j = 0;
     for (; j + 1 < N; j += 2) {
-      const float m0 = sm.Ms[j * N + r].x, m1 = sm.Ms[(j + 1) * N + r].x;
+      const float m0 = __ldg(Mh + j * N + r), m1 = __ldg(Mh + (j + 1) * N + r);
       const float2 d0 = sm.xs[j], d1 = sm.xs[j + 1];
       S0 = ffma2(pk(m0, m0), pk(d0.x, d0.y), S0);
       S1 = ffma2(pk(m1, m1), pk(d1.x, d1.y), S1);
     }
     if (j < N) {
-      const float m0 = sm.Ms[j * N + r].x;
+      const float m0 = __ldg(Mh + j * N + r);
       const float2 d0 = sm.xs[j];
       S0 = ffma2(pk(m0, m0), pk(d0.x, d0.y), S0);
     }
@@ -602,10 +617,15 @@ __global__ void __launch_bounds__(NM >= 64 ? NM : 128) solve_mixed_v3(SolveArgs 
             const int64_t n = 2 * (si.b * F + si.f) + c;
             const int64_t tile = n / kTileN;
             const uint32_t rr = (uint32_t)(n % kTileN);
-            double remd = own ? (c == 0 ? x.x : x.y) : 0.0;
+            // x = xh + xl (FP32 pair); pieces p_q = bf16(rem), rem -= p_q in FP32 (exact
+            // apart from the final rounding of rem + xl, 2^-32 relative)
+            const double xv = own ? (c == 0 ? x.x : x.y) : 0.0;
+            const float xh = (float)xv, xl = (float)(xv - (double)xh);
+            float rem = xh;
             for (int q = 0; q < a.npieces; ++q) {
-              __nv_bfloat16 h = __float2bfloat16_rn((float)remd);
-              remd -= (double)__bfloat162float(h);
+              const __nv_bfloat16 h = __float2bfloat16_rn(rem);
+              rem = rem - __bfloat162float(h);
+              if (q == 0) rem += xl;
               size_t off = ((size_t)(q * ntile + tile) * nkc + kc) * tile_bytes + swz128(rr, kc_k);
               *reinterpret_cast<__nv_bfloat16*>(base + off) = h;
             }
@@ -638,7 +658,9 @@ __global__ void __launch_bounds__(NM >= 64 ? NM : 128) solve_mixed_v3(SolveArgs 
               b0 = ffma2(pk(h0, h0), sm.xhl[k].x, b0);
             }
             const float2 bl = make_float2(up(b0).x + up(b1).x, up(b0).y + up(b1).y);
-            lsum += point_loss(a.loss_mode, cd{(double)bl.x, (double)bl.y}, tb + (int64_t)l * tw, &Gl);
+            float gx, gy;
+            lsum += (double)point_loss_f(a.loss_mode, bl, tb + (int64_t)l * tw, &gx, &gy);
+            Gl = {(double)gx, (double)gy};
           }
           sm.Gs[r] = make_float2((float)Gl.x, -(float)Gl.y);  // conj(G)
           gsync<NM>();
