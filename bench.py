@@ -68,6 +68,22 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest x over all ranks (all_reduce MAX; no-op for one rank)."""
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    if world > 1:
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(n_cfg_per_rank: int, steps: int, world: int, max_ms: float) -> float:
+    """Configurations per second of the whole job: every rank's batches over the slowest
+    rank's time (weak scaling: each rank owns n_cfg_per_rank configurations)."""
+    return world * n_cfg_per_rank * steps / (max_ms / 1e3)
+
+
 # ---------------------------------------------------------------------------------------
 # clocks sampled during the timed region
 # ---------------------------------------------------------------------------------------
@@ -207,11 +223,8 @@ def run_ours(args, rank, world, local):
     gemm_ms = sum(e[1].elapsed_time(e[2]) for e in evs) / K
     solve_ms = sum(e[0].elapsed_time(e[1]) for e in evs) / K
     bwd_ms = sum(e[2].elapsed_time(e[3]) for e in evs) / K
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-    max_ms = float(t.item())
-    value = world * n_cfg * K / (max_ms / 1e3)
+    max_ms = max_over_ranks(total_ms, world, dev)
+    value = whole_job_value(n_cfg, K, world, max_ms)
 
     # ---- end to end through the public API, host buffers, copies inside the timed region
     Ch = torch.from_numpy(wl.C).pin_memory()
@@ -241,10 +254,7 @@ def run_ours(args, rank, world, local):
         a1.record(st)
         a1.synchronize()  # the host reads the result
         e2e_ms += a0.elapsed_time(a1)
-    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        tdist.all_reduce(te, op=tdist.ReduceOp.MAX)
-    e2e_value = world * n_cfg * KE / (float(te.item()) / 1e3)
+    e2e_value = whole_job_value(n_cfg, KE, world, max_over_ranks(e2e_ms, world, dev))
 
     # ---- roofline of the dominant kernel (superposition): algorithmic bytes per launch
     P = wl.n_points

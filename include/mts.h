@@ -87,7 +87,9 @@ typedef enum {
  * when L_self is NULL, need every segment pair to be parallel or perpendicular
  * (rectilinear loops); other pairs give MTS_EUNSUPPORTED from mts_basis_status.
  * Offset tables are given twice, identical: host copies (h_*) plan launches, device
- * copies are read by the kernels. Limits: 1 <= ports per structure <= 128.
+ * copies are read by the kernels. Limits: 1 <= ports per structure <= 1024 (more give
+ * MTS_EUNSUPPORTED from every entry point, before any launch). Systems of up to 64 ports
+ * are solved in registers; larger ones by a blocked LU whose factors live in the tape.
  */
 typedef struct mts_problem {
   int32_t n_struct;
@@ -178,7 +180,9 @@ mts_status mts_basis_status(const mts_problem* pb, mts_precision prec, const voi
 /* ---------------------------------------------------------------------------------
  * Tape: the per-call state written by the forward calls and read by mts_backward
  * (currents I, tensor-core operand copies of I, per-system objective and gradient
- * partials, per-system status, backward scratch). Device buffer of
+ * partials, per-system status, backward scratch, and the LU factors of systems with more
+ * than 64 ports: 8 bytes (16 for MTS_FP64) per matrix element, per configuration and
+ * frequency of such a structure). Device buffer of
  * mts_tape_bytes(...) bytes, 256-byte aligned.
  * --------------------------------------------------------------------------------- */
 size_t mts_tape_bytes(const mts_problem* pb, int64_t n_cfg, mts_precision prec);

@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libmts.so")
-SOURCES = ["abi.cu", "basis.cu", "solve.cu", "solve_mixed.cu", "superpose.cu", "superpose_tc.cu", "backward.cu",
+SOURCES = ["abi.cu", "basis.cu", "solve.cu", "solve_mixed.cu", "solve_large.cu", "superpose.cu", "superpose_tc.cu",
+           "backward.cu",
            "static_solve.cu"]
 HEADERS = ["common.cuh", "kernels.h", "solve_common.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

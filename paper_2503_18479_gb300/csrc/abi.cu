@@ -14,8 +14,6 @@ namespace mts {
 static std::atomic<uint64_t> g_launches{0};
 void note_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 
-constexpr int kSolveMaxPorts = 64;  // largest system size the solve kernels handle today
-
 ProblemSums problem_sums(const mts_problem* pb, mts_precision prec) {
   ProblemSums ps;
   ps.n_struct = pb->n_struct;
@@ -26,6 +24,8 @@ ProblemSums problem_sums(const mts_problem* pb, mts_precision prec) {
     int64_t F = pb->h_freq_off[s + 1] - pb->h_freq_off[s];
     int64_t L = pb->h_loss_off ? pb->h_loss_off[s + 1] - pb->h_loss_off[s] : 0;
     if (N > ps.max_ports) ps.max_ports = (int)N;
+    if (s == 0 || N < ps.min_ports) ps.min_ports = (int)N;
+    if (N > kRegMaxPorts) ps.sumLU += F * N * N;
     ps.sumNN += N * N;
     ps.sumPN += P * N;
     ps.sumLN += L * N;
@@ -78,7 +78,8 @@ PlanLayout plan_layout(int n_struct) {
   size_t arr = align256(sizeof(int64_t) * (size_t)(n_struct + 1));
   p.bop_off = 0;
   p.unit_off = arr;
-  p.bytes = 2 * arr;
+  p.lu_off = 2 * arr;
+  p.bytes = 3 * arr;
   return p;
 }
 
@@ -114,6 +115,7 @@ TapeLayout tape_layout(const mts_problem* pb, int64_t n_cfg, mts_precision prec)
   t.plan = o; o += plan_layout(pb->n_struct).bytes;
   t.err = o; o += 256;
   t.Bop = o; o += align256(2 * (size_t)bop_elems(pb, n_cfg, n_pieces(prec), nullptr));
+  t.lu = o; o += align256((prec == MTS_FP64 ? 16 : 8) * nc * (size_t)ps.sumLU);
   t.total = o;
   return t;
 }
@@ -218,6 +220,8 @@ static SolveArgs solve_args(const mts_problem* pb, mts_precision prec, const voi
   a.npieces = n_pieces(prec);
   a.Bop = a.npieces ? reinterpret_cast<__nv_bfloat16*>(T + tl.Bop) : nullptr;
   a.bop_off = reinterpret_cast<const int64_t*>(T + tl.plan + pl.bop_off);
+  a.lu_off = reinterpret_cast<const int64_t*>(T + tl.plan + pl.lu_off);
+  a.lu = T + tl.lu;
   a.max_loss = max_loss_points(pb);
   a.rhs_in = nullptr;
   return a;
@@ -323,8 +327,6 @@ static mts_status check_solve_args(const mts_problem* pb, mts_precision prec, co
   v = validate_eval(pb, ev);
   if (v != MTS_OK) return v;
   if (tape_bytes < tape_layout(pb, ev->n_cfg, prec).total) return MTS_EWORKSPACE;
-  ProblemSums ps = problem_sums(pb, prec);
-  if (ps.max_ports > kSolveMaxPorts) return MTS_EUNSUPPORTED;
   return MTS_OK;
 }
 
@@ -342,11 +344,12 @@ mts_status mts_solve(const mts_problem* pb, mts_precision prec, const void* basi
   cudaError_t e = cudaMemsetAsync(T + tl.err, 0, 16, st);
   if (e == cudaSuccess)
     e = launch_plan(pb, ev->n_cfg, n_pieces(prec), reinterpret_cast<int64_t*>(T + tl.plan + pl.bop_off),
-                    reinterpret_cast<int64_t*>(T + tl.plan + pl.unit_off), st);
+                    reinterpret_cast<int64_t*>(T + tl.plan + pl.unit_off),
+                    reinterpret_cast<int64_t*>(T + tl.plan + pl.lu_off), st);
   if (e != cudaSuccess) return MTS_ECUDA;
   SolveArgs a = solve_args(pb, prec, basis, ev, tape, ps);
   a.I_out = I_out;
-  e = launch_solve(a, prec, ps.max_ports, st);
+  e = launch_solve(a, prec, ps.min_ports, ps.max_ports, st);
   if (e == cudaErrorNotSupported) return MTS_EUNSUPPORTED;
   if (e != cudaSuccess) return MTS_ECUDA;
   if (ev->target) {
@@ -448,7 +451,7 @@ mts_status mts_backward(const mts_problem* pb, mts_precision prec, const void* b
     a.rhs_in = reinterpret_cast<const double*>(T + tl.mu);
     a.Bop = nullptr;
     a.target = nullptr;
-    e = launch_solve(a, prec, ps.max_ports, st);
+    e = launch_solve(a, prec, ps.min_ports, ps.max_ports, st);
     if (e == cudaErrorNotSupported) return MTS_EUNSUPPORTED;
     if (e != cudaSuccess) return MTS_ECUDA;
     ReduceArgs r = reduce_args(pb, prec, basis, ev, tape, ps);

@@ -14,8 +14,9 @@ namespace mts {
 constexpr int kFaSys = 8;     // systems per CTA (share the H reads)
 constexpr int kFaChunk = 128; // points per staged chunk
 
-// CTA = 128 threads (one per port k, N <= 128), kFaSys configurations of one frequency g.
-// Inner sums over a chunk of points in the working precision, outer sums in FP64.
+// CTA = 128 threads (one per port k of the CTA's 128-port slice, blockIdx.z), kFaSys
+// configurations of one frequency g. Inner sums over a chunk of points in the working
+// precision, outer sums in FP64.
 template <typename HT, typename GT>
 __global__ void __launch_bounds__(128) field_adjoint_kernel(FieldAdjArgs a) {
   __shared__ GT sg[kFaSys][kFaChunk];
@@ -24,8 +25,9 @@ __global__ void __launch_bounds__(128) field_adjoint_kernel(FieldAdjArgs a) {
   const int s = a.t.freq_struct[g];
   const int f = g - a.freq_off[s];
   const int N = a.port_off[s + 1] - a.port_off[s];
+  if ((int)blockIdx.z * 128 >= N) return;  // slice beyond this structure's ports (CTA-uniform)
   const int64_t P = a.point_off[s + 1] - a.point_off[s];
-  const int k = threadIdx.x;
+  const int k = (int)blockIdx.z * 128 + threadIdx.x;
   const HT* H = static_cast<const HT*>(a.H) + a.t.pn_off[s];
   const GT* gB = static_cast<const GT*>(a.grad_B);
   double accx[kFaSys], accy[kFaSys];
@@ -78,8 +80,9 @@ __global__ void __launch_bounds__(128) field_adjoint_kernel(FieldAdjArgs a) {
 
 cudaError_t launch_field_adjoint_rhs(const FieldAdjArgs& a, mts_precision prec, int max_ports,
                                      cudaStream_t st) {
-  if (max_ports > 128) return cudaErrorNotSupported;
-  dim3 grid((unsigned)a.n_freq, (unsigned)((a.n_cfg + kFaSys - 1) / kFaSys));
+  if (max_ports > kMaxPorts) return cudaErrorNotSupported;
+  dim3 grid((unsigned)a.n_freq, (unsigned)((a.n_cfg + kFaSys - 1) / kFaSys),
+            (unsigned)((max_ports + 127) / 128));
   if (prec == MTS_FP64)
     field_adjoint_kernel<double, double2><<<grid, 128, 0, st>>>(a);
   else

@@ -23,10 +23,12 @@
 //   status     int32 [n_cfg][n_freq]            0 ok, 1 not converged, 2 non-finite
 //   mu         FP64 complex [n_cfg][sum F N]    backward scratch (u = H^T conj(grad_B))
 //   gfield     FP64 [n_cfg][n_ports]            field-cotangent part of the gradient
-//   plan       int64 per-call tables (B-operand bases, GEMM unit prefixes)
+//   plan       int64 per-call tables (B-operand bases, GEMM unit prefixes, factor bases)
 //   err        int32 [4]: [0] bounded-wait timeout code, [1] count of bad systems
 //   Bop        bf16 tensor-core operand of I, per structure
 //              [piece][n_tile][k_chunk][128 rows x 64 k], row = 2 (b F_s + f) + c
+//   lu         complex FP32 (FP64 for MTS_FP64) [n_cfg][sum_{N_s > 64} F_s N_s^2]: LU
+//              factors of the systems too large for the register-resident solve
 #pragma once
 #include <cstddef>
 #include <cstdint>
@@ -39,7 +41,8 @@ namespace mts {
 constexpr int kTileP = 128;   // GEMM rows (points) per tile = TMEM lanes
 constexpr int kTileN = 128;   // GEMM columns ((cfg, freq, re/im)) per tile
 constexpr int kChunkK = 64;   // K elements per 128-byte swizzle atom (16-bit types)
-constexpr int kMaxPorts = 128;
+constexpr int kMaxPorts = 1024;    // largest structure (ports) the library accepts
+constexpr int kRegMaxPorts = 64;   // largest system the register-resident solve kernels hold
 
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 inline size_t align256(size_t a) { return (a + 255) / 256 * 256; }
@@ -50,6 +53,8 @@ inline int n_pieces(mts_precision p) { return p == MTS_MIXED ? 3 : (p == MTS_BF1
 struct ProblemSums {
   int n_struct = 0;
   int max_ports = 0;
+  int min_ports = 0;
+  int64_t sumLU = 0;  // sum over structures with N_s > kRegMaxPorts of F_s N_s^2 (factor scratch)
   int64_t sumNN = 0, sumPN = 0, sumLN = 0, sumFN = 0, sumFP = 0, sumFL = 0;
   int64_t sumAop = 0;  // bf16 elements per piece-set of the H operand (all pieces)
 };
@@ -68,12 +73,12 @@ struct TableLayout {
 
 struct TapeLayout {
   size_t I = 0, loss_part = 0, grad_part = 0, dldc = 0, lossv = 0, status = 0, mu = 0,
-         gfield = 0, plan = 0, err = 0, Bop = 0, total = 0;
+         gfield = 0, plan = 0, err = 0, Bop = 0, lu = 0, total = 0;
 };
 
 // Per-call plan tables inside the tape (arrays of n_struct+1 int64).
 struct PlanLayout {
-  size_t bop_off, unit_off, bytes;
+  size_t bop_off, unit_off, lu_off, bytes;
 };
 
 ProblemSums problem_sums(const mts_problem* pb, mts_precision prec);

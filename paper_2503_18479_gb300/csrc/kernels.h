@@ -37,6 +37,9 @@ struct SolveArgs {
   int32_t* status;    // [n_cfg][n_freq]
   __nv_bfloat16* Bop;      // tensor-core operand of I (nullptr for FP64)
   const int64_t* bop_off;  // per-structure element base of Bop (plan table)
+  const int64_t* lu_off;   // per-structure element base of the factor scratch (plan table;
+                           // [n_struct] = elements per configuration)
+  void* lu;                // factor scratch of the large-system kernel
   int npieces;
   int max_loss;  // max loss points of one structure (uniform trip count for group loops)
   // backward (field cotangent) mode: solve A mu = rhs_in and write grad terms only
@@ -66,9 +69,15 @@ cudaError_t launch_export_basis(const mts_problem* pb, mts_precision prec, const
 
 // Per-call plan tables in the tape (bases of the B operand, GEMM unit prefixes).
 cudaError_t launch_plan(const mts_problem* pb, int64_t n_cfg, int npieces, int64_t* bop_off,
-                        int64_t* unit_off, cudaStream_t st);
+                        int64_t* unit_off, int64_t* lu_off, cudaStream_t st);
 
-cudaError_t launch_solve(const SolveArgs& a, mts_precision prec, int max_ports, cudaStream_t st);
+// Solve of every system: the register-resident kernels for N <= kRegMaxPorts, the blocked
+// large-system kernel (solve_large.cu) for the others.
+cudaError_t launch_solve(const SolveArgs& a, mts_precision prec, int min_ports, int max_ports,
+                         cudaStream_t st);
+size_t large_solve_smem(mts_precision prec, int max_ports);
+cudaError_t launch_solve_large(const SolveArgs& a, mts_precision prec, int64_t n_sys,
+                               int min_ports, int max_ports, void* scratch, cudaStream_t st);
 cudaError_t launch_reduce(const ReduceArgs& a, cudaStream_t st);
 
 // Unit geometry of a single-structure problem, passed by value so that the persistent

@@ -49,8 +49,10 @@ __global__ void __launch_bounds__(NM >= 128 ? NM : 128) solve_fp64_kernel(SolveA
   int* redi = reinterpret_cast<int*>(red + 32);
 
   int64_t sys = (int64_t)blockIdx.x * G + grp;
-  const bool valid = sys < n_sys;
-  SysInfo si = sys_info(a, valid ? sys : 0);
+  const bool in_range = sys < n_sys;
+  SysInfo si = sys_info(a, in_range ? sys : 0);
+  const bool valid = in_range && si.N <= NM;  // larger systems: solve_large.cu
+  if (!valid) si.N = 0;
   const int N = si.N;
   const double w = si.w;
   const bool real_row = r < N;
@@ -273,17 +275,28 @@ static cudaError_t launch_fp64(const SolveArgs& a, int64_t n_sys, cudaStream_t s
 
 cudaError_t launch_solve_mixed(const SolveArgs& a, int64_t n_sys, int max_ports, cudaStream_t st);
 
-cudaError_t launch_solve(const SolveArgs& a, mts_precision prec, int max_ports, cudaStream_t st) {
+cudaError_t launch_solve(const SolveArgs& a, mts_precision prec, int min_ports, int max_ports,
+                         cudaStream_t st) {
   int64_t n_sys = a.n_cfg * a.n_freq;
   if (n_sys == 0) return cudaSuccess;
-  if (prec == MTS_FP64) {
-    if (max_ports <= 8) return launch_fp64<8>(a, n_sys, st);
-    if (max_ports <= 16) return launch_fp64<16>(a, n_sys, st);
-    if (max_ports <= 32) return launch_fp64<32>(a, n_sys, st);
-    if (max_ports <= 64) return launch_fp64<64>(a, n_sys, st);
-    return cudaErrorNotSupported;
+  cudaError_t e = cudaSuccess;
+  if (min_ports <= kRegMaxPorts) {  // some structure fits the register-resident kernels
+    const int m = max_ports < kRegMaxPorts ? max_ports : kRegMaxPorts;
+    if (prec == MTS_FP64) {
+      if (m <= 8) e = launch_fp64<8>(a, n_sys, st);
+      else if (m <= 16) e = launch_fp64<16>(a, n_sys, st);
+      else if (m <= 32) e = launch_fp64<32>(a, n_sys, st);
+      else e = launch_fp64<64>(a, n_sys, st);
+    } else {
+      e = launch_solve_mixed(a, n_sys, m, st);
+    }
+    if (e != cudaSuccess) return e;
   }
-  return launch_solve_mixed(a, n_sys, max_ports, st);
+  if (max_ports > kRegMaxPorts) {
+    if (max_ports > kMaxPorts) return cudaErrorNotSupported;
+    e = launch_solve_large(a, prec, n_sys, kRegMaxPorts, max_ports, a.lu, st);
+  }
+  return e;
 }
 
 cudaError_t launch_reduce(const ReduceArgs& a, cudaStream_t st) {

@@ -1,0 +1,543 @@
+// solve_large.cu -- (b) port solve, (d) objective and (adj) adjoint for structures with more
+// ports than the register-resident kernels hold (64 < N <= 1024).
+//
+// One system (configuration b, frequency g) per 256-thread CTA. The matrix
+// A = diag(R) + j w M + diag(1/(j w C)) (paper Eq. 2, 11) is assembled into the tape's
+// factor scratch (global memory) and factorised there by a blocked right-looking LU with
+// partial pivoting, without moving rows (the pivot of column k is the largest |a_rk| among
+// rows not chosen yet; chosen rows keep U in place, the others keep their multipliers):
+//   panel   the NB columns [c0, c0+NB) of every row, staged column-major in shared memory,
+//           factorised step by step (block arg-max per step);
+//   U12     the NB pivot rows of the panel over the trailing columns: a unit-lower
+//           triangular solve against the panel's multipliers;
+//   update  every row not chosen yet: A[r][j] -= sum_m L[r][m] U12[m][j], thread per
+//           column j of a CW-column chunk with U12[.][j] in registers (coalesced rows).
+// Triangular solves run panel by panel: a warp solves the panel's NB x NB triangle, then
+// the other rows take the panel's contribution (thread per row).
+//
+//   R = double: FP64 factors and one solve (MTS_FP64, NB = 8).
+//   R = float : FP32 factors (NB = 16) and iterative refinement on FP64 residuals
+//               rhs - A x, stopped by the same predictive estimate as the small systems.
+// The objective at the loss points, the adjoint solve with the same matrix (A^T = A) and
+// dloss/dC_k = Im(mu_k I_k)/(w C_k^2) (Eq. 8-9) are as in solve.cu.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "solve_common.cuh"
+
+namespace mts {
+
+constexpr int kLargeThreads = 256;
+constexpr int kLargeWarps = kLargeThreads / 32;
+
+template <typename R>
+struct Cx {
+  R x, y;
+};
+template <typename R>
+__device__ inline Cx<R> cx_div(Cx<R> a, Cx<R> b) {
+  const R d = b.x * b.x + b.y * b.y;
+  return {(a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d};
+}
+// v -= l * u
+template <typename R>
+__device__ inline void cx_fnma(Cx<R>& v, Cx<R> l, Cx<R> u) {
+  v.x = fma(-l.x, u.x, fma(l.y, u.y, v.x));
+  v.y = fma(-l.x, u.y, fma(-l.y, u.x, v.y));
+}
+
+template <typename R>
+struct LargeCfg;
+template <>
+struct LargeCfg<float> {
+  static constexpr int NB = 16, CW = 128;
+};
+template <>
+struct LargeCfg<double> {
+  static constexpr int NB = 8, CW = 64;
+};
+
+struct BlockRed {
+  double key[kLargeWarps];
+  int idx[kLargeWarps];
+};
+
+// Shared-memory carve-up for systems of up to n ports (host and device agree on it).
+template <typename R>
+struct LargeSmem {
+  static constexpr int NB = LargeCfg<R>::NB, CW = LargeCfg<R>::CW;
+  size_t pan, u12, wv, piv, ord, rhs, sv, xk, xc, red, pvec, bytes;
+  __host__ __device__ explicit LargeSmem(int n) {
+    const size_t cx = sizeof(Cx<R>);
+    size_t o = 0;
+    pan = o; o += cx * (size_t)NB * (n + 1);  // panel, column-major, pitch n + 1
+    u12 = o; o += cx * (size_t)NB * CW;       // U12 chunk
+    wv = o; o += cx * (size_t)n;              // triangular-solve vector (by row)
+    piv = o; o += sizeof(int) * (size_t)n;    // step at which a row became the pivot
+    ord = o; o += sizeof(int) * (size_t)n;    // pivot row of each step
+    o = (o + 15) / 16 * 16;
+    rhs = o; o += sizeof(cd) * (size_t)n;     // FP64 right-hand side / residual
+    sv = o; o += sizeof(cd) * (size_t)n;      // FP64 saved right-hand side
+    xk = o; o += sizeof(cd) * (size_t)n;      // FP64 iterate
+    xc = o; o += sizeof(cd) * (size_t)n;      // FP64 currents I
+    red = o; o += sizeof(BlockRed);
+    o = (o + 15) / 16 * 16;
+    pvec = o; o += cx * NB;                   // panel part of y or x
+    bytes = o;
+  }
+};
+
+// block-wide arg-max of (key, idx), ties to the smaller index; every thread gets idx.
+__device__ inline int block_argmax(double key, int idx, BlockRed* red) {
+  argmax_shfl_d(key, idx, 32);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    red->key[threadIdx.x >> 5] = key;
+    red->idx[threadIdx.x >> 5] = idx;
+  }
+  __syncthreads();
+  double kb = red->key[0];
+  int ib = red->idx[0];
+#pragma unroll
+  for (int q = 1; q < kLargeWarps; ++q)
+    if (red->key[q] > kb || (red->key[q] == kb && red->idx[q] < ib)) {
+      kb = red->key[q];
+      ib = red->idx[q];
+    }
+  return ib;
+}
+
+__device__ inline double block_max(double v, BlockRed* red) {
+  for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red->key[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double m = red->key[0];
+#pragma unroll
+  for (int q = 1; q < kLargeWarps; ++q) m = fmax(m, red->key[q]);
+  return m;
+}
+
+__device__ inline double block_sum(double v, BlockRed* red) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red->key[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+#pragma unroll
+  for (int q = 0; q < kLargeWarps; ++q) s += red->key[q];
+  return s;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kLargeThreads) solve_large_kernel(SolveArgs a, int64_t n_sys,
+                                                                     int min_ports, int smem_n,
+                                                                     Cx<R>* __restrict__ scratch) {
+  constexpr int NB = LargeCfg<R>::NB, CW = LargeCfg<R>::CW;
+  constexpr int RG = kLargeThreads / CW;  // row groups of the trailing update
+  const int64_t sys = blockIdx.x;
+  if (sys >= n_sys) return;
+  const SysInfo si = sys_info(a, sys);
+  const int N = si.N;
+  if (N <= min_ports) return;  // a register-resident kernel owns this system (CTA-uniform)
+
+  extern __shared__ __align__(16) unsigned char dsm[];
+  const LargeSmem<R> L(smem_n);
+  Cx<R>* pan = reinterpret_cast<Cx<R>*>(dsm + L.pan);
+  Cx<R>* u12 = reinterpret_cast<Cx<R>*>(dsm + L.u12);
+  Cx<R>* wv = reinterpret_cast<Cx<R>*>(dsm + L.wv);
+  int* pivstep = reinterpret_cast<int*>(dsm + L.piv);
+  int* order = reinterpret_cast<int*>(dsm + L.ord);
+  cd* rhs = reinterpret_cast<cd*>(dsm + L.rhs);
+  cd* sv = reinterpret_cast<cd*>(dsm + L.sv);
+  cd* xk = reinterpret_cast<cd*>(dsm + L.xk);
+  cd* xc = reinterpret_cast<cd*>(dsm + L.xc);
+  BlockRed* red = reinterpret_cast<BlockRed*>(dsm + L.red);
+  Cx<R>* pvec = reinterpret_cast<Cx<R>*>(dsm + L.pvec);
+  const int NP = N + 1;  // panel pitch
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double w = si.w;
+  const bool bwd = a.rhs_in != nullptr;
+  const double* __restrict__ M = a.M64 + a.t.nn_off[si.s];
+  const double* __restrict__ Cb = a.C + si.b * a.n_ports + si.k0;
+  const double* __restrict__ Rk = a.R + si.k0;
+  const int F = a.freq_off[si.s + 1] - a.freq_off[si.s];
+  Cx<R>* A = scratch + si.b * a.lu_off[a.n_struct] + a.lu_off[si.s] + (int64_t)si.f * N * N;
+
+  // ---- assemble A (Eq. 2, 11) ----
+  for (int r = 0; r < N; ++r)
+    for (int j = tid; j < N; j += kLargeThreads) {
+      double im = w * M[(int64_t)r * N + j], re = 0.0;
+      if (j == r) {
+        re = Rk[r];
+        im -= 1.0 / (w * Cb[r]);
+      }
+      A[(int64_t)r * N + j] = {(R)re, (R)im};
+    }
+  for (int r = tid; r < N; r += kLargeThreads) pivstep[r] = N;
+  __syncthreads();
+
+  // ---- blocked LU with partial pivoting ----
+  for (int c0 = 0; c0 < N; c0 += NB) {
+    const int nb = min(NB, N - c0);
+    for (int e = tid; e < N * NB; e += kLargeThreads) {
+      const int r = e / NB, j = e - r * NB;
+      Cx<R> v = {0, 0};
+      if (j < nb && pivstep[r] == N) v = A[(int64_t)r * N + c0 + j];
+      pan[j * NP + r] = v;
+    }
+    __syncthreads();
+    for (int kk = 0; kk < nb; ++kk) {
+      double best = -1.0;
+      int bi = N;
+      for (int r = tid; r < N; r += kLargeThreads)
+        if (pivstep[r] == N) {
+          const Cx<R> v = pan[kk * NP + r];
+          double m = (double)v.x * v.x + (double)v.y * v.y;
+          if (!(m >= 0.0)) m = 0.0;  // NaN: still a candidate, so a row is always chosen
+          if (m > best) {
+            best = m;
+            bi = r;
+          }
+        }
+      const int p = block_argmax(best, bi, red);
+      const Cx<R> piv = pan[kk * NP + p];
+      for (int r = tid; r < N; r += kLargeThreads)
+        if (pivstep[r] == N && r != p) {
+          const Cx<R> l = cx_div(pan[kk * NP + r], piv);
+          pan[kk * NP + r] = l;
+          for (int j = kk + 1; j < nb; ++j) cx_fnma(pan[j * NP + r], l, pan[j * NP + p]);
+        }
+      __syncthreads();
+      if (tid == 0) {
+        pivstep[p] = c0 + kk;
+        order[c0 + kk] = p;
+      }
+      __syncthreads();
+    }
+    // panel back to the matrix (rows chosen in this panel or later)
+    for (int e = tid; e < N * NB; e += kLargeThreads) {
+      const int r = e / NB, j = e - r * NB;
+      if (j < nb && pivstep[r] >= c0) A[(int64_t)r * N + c0 + j] = pan[j * NP + r];
+    }
+    __syncthreads();
+    // trailing columns, CW at a time
+    for (int j0 = c0 + nb; j0 < N; j0 += CW) {
+      if (tid < CW) {
+        const int j = j0 + tid;
+        Cx<R> uu[NB];
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+          Cx<R> v = {0, 0};
+          if (i < nb && j < N) {
+            const int pi = order[c0 + i];
+            v = A[(int64_t)pi * N + j];
+#pragma unroll
+            for (int m = 0; m < i; ++m) cx_fnma(v, pan[m * NP + pi], uu[m]);
+            A[(int64_t)pi * N + j] = v;
+          }
+          uu[i] = v;
+          u12[i * CW + tid] = v;
+        }
+      }
+      __syncthreads();
+      {
+        const int col = tid % CW, rg = tid / CW;
+        const int j = j0 + col;
+        Cx<R> uu[NB];
+#pragma unroll
+        for (int m = 0; m < NB; ++m) uu[m] = u12[m * CW + col];
+        if (j < N) {
+          int r = rg;
+          for (; r + 3 * RG < N; r += 4 * RG) {  // four rows in flight
+            bool act[4];
+            Cx<R> v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              act[q] = pivstep[r + q * RG] == N;
+              v[q] = act[q] ? A[(int64_t)(r + q * RG) * N + j] : Cx<R>{0, 0};
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (act[q]) {
+#pragma unroll
+                for (int m = 0; m < NB; ++m) cx_fnma(v[q], pan[m * NP + r + q * RG], uu[m]);
+                A[(int64_t)(r + q * RG) * N + j] = v[q];
+              }
+          }
+          for (; r < N; r += RG)
+            if (pivstep[r] == N) {
+              Cx<R> v = A[(int64_t)r * N + j];
+#pragma unroll
+              for (int m = 0; m < NB; ++m) cx_fnma(v, pan[m * NP + r], uu[m]);
+              A[(int64_t)r * N + j] = v;
+            }
+        }
+      }
+      __syncthreads();
+    }
+  }
+
+  // ---- solve A x = rhs (FP64 rhs in shared memory) into wv (by row) with the factors;
+  // the unknown of column k ends in wv[order[k]] ----
+  auto lu_solve = [&]() {
+    for (int r = tid; r < N; r += kLargeThreads) wv[r] = {(R)rhs[r].x, (R)rhs[r].y};
+    __syncthreads();
+    for (int c0 = 0; c0 < N; c0 += NB) {  // forward: L y = P rhs
+      const int nb = min(NB, N - c0);
+      if (warp == 0) {
+        Cx<R> wi = {0, 0}, lr[NB];
+        int pi = 0;
+        if (lane < nb) {
+          pi = order[c0 + lane];
+          wi = wv[pi];
+        }
+#pragma unroll
+        for (int m = 0; m < NB; ++m) {
+          lr[m] = {0, 0};
+          if (lane < nb && m < lane) lr[m] = A[(int64_t)pi * N + c0 + m];
+        }
+#pragma unroll
+        for (int m = 0; m < NB; ++m) {
+          const Cx<R> ym = {__shfl_sync(0xffffffffu, wi.x, m), __shfl_sync(0xffffffffu, wi.y, m)};
+          if (lane > m && lane < nb) cx_fnma(wi, lr[m], ym);
+        }
+        if (lane < NB) pvec[lane] = lane < nb ? wi : Cx<R>{0, 0};
+        if (lane < nb) wv[pi] = wi;
+      }
+      __syncthreads();
+      for (int r = tid; r < N; r += kLargeThreads)
+        if (pivstep[r] >= c0 + nb) {
+          Cx<R> v = wv[r];
+#pragma unroll
+          for (int m = 0; m < NB; ++m)
+            if (m < nb) cx_fnma(v, A[(int64_t)r * N + c0 + m], pvec[m]);
+          wv[r] = v;
+        }
+      __syncthreads();
+    }
+    const int last = (N - 1) / NB * NB;
+    for (int c0 = last; c0 >= 0; c0 -= NB) {  // back: U x = y
+      const int nb = min(NB, N - c0);
+      if (warp == 0) {
+        Cx<R> wi = {0, 0}, ur[NB];
+        int pi = 0;
+        if (lane < nb) {
+          pi = order[c0 + lane];
+          wi = wv[pi];
+        }
+#pragma unroll
+        for (int m = 0; m < NB; ++m) {
+          ur[m] = {0, 0};
+          if (lane < nb && m >= lane && m < nb) ur[m] = A[(int64_t)pi * N + c0 + m];
+        }
+#pragma unroll
+        for (int m = NB - 1; m >= 0; --m) {
+          if (lane == m && lane < nb) wi = cx_div(wi, ur[m]);
+          const Cx<R> xm = {__shfl_sync(0xffffffffu, wi.x, m), __shfl_sync(0xffffffffu, wi.y, m)};
+          if (lane < m && m < nb) cx_fnma(wi, ur[m], xm);
+        }
+        if (lane < NB) pvec[lane] = lane < nb ? wi : Cx<R>{0, 0};
+        if (lane < nb) wv[pi] = wi;
+      }
+      __syncthreads();
+      for (int r = tid; r < N; r += kLargeThreads)
+        if (pivstep[r] < c0) {
+          Cx<R> v = wv[r];
+#pragma unroll
+          for (int m = 0; m < NB; ++m)
+            if (m < nb) cx_fnma(v, A[(int64_t)r * N + c0 + m], pvec[m]);
+          wv[r] = v;
+        }
+      __syncthreads();
+    }
+  };
+
+  // refined solve of A x = rhs into xk (rhs is kept); returns whether it converged
+  auto refined = [&]() -> bool {
+    for (int r = tid; r < N; r += kLargeThreads) sv[r] = rhs[r];
+    lu_solve();
+    double xm = 0.0;
+    for (int k = tid; k < N; k += kLargeThreads) {
+      const Cx<R> v = wv[order[k]];
+      xk[k] = {(double)v.x, (double)v.y};
+      xm = fmax(xm, fabs((double)v.x) + fabs((double)v.y));
+    }
+    bool conv = true;
+    if (sizeof(R) < 8) {
+      double dprev = block_max(xm, red);  // its barriers also publish xk
+      conv = a.max_refine == 0;
+      for (int it = 0; it < a.max_refine; ++it) {
+        for (int r = tid; r < N; r += kLargeThreads) {  // FP64 residual sv - A xk
+          double sx = 0.0, sy = 0.0;
+          for (int j = 0; j < N; ++j) {
+            const double m = M[(int64_t)j * N + r];  // M symmetric: column r, coalesced
+            sx = fma(m, xk[j].x, sx);
+            sy = fma(m, xk[j].y, sy);
+          }
+          const double dx = Rk[r], dy = -1.0 / (w * Cb[r]);
+          const double ax = dx * xk[r].x - dy * xk[r].y - w * sy;
+          const double ay = dx * xk[r].y + dy * xk[r].x + w * sx;
+          rhs[r] = {sv[r].x - ax, sv[r].y - ay};
+        }
+        __syncthreads();
+        lu_solve();
+        double dm = 0.0, xm2 = 0.0;
+        for (int k = tid; k < N; k += kLargeThreads) {
+          const Cx<R> d = wv[order[k]];
+          xk[k].x += (double)d.x;
+          xk[k].y += (double)d.y;
+          dm = fmax(dm, fabs((double)d.x) + fabs((double)d.y));
+          xm2 = fmax(xm2, fabs(xk[k].x) + fabs(xk[k].y));
+        }
+        dm = block_max(dm, red);
+        xm2 = block_max(xm2, red);
+        const double est = dm * fmin(1.0, dm / fmax(dprev, 1e-300));
+        conv = conv || est <= a.tol * xm2;
+        const bool stop = conv || !(dm <= 0.5 * dprev);
+        dprev = dm;
+        if (stop) break;
+      }
+      for (int r = tid; r < N; r += kLargeThreads) rhs[r] = sv[r];
+    }
+    __syncthreads();
+    return conv;
+  };
+
+  const int64_t ioff = si.b * a.sumFN + a.t.fn_off[si.s] + (int64_t)si.f * N;
+  bool conv_all = true;
+  if (!bwd) {
+    for (int r = tid; r < N; r += kLargeThreads) {
+      const double* Vp = a.V + 2 * (a.t.fn_off[si.s] + (int64_t)si.f * N + r);
+      rhs[r] = {Vp[0], Vp[1]};
+    }
+    __syncthreads();
+    conv_all = refined();
+    for (int r = tid; r < N; r += kLargeThreads) {
+      xc[r] = xk[r];
+      a.I[2 * (ioff + r)] = xk[r].x;
+      a.I[2 * (ioff + r) + 1] = xk[r].y;
+      if (a.I_out) {
+        a.I_out[2 * (ioff + r)] = xk[r].x;
+        a.I_out[2 * (ioff + r) + 1] = xk[r].y;
+      }
+    }
+    if (a.Bop != nullptr) {
+      // tensor-core operand pieces of I: rows 2 (b F_s + f) + {0: re, 1: im}, columns
+      // N .. K_pad-1 zero; x = xh + xl, pieces bf16(rem), rem -= piece in FP32
+      const int nkc = (N + kChunkK - 1) / kChunkK;
+      const int64_t ntile = (2 * a.n_cfg * F + kTileN - 1) / kTileN;
+      char* base = reinterpret_cast<char*>(a.Bop + a.bop_off[si.s]);
+      const size_t tile_bytes = (size_t)kTileN * kChunkK * 2;
+      for (int kg = tid; kg < nkc * kChunkK; kg += kLargeThreads) {
+        const int kc = kg / kChunkK, kk = kg % kChunkK;
+        for (int c = 0; c < 2; ++c) {
+          const int64_t n = 2 * (si.b * F + si.f) + c;
+          const int64_t tile = n / kTileN;
+          const uint32_t rr = (uint32_t)(n % kTileN);
+          const double xv = kg < N ? (c == 0 ? xk[kg].x : xk[kg].y) : 0.0;
+          const float xh = (float)xv, xl = (float)(xv - (double)xh);
+          float rem = xh;
+          for (int q = 0; q < a.npieces; ++q) {
+            const __nv_bfloat16 h = __float2bfloat16_rn(rem);
+            rem = rem - __bfloat162float(h);
+            if (q == 0) rem += xl;
+            const size_t off = ((size_t)(q * ntile + tile) * nkc + kc) * tile_bytes + swz128(rr, kk);
+            *reinterpret_cast<__nv_bfloat16*>(base + off) = h;
+          }
+        }
+      }
+    }
+  } else {
+    for (int r = tid; r < N; r += kLargeThreads) xc[r] = {a.I[2 * (ioff + r)], a.I[2 * (ioff + r) + 1]};
+  }
+  __syncthreads();
+
+  // ---- objective at the loss points and the adjoint right-hand side u = H_loss^T conj(G) ----
+  const bool has_obj = !bwd && a.target != nullptr;
+  if (has_obj || bwd) {
+    if (has_obj) {
+      const int Ls = a.loss_off[si.s + 1] - a.loss_off[si.s];
+      const double* __restrict__ Hl = a.Hl64 + a.t.ln_off[si.s];
+      const int tw = a.loss_mode == 0 ? 1 : 2;
+      const double* tb = a.target + (a.target_per_cfg ? si.b * a.sumFL * tw : 0) +
+                         (a.t.fl_off[si.s] + (int64_t)si.f * Ls) * tw;
+      cd* Gs = reinterpret_cast<cd*>(dsm + L.pan);  // the panel is free after the LU
+      double lsum = 0.0;
+      for (int r = tid; r < N; r += kLargeThreads) rhs[r] = {0.0, 0.0};
+      for (int c0 = 0; c0 < Ls; c0 += kLargeThreads) {
+        const int l = c0 + tid;
+        cd Gl = {0.0, 0.0};
+        if (l < Ls) {
+          double bx = 0.0, by = 0.0;
+          for (int k = 0; k < N; ++k) {
+            const double h = Hl[(int64_t)l * N + k];
+            bx = fma(h, xc[k].x, bx);
+            by = fma(h, xc[k].y, by);
+          }
+          lsum += point_loss(a.loss_mode, cd{bx, by}, tb + (int64_t)l * tw, &Gl);
+        }
+        Gs[tid] = {Gl.x, -Gl.y};  // conj(G)
+        __syncthreads();
+        const int lc = min(kLargeThreads, Ls - c0);
+        for (int r = tid; r < N; r += kLargeThreads) {
+          double ux = rhs[r].x, uy = rhs[r].y;
+          for (int q = 0; q < lc; ++q) {
+            const double h = Hl[(int64_t)(c0 + q) * N + r];
+            ux = fma(h, Gs[q].x, ux);
+            uy = fma(h, Gs[q].y, uy);
+          }
+          rhs[r] = {ux, uy};
+        }
+        __syncthreads();
+      }
+      const double tot = block_sum(lsum, red);
+      if (tid == 0) a.loss_part[sys] = tot;
+    } else {
+      for (int r = tid; r < N; r += kLargeThreads)
+        rhs[r] = {a.rhs_in[2 * (ioff + r)], a.rhs_in[2 * (ioff + r) + 1]};
+    }
+    __syncthreads();
+    conv_all = refined() && conv_all;
+    for (int r = tid; r < N; r += kLargeThreads) {
+      const cd mu = xk[r], x = xc[r];
+      a.grad_part[ioff + r] = (mu.x * x.y + mu.y * x.x) / (w * Cb[r] * Cb[r]);
+    }
+  }
+  double bad = 0.0;
+  for (int r = tid; r < N; r += kLargeThreads)
+    if (!(isfinite(xc[r].x) && isfinite(xc[r].y) && isfinite(xk[r].x) && isfinite(xk[r].y)))
+      bad = 1.0;
+  bad = block_max(bad, red);
+  if (tid == 0 && !bwd) a.status[sys] = bad > 0.0 ? 2 : (conv_all ? 0 : 1);
+}
+
+size_t large_solve_smem(mts_precision prec, int max_ports) {
+  return prec == MTS_FP64 ? LargeSmem<double>(max_ports).bytes : LargeSmem<float>(max_ports).bytes;
+}
+
+cudaError_t launch_solve_large(const SolveArgs& a, mts_precision prec, int64_t n_sys, int min_ports,
+                               int max_ports, void* scratch, cudaStream_t st) {
+  if (n_sys == 0) return cudaSuccess;
+  const size_t sm = large_solve_smem(prec, max_ports);
+  if (prec == MTS_FP64) {
+    cudaError_t e = cudaFuncSetAttribute(solve_large_kernel<double>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    solve_large_kernel<double><<<(unsigned)n_sys, kLargeThreads, sm, st>>>(
+        a, n_sys, min_ports, max_ports, static_cast<Cx<double>*>(scratch));
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(solve_large_kernel<float>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    solve_large_kernel<float><<<(unsigned)n_sys, kLargeThreads, sm, st>>>(
+        a, n_sys, min_ports, max_ports, static_cast<Cx<float>*>(scratch));
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace mts

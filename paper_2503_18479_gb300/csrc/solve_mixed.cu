@@ -192,8 +192,10 @@ __global__ void __launch_bounds__(NM >= 64 ? NM : 128, NM >= 64 ? 5 : 1) solve_m
   SmemV3<NM>& sm = reinterpret_cast<SmemV3<NM>*>(dsm)[grp];
 
   const int64_t sys = (int64_t)blockIdx.x * G + grp;
-  const bool valid = sys < n_sys;
-  SysInfo si = sys_info(a, valid ? sys : 0);
+  const bool in_range = sys < n_sys;
+  SysInfo si = sys_info(a, in_range ? sys : 0);
+  const bool valid = in_range && si.N <= NM;  // larger systems: solve_large.cu
+  if (!valid) si.N = 0;
   const int N = si.N;
   const double w = si.w;
   const float w32 = (float)w;

@@ -1,8 +1,9 @@
 // superpose.cu -- (c) of the method: B = H I (paper Eq. 7), the field of every
 // configuration and frequency as the superposition of the per-port basis fields.
 //
-//   plan_kernel          per-call tables: bases of the tensor-core operand of I and the
-//                        prefix of GEMM work units per structure
+//   plan_kernel          per-call tables: bases of the tensor-core operand of I, the
+//                        prefix of GEMM work units and the bases of the LU factor scratch
+//                        per structure
 //   superpose_fp64_kernel  FP64 SIMT (MTS_FP64): CTA = 128 points x 64 systems
 //   The tensor-core kernel for MTS_MIXED / MTS_BF16 lives in superpose_tc.cu.
 #include <cuda_runtime.h>
@@ -15,12 +16,13 @@ namespace mts {
 __global__ void plan_kernel(int n_struct, int64_t n_cfg, const int32_t* __restrict__ port_off,
                             const int64_t* __restrict__ point_off,
                             const int32_t* __restrict__ freq_off, int npieces,
-                            int64_t* bop_off, int64_t* unit_off) {
+                            int64_t* bop_off, int64_t* unit_off, int64_t* lu_off) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  int64_t a = 0, u = 0;
+  int64_t a = 0, u = 0, f = 0;
   for (int s = 0; s < n_struct; ++s) {
     bop_off[s] = a;
     unit_off[s] = u;
+    lu_off[s] = f;
     int64_t N = port_off[s + 1] - port_off[s];
     int64_t P = point_off[s + 1] - point_off[s];
     int64_t F = freq_off[s + 1] - freq_off[s];
@@ -29,15 +31,17 @@ __global__ void plan_kernel(int n_struct, int64_t n_cfg, const int32_t* __restri
     int64_t nkc = (N + kChunkK - 1) / kChunkK;
     a += (int64_t)npieces * nn * nkc * kTileN * kChunkK;
     u += np * nn;
+    if (N > kRegMaxPorts) f += F * N * N;
   }
   bop_off[n_struct] = a;
   unit_off[n_struct] = u;
+  lu_off[n_struct] = f;
 }
 
 cudaError_t launch_plan(const mts_problem* pb, int64_t n_cfg, int npieces, int64_t* bop_off,
-                        int64_t* unit_off, cudaStream_t st) {
+                        int64_t* unit_off, int64_t* lu_off, cudaStream_t st) {
   plan_kernel<<<1, 32, 0, st>>>(pb->n_struct, n_cfg, pb->port_off, pb->point_off, pb->freq_off,
-                                npieces, bop_off, unit_off);
+                                npieces, bop_off, unit_off, lu_off);
   note_launch();
   return cudaGetLastError();
 }

@@ -325,9 +325,9 @@ def ragged(seed: int = 0, n_struct: int = 10000, grid: int = 64, max_freq: int =
 
 
 def array_32x32(seed: int = 0, n_cfg: int = 256, grid: int = 512,
-                planes=(0.010, 0.020, 0.030, 0.040)) -> Workload:
+                planes=(0.010, 0.020, 0.030, 0.040), seg_per_side: int = 16) -> Workload:
     rng = np.random.Generator(np.random.PCG64(seed))
-    loops = square_array(32, 32)
+    loops = square_array(32, 32, seg_per_side=seg_per_side)
     omega = 2 * np.pi * np.array([63.6 * MHZ])
     pts = _concat_points(*[grid_plane(grid, 0.900, z) for z in planes],
                          _cell_centre_points(32, 32, 0.055, 0.040))

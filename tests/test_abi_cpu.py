@@ -152,16 +152,41 @@ def test_workspace_and_alignment_checks(nv):
     assert nv.mts_launch_count() == 0
 
 
-def test_solver_size_limit_is_reported(nv):
-    """Structures with more than 64 ports validate, but the solve reports MTS_EUNSUPPORTED
-    (before any launch) until the large-system kernels exist."""
+def _wide_workload(nx, ny, n_freq=1):
+    loops = W.square_array(nx, ny, seg_per_side=1)
+    pts = W.grid_plane(2, 0.1, 0.02)
+    omega = 2 * np.pi * np.linspace(60e6, 68e6, n_freq)
+    st = W._structure_from(loops, pts, omega, 0.1, np.arange(2))
+    C = np.full((1, nx * ny), 50e-12)
+    return W.Workload("wide", [st], C, 0.001, target=np.zeros(2 * n_freq))
+
+
+def test_port_limit_is_reported(nv):
+    """Up to 1024 ports per structure validate; 1025 ports give MTS_EUNSUPPORTED (before any
+    launch) from every entry point that validates the problem."""
     L = nv.lib()
-    wl = W.ragged(n_struct=2, grid=4, max_freq=1, port_choices=(128,))
-    c, keep = fake_problem(nv, wl)
+    c, keep = fake_problem(nv, _wide_workload(32, 32))
+    assert L.mts_basis_bytes(ct.byref(c), nv.MTS_MIXED) > 0
+    c, keep = fake_problem(nv, _wide_workload(41, 25))
+    assert L.mts_basis_bytes(ct.byref(c), nv.MTS_MIXED) == 0
     ev = nv.MtsEval()
     ev.n_cfg = 1
     ev.C = ev.omega = ev.V = FAKE
-    tneed = L.mts_tape_bytes(ct.byref(c), 1, nv.MTS_MIXED)
     code = L.mts_solve(ct.byref(c), nv.MTS_MIXED, ct.c_void_p(FAKE), ct.byref(ev), None, None,
-                       ct.c_void_p(FAKE), tneed, None)
+                       ct.c_void_p(FAKE), 1 << 40, None)
     assert code == nv.MTS_EUNSUPPORTED
+
+
+def test_tape_holds_factors_of_large_systems(nv):
+    """Structures with more than 64 ports keep their LU factors in the tape: complex FP32
+    (8 bytes) per matrix element for MTS_MIXED, complex FP64 (16 bytes) for MTS_FP64, for
+    every configuration and frequency; structures of up to 64 ports add nothing."""
+    L = nv.lib()
+    small, k1 = fake_problem(nv, _wide_workload(8, 8, n_freq=3))
+    big, k2 = fake_problem(nv, _wide_workload(16, 8, n_freq=3))
+    for prec, elem in ((nv.MTS_MIXED, 8), (nv.MTS_FP64, 16)):
+        t1 = L.mts_tape_bytes(ct.byref(big), 5, prec) - L.mts_tape_bytes(ct.byref(big), 4, prec)
+        t0 = L.mts_tape_bytes(ct.byref(small), 5, prec) - L.mts_tape_bytes(ct.byref(small), 4, prec)
+        # per-configuration growth: the factor block plus the small per-port arrays
+        assert t1 - elem * 3 * 128 * 128 > 0
+        assert t1 - elem * 3 * 128 * 128 < 4 * t0 + 4096

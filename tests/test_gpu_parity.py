@@ -15,6 +15,11 @@ from paper_2503_18479_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 TOL_B = {"fp64": 1e-10, "mixed": 1e-6, "bf16": 1e-2}
+# MTS_MIXED at K = 1024 ports: the tensor core rounds its FP32 accumulator once per 16-term
+# MMA, 6 piece pairs x 64 K-steps = 384 roundings along each output. A plain sequential FP32
+# sum of the exact products already gives 8.3e-7 on this case (Sum|H_pk I_k| / |B_p| up to
+# 95), so the bound there is the FP32-accumulation floor, not the piece split.
+TOL_B_K1024_MIXED = 5e-6
 TOL_I = {"fp64": 1e-10, "mixed": 1e-7, "bf16": 1e-7}  # refinement default 1e-8
 TOL_LOSS = {"fp64": 1e-10, "mixed": 1e-6, "bf16": 1e-6}
 TOL_GRAD = {"fp64": 1e-10, "mixed": 1e-6, "bf16": 1e-6}
@@ -31,6 +36,10 @@ _CASES = {
     "line": lambda: small_line(),
     "8x8": lambda: small_8x8(),
     "ragged": lambda: apply_target_rule(small_ragged()),
+    # 128-port structures (blocked large-system solve) beside register-resident ones
+    "ragged128": lambda: small_ragged(n_struct=7, seed=5, grid=10, max_freq=3, ports=(8, 64, 128)),
+    # 1024 ports: coarse loop polygons keep the oracle's inductance matrix quick
+    "32x32": lambda: W.array_32x32(seed=2, n_cfg=3, grid=12, planes=(0.02,), seg_per_side=2),
 }
 _cache = {}
 
@@ -83,7 +92,8 @@ def test_forward(name, prec):
     loss = out["loss"].cpu().numpy()
     for s in range(len(wl.structures)):
         assert rel(Is[s], ref[s]["I"]) < TOL_I[prec], (s, rel(Is[s], ref[s]["I"]))
-        assert rel(Bs[s], ref[s]["B"]) < TOL_B[prec], (s, rel(Bs[s], ref[s]["B"]))
+        tb = TOL_B_K1024_MIXED if (prec == "mixed" and wl.structures[s].n_ports > 128) else TOL_B[prec]
+        assert rel(Bs[s], ref[s]["B"]) < tb, (s, rel(Bs[s], ref[s]["B"]))
         assert rel(loss[:, s], ref[s]["loss"]) < TOL_LOSS[prec], (s, rel(loss[:, s], ref[s]["loss"]))
 
 
@@ -102,24 +112,28 @@ def test_gradient(name, prec):
         assert cosine(g[s], ref[s]["grad"]) >= 0.9999
 
 
+@pytest.mark.parametrize("name", ["8x8", "ragged128", "32x32"])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_field_cotangent(prec):
+def test_field_cotangent(name, prec):
     """Backward with a field cotangent dL/dRe B + j dL/dIm B (and a loss cotangent)."""
-    wl, _ = case("8x8")
-    nc = 40
-    cfg = np.arange(nc)
+    wl, _ = case(name)
+    nc = min(40, wl.n_cfg)
     sub = W.Workload(wl.name, wl.structures, wl.C[:nc].copy(), wl.wire_radius, target=wl.target)
-    st = sub.structures[0]
-    gB = W.random_cotangent((nc, st.n_freq, st.n_points), seed=7)
-    bases = [structure_basis(sub, 0)]
-    ref = oracle_reference(sub, want_B=False, gB=[gB], bases=bases)
+    gBs = [W.random_cotangent((nc, st.n_freq, st.n_points), seed=7 + s)
+           for s, st in enumerate(sub.structures)]
+    bases = [structure_basis(sub, s) for s in range(len(sub.structures))]
+    ref = oracle_reference(sub, want_B=False, gB=gBs, bases=bases)
     sim = sim_for(sub, prec)
     C = torch.from_numpy(sub.C).cuda().requires_grad_(True)
     B, loss = sim(C, want_B=True)
     gl = torch.linspace(0.5, 2.0, nc, dtype=torch.float64, device="cuda")[:, None]
-    gBt = torch.from_numpy(gB.reshape(nc, -1)).to(B.dtype).cuda()
+    gl = gl.expand(nc, len(sub.structures)).contiguous()
+    gflat = np.concatenate([g.reshape(nc, -1) for g in gBs], axis=1)
+    gBt = torch.from_numpy(gflat).to(B.dtype).cuda()
     torch.autograd.backward([B, loss], [gBt, gl])
-    want = ref[0]["grad_field"] + gl.cpu().numpy() * ref[0]["grad"]
+    glc = gl.cpu().numpy()
+    want = np.concatenate([ref[s]["grad_field"] + glc[:, s:s + 1] * ref[s]["grad"]
+                           for s in range(len(sub.structures))], axis=1)
     tol = 1e-9 if prec == "fp64" else 1e-5
     assert rel(C.grad.cpu().numpy(), want) < tol, rel(C.grad.cpu().numpy(), want)
     assert cosine(C.grad.cpu().numpy(), want) >= 0.9999
