@@ -26,6 +26,9 @@ ProblemSums problem_sums(const mts_problem* pb, mts_precision prec) {
     if (N > ps.max_ports) ps.max_ports = (int)N;
     if (s == 0 || N < ps.min_ports) ps.min_ports = (int)N;
     if (N > kRegMaxPorts) ps.sumLU += F * N * N;
+    const int c = port_class(N);
+    ps.cls_count[c] += F;
+    if (N > ps.cls_max_ports[c]) ps.cls_max_ports[c] = (int)N;
     ps.sumNN += N * N;
     ps.sumPN += P * N;
     ps.sumLN += L * N;
@@ -51,6 +54,7 @@ TableLayout table_layout(int n_struct, int n_freq) {
   t.ptile_off = o; o += arr;
   t.pair_off = o; o += arr;
   t.freq_struct = o; o += align256(sizeof(int32_t) * (size_t)(n_freq > 0 ? n_freq : 1));
+  t.cls_freq = o; o += align256(sizeof(int32_t) * (size_t)(n_freq > 0 ? n_freq : 1));
   t.bytes = o;
   return t;
 }
@@ -79,23 +83,31 @@ PlanLayout plan_layout(int n_struct) {
   p.bop_off = 0;
   p.unit_off = arr;
   p.lu_off = 2 * arr;
-  p.bytes = 3 * arr;
+  p.simt_off = 3 * arr;
+  p.bytes = 4 * arr;
   return p;
 }
 
-static int64_t bop_elems(const mts_problem* pb, int64_t n_cfg, int npieces, int64_t* units) {
-  int64_t a = 0, u = 0;
+// Elements of the tensor-core B operand, and the GEMM / SIMT work units of the superposition.
+static int64_t bop_elems(const mts_problem* pb, int64_t n_cfg, int npieces, int64_t* units,
+                         int64_t* simt_units = nullptr) {
+  int64_t a = 0, u = 0, v = 0;
   for (int s = 0; s < pb->n_struct; ++s) {
     int64_t N = pb->h_port_off[s + 1] - pb->h_port_off[s];
     int64_t P = pb->h_point_off[s + 1] - pb->h_point_off[s];
     int64_t F = pb->h_freq_off[s + 1] - pb->h_freq_off[s];
-    int64_t nn = (2 * n_cfg * F + kTileN - 1) / kTileN;
-    int64_t npt = (P + kTileP - 1) / kTileP;
-    int64_t nkc = (N + kChunkK - 1) / kChunkK;
-    a += (int64_t)npieces * nn * nkc * kTileN * kChunkK;
-    u += npt * nn;
+    if (use_tensor_path(npieces, n_cfg, F)) {
+      int64_t nn = (2 * n_cfg * F + kTileN - 1) / kTileN;
+      int64_t npt = (P + kTileP - 1) / kTileP;
+      int64_t nkc = (N + kChunkK - 1) / kChunkK;
+      a += (int64_t)npieces * nn * nkc * kTileN * kChunkK;
+      u += npt * nn;
+    } else {
+      v += (P + kSimtPts - 1) / kSimtPts * ((n_cfg * F + kSimtSys - 1) / kSimtSys);
+    }
   }
   if (units) *units = u;
+  if (simt_units) *simt_units = v;
   return a;
 }
 
@@ -345,11 +357,12 @@ mts_status mts_solve(const mts_problem* pb, mts_precision prec, const void* basi
   if (e == cudaSuccess)
     e = launch_plan(pb, ev->n_cfg, n_pieces(prec), reinterpret_cast<int64_t*>(T + tl.plan + pl.bop_off),
                     reinterpret_cast<int64_t*>(T + tl.plan + pl.unit_off),
-                    reinterpret_cast<int64_t*>(T + tl.plan + pl.lu_off), st);
+                    reinterpret_cast<int64_t*>(T + tl.plan + pl.lu_off),
+                    reinterpret_cast<int64_t*>(T + tl.plan + pl.simt_off), st);
   if (e != cudaSuccess) return MTS_ECUDA;
   SolveArgs a = solve_args(pb, prec, basis, ev, tape, ps);
   a.I_out = I_out;
-  e = launch_solve(a, prec, ps.min_ports, ps.max_ports, st);
+  e = launch_solve(a, prec, ps, st);
   if (e == cudaErrorNotSupported) return MTS_EUNSUPPORTED;
   if (e != cudaSuccess) return MTS_ECUDA;
   if (ev->target) {
@@ -386,8 +399,9 @@ mts_status mts_superpose(const mts_problem* pb, mts_precision prec, const void* 
   a.n_cfg = ev->n_cfg;
   a.sumFN = ps.sumFN;
   a.sumFP = ps.sumFP;
-  bop_elems(pb, ev->n_cfg, n_pieces(prec), &a.total_units);
+  bop_elems(pb, ev->n_cfg, n_pieces(prec), &a.total_units, &a.total_simt);
   a.unit_off = reinterpret_cast<const int64_t*>(T + tl.plan + pl.unit_off);
+  a.simt_off = reinterpret_cast<const int64_t*>(T + tl.plan + pl.simt_off);
   a.H = B + bl.H;
   a.I = reinterpret_cast<const double*>(T + tl.I);
   a.Aop = reinterpret_cast<const __nv_bfloat16*>(B + bl.Aop);
@@ -396,7 +410,7 @@ mts_status mts_superpose(const mts_problem* pb, mts_precision prec, const void* 
   a.npieces = n_pieces(prec);
   a.B_out = B_out;
   a.err = reinterpret_cast<int32_t*>(const_cast<char*>(T) + tl.err);
-  if (pb->n_struct == 1) {
+  if (pb->n_struct == 1 && a.total_units > 0) {
     a.uni.on = 1;
     a.uni.N = pb->h_port_off[1];
     a.uni.F = pb->h_freq_off[1];
@@ -451,7 +465,7 @@ mts_status mts_backward(const mts_problem* pb, mts_precision prec, const void* b
     a.rhs_in = reinterpret_cast<const double*>(T + tl.mu);
     a.Bop = nullptr;
     a.target = nullptr;
-    e = launch_solve(a, prec, ps.min_ports, ps.max_ports, st);
+    e = launch_solve(a, prec, ps, st);
     if (e == cudaErrorNotSupported) return MTS_EUNSUPPORTED;
     if (e != cudaSuccess) return MTS_ECUDA;
     ReduceArgs r = reduce_args(pb, prec, basis, ev, tape, ps);

@@ -31,7 +31,9 @@ __global__ void tables_kernel(int n_struct, int n_freq, const int32_t* __restric
                               const int32_t* __restrict__ loss_off, int npieces, int64_t* nn,
                               int64_t* pn, int64_t* ln, int64_t* fn, int64_t* fp, int64_t* fl,
                               int64_t* aop, int64_t* ptile, int64_t* pair,
-                              int32_t* freq_struct) {
+                              int32_t* freq_struct, int32_t* cls_freq) {
+  __shared__ int cls_base[kNumPortClasses];
+  __shared__ int wcnt[8][kNumPortClasses];
   if (threadIdx.x == 0) {
     int64_t a = 0, b = 0, c = 0, d = 0, e = 0, f = 0, g = 0, h = 0, q = 0;
     for (int s = 0; s < n_struct; ++s) {
@@ -56,6 +58,52 @@ __global__ void tables_kernel(int n_struct, int n_freq, const int32_t* __restric
       if (freq_off[mid] <= gi) lo = mid; else hi = mid;
     }
     freq_struct[gi] = lo;
+  }
+  // frequencies grouped by the port class of their structure, ascending within a class
+  // (stable partition: class counts, then ballot prefix sums over chunks of 256)
+  if (threadIdx.x < kNumPortClasses) cls_base[threadIdx.x] = 0;
+  __syncthreads();
+  for (int gi = threadIdx.x; gi < n_freq; gi += blockDim.x) {
+    int s = freq_struct[gi];
+    atomicAdd(&cls_base[port_class(port_off[s + 1] - port_off[s])], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int o = 0;
+    for (int c = 0; c < kNumPortClasses; ++c) {
+      int n = cls_base[c];
+      cls_base[c] = o;
+      o += n;
+    }
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int g0 = 0; g0 < n_freq; g0 += blockDim.x) {
+    const int gi = g0 + threadIdx.x;
+    int c = -1;
+    if (gi < n_freq) {
+      int s = freq_struct[gi];
+      c = port_class(port_off[s + 1] - port_off[s]);
+    }
+    unsigned mine = 0u;
+    for (int cc = 0; cc < kNumPortClasses; ++cc) {
+      unsigned bal = __ballot_sync(0xffffffffu, c == cc);
+      if (lane == 0) wcnt[w][cc] = __popc(bal);
+      if (c == cc) mine = __popc(bal & ((1u << lane) - 1u));
+    }
+    __syncthreads();
+    if (c >= 0) {
+      int o = cls_base[c] + (int)mine;
+      for (int q = 0; q < w; ++q) o += wcnt[q][c];
+      cls_freq[o] = gi;
+    }
+    __syncthreads();
+    if (threadIdx.x < kNumPortClasses) {
+      int t = 0;
+      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += wcnt[q][threadIdx.x];
+      cls_base[threadIdx.x] += t;
+    }
+    __syncthreads();
   }
 }
 
@@ -431,7 +479,7 @@ cudaError_t launch_build_basis(const mts_problem* pb, mts_precision prec, void* 
       (int64_t*)(T + tl.nn_off), (int64_t*)(T + tl.pn_off), (int64_t*)(T + tl.ln_off),
       (int64_t*)(T + tl.fn_off), (int64_t*)(T + tl.fp_off), (int64_t*)(T + tl.fl_off),
       (int64_t*)(T + tl.aop_off), (int64_t*)(T + tl.ptile_off), (int64_t*)(T + tl.pair_off),
-      (int32_t*)(T + tl.freq_struct));
+      (int32_t*)(T + tl.freq_struct), (int32_t*)(T + tl.cls_freq));
   note_launch();
   DevTables t = dev_tables(basis, bl, pb->n_struct, pb->n_freq);
   // host copies of the tile and pair counts

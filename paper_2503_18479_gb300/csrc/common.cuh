@@ -3,7 +3,8 @@
 // Buffer layouts (all offsets in bytes from the caller's 256-byte aligned buffer):
 //
 // Basis (built by mts_build_basis, read-only afterwards):
-//   tables     int64 per-structure prefix tables (device copies, written by a kernel)
+//   tables     int64 per-structure prefix tables (device copies, written by a kernel), the
+//              structure of every frequency, and the frequencies grouped by port class
 //   M64        FP64 [sum_s N_s^2]               inductance matrix blocks
 //   H          FP64 (MTS_FP64) or FP32 [sum_s P_s N_s]   field basis, points x loops
 //   Hloss64    FP64 [sum_s L_s N_s]             rows of H at the loss points
@@ -23,7 +24,8 @@
 //   status     int32 [n_cfg][n_freq]            0 ok, 1 not converged, 2 non-finite
 //   mu         FP64 complex [n_cfg][sum F N]    backward scratch (u = H^T conj(grad_B))
 //   gfield     FP64 [n_cfg][n_ports]            field-cotangent part of the gradient
-//   plan       int64 per-call tables (B-operand bases, GEMM unit prefixes, factor bases)
+//   plan       int64 per-call tables (B-operand bases, GEMM and SIMT unit prefixes, factor
+//              bases)
 //   err        int32 [4]: [0] bounded-wait timeout code, [1] count of bad systems
 //   Bop        bf16 tensor-core operand of I, per structure
 //              [piece][n_tile][k_chunk][128 rows x 64 k], row = 2 (b F_s + f) + c
@@ -44,6 +46,26 @@ constexpr int kChunkK = 64;   // K elements per 128-byte swizzle atom (16-bit ty
 constexpr int kMaxPorts = 1024;    // largest structure (ports) the library accepts
 constexpr int kRegMaxPorts = 64;   // largest system the register-resident solve kernels hold
 
+// Solve schedules by port count: classes 0..3 run the register-resident kernels with
+// 8/16/32/64 threads per system, class 4 the blocked large-system kernel.
+constexpr int kNumPortClasses = 5;
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline int port_class(int64_t N) { return N <= 8 ? 0 : N <= 16 ? 1 : N <= 32 ? 2 : N <= 64 ? 3 : 4; }
+
+// Superposition schedule of a structure: the tensor-core GEMM when its configurations x
+// frequencies fill column tiles, else the SIMT kernel (H read once, no padded columns).
+// MTS_FP64 (npieces == 0) always takes the SIMT kernel.
+constexpr int kSimtPts = 128;  // points per SIMT unit (one per thread)
+constexpr int kSimtSys = 16;   // systems per SIMT unit
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline bool use_tensor_path(int npieces, int64_t n_cfg, int64_t F) {
+  return npieces > 0 && n_cfg * F > kSimtSys;
+}
+
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 inline size_t align256(size_t a) { return (a + 255) / 256 * 256; }
 
@@ -55,6 +77,8 @@ struct ProblemSums {
   int max_ports = 0;
   int min_ports = 0;
   int64_t sumLU = 0;  // sum over structures with N_s > kRegMaxPorts of F_s N_s^2 (factor scratch)
+  int64_t cls_count[kNumPortClasses] = {0, 0, 0, 0, 0};  // frequencies per port class
+  int cls_max_ports[kNumPortClasses] = {0, 0, 0, 0, 0};
   int64_t sumNN = 0, sumPN = 0, sumLN = 0, sumFN = 0, sumFP = 0, sumFL = 0;
   int64_t sumAop = 0;  // bf16 elements per piece-set of the H operand (all pieces)
 };
@@ -68,7 +92,7 @@ struct BasisLayout {
 // Device-side table block inside the basis (arrays of n_struct+1 int64 unless noted).
 struct TableLayout {
   size_t nn_off, pn_off, ln_off, fn_off, fp_off, fl_off, aop_off, ptile_off, pair_off,
-      freq_struct /* int32 [n_freq] */, bytes;
+      freq_struct /* int32 [n_freq] */, cls_freq /* int32 [n_freq] */, bytes;
 };
 
 struct TapeLayout {
@@ -78,7 +102,7 @@ struct TapeLayout {
 
 // Per-call plan tables inside the tape (arrays of n_struct+1 int64).
 struct PlanLayout {
-  size_t bop_off, unit_off, lu_off, bytes;
+  size_t bop_off, unit_off, lu_off, simt_off, bytes;
 };
 
 ProblemSums problem_sums(const mts_problem* pb, mts_precision prec);
@@ -99,6 +123,7 @@ struct DevTables {
   const int64_t* ptile_off;  // prefix of ceil(P_s / 128): point tiles of the basis kernels
   const int64_t* pair_off;   // prefix of N_s (N_s + 1) / 2: loop pairs of the M kernel
   const int32_t* freq_struct;
+  const int32_t* cls_freq;  // frequencies grouped by port class, ascending within a class
 };
 
 inline DevTables dev_tables(const void* basis, const BasisLayout& bl, int n_struct, int n_freq) {
@@ -115,6 +140,7 @@ inline DevTables dev_tables(const void* basis, const BasisLayout& bl, int n_stru
   t.ptile_off = reinterpret_cast<const int64_t*>(b + tl.ptile_off);
   t.pair_off = reinterpret_cast<const int64_t*>(b + tl.pair_off);
   t.freq_struct = reinterpret_cast<const int32_t*>(b + tl.freq_struct);
+  t.cls_freq = reinterpret_cast<const int32_t*>(b + tl.cls_freq);
   return t;
 }
 

@@ -40,6 +40,10 @@ struct SolveArgs {
   const int64_t* lu_off;   // per-structure element base of the factor scratch (plan table;
                            // [n_struct] = elements per configuration)
   void* lu;                // factor scratch of the large-system kernel
+  // systems of one launch: all (glist == nullptr: system = launch index), or the
+  // configurations x the gcount frequencies glist[0 .. gcount-1] of one port class
+  const int32_t* glist;
+  int64_t gcount;
   int npieces;
   int max_loss;  // max loss points of one structure (uniform trip count for group loops)
   // backward (field cotangent) mode: solve A mu = rhs_in and write grad terms only
@@ -69,11 +73,11 @@ cudaError_t launch_export_basis(const mts_problem* pb, mts_precision prec, const
 
 // Per-call plan tables in the tape (bases of the B operand, GEMM unit prefixes).
 cudaError_t launch_plan(const mts_problem* pb, int64_t n_cfg, int npieces, int64_t* bop_off,
-                        int64_t* unit_off, int64_t* lu_off, cudaStream_t st);
+                        int64_t* unit_off, int64_t* lu_off, int64_t* simt_off, cudaStream_t st);
 
 // Solve of every system: the register-resident kernels for N <= kRegMaxPorts, the blocked
 // large-system kernel (solve_large.cu) for the others.
-cudaError_t launch_solve(const SolveArgs& a, mts_precision prec, int min_ports, int max_ports,
+cudaError_t launch_solve(const SolveArgs& a, mts_precision prec, const ProblemSums& ps,
                          cudaStream_t st);
 size_t large_solve_smem(mts_precision prec, int max_ports);
 cudaError_t launch_solve_large(const SolveArgs& a, mts_precision prec, int64_t n_sys,
@@ -97,6 +101,8 @@ struct SuperposeArgs {
   int64_t n_cfg, sumFN, sumFP;
   int64_t total_units;      // GEMM work units (host-computed)
   const int64_t* unit_off;  // per-structure prefix of GEMM units (plan table)
+  int64_t total_simt;       // SIMT work units (host-computed)
+  const int64_t* simt_off;  // per-structure prefix of SIMT units (plan table)
   const void* H;            // FP64 (MTS_FP64) basis
   const double* I;          // tape currents
   const __nv_bfloat16* Aop;

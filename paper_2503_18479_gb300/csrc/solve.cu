@@ -48,9 +48,10 @@ __global__ void __launch_bounds__(NM >= 128 ? NM : 128) solve_fp64_kernel(SolveA
   double* red = reinterpret_cast<double*>(Gs + NM);
   int* redi = reinterpret_cast<int*>(red + 32);
 
-  int64_t sys = (int64_t)blockIdx.x * G + grp;
-  const bool in_range = sys < n_sys;
-  SysInfo si = sys_info(a, in_range ? sys : 0);
+  const int64_t li = (int64_t)blockIdx.x * G + grp;
+  const bool in_range = li < n_sys;
+  const int64_t sys = in_range ? launch_sys(a, li) : 0;
+  SysInfo si = sys_info(a, sys);
   const bool valid = in_range && si.N <= NM;  // larger systems: solve_large.cu
   if (!valid) si.N = 0;
   const int N = si.N;
@@ -275,28 +276,37 @@ static cudaError_t launch_fp64(const SolveArgs& a, int64_t n_sys, cudaStream_t s
 
 cudaError_t launch_solve_mixed(const SolveArgs& a, int64_t n_sys, int max_ports, cudaStream_t st);
 
-cudaError_t launch_solve(const SolveArgs& a, mts_precision prec, int min_ports, int max_ports,
+// One launch per port class present (classes 0..3: the register-resident kernel with
+// 8/16/32/64 threads per system; class 4: the blocked large-system kernel). A problem of one
+// structure is a single class and launches over all systems without the frequency list.
+cudaError_t launch_solve(const SolveArgs& a0, mts_precision prec, const ProblemSums& ps,
                          cudaStream_t st) {
-  int64_t n_sys = a.n_cfg * a.n_freq;
-  if (n_sys == 0) return cudaSuccess;
-  cudaError_t e = cudaSuccess;
-  if (min_ports <= kRegMaxPorts) {  // some structure fits the register-resident kernels
-    const int m = max_ports < kRegMaxPorts ? max_ports : kRegMaxPorts;
-    if (prec == MTS_FP64) {
-      if (m <= 8) e = launch_fp64<8>(a, n_sys, st);
-      else if (m <= 16) e = launch_fp64<16>(a, n_sys, st);
-      else if (m <= 32) e = launch_fp64<32>(a, n_sys, st);
-      else e = launch_fp64<64>(a, n_sys, st);
+  if (a0.n_cfg * a0.n_freq == 0) return cudaSuccess;
+  if (ps.max_ports > kMaxPorts) return cudaErrorNotSupported;
+  const bool one = a0.n_struct == 1;
+  int64_t off = 0;
+  for (int c = 0; c < kNumPortClasses; ++c) {
+    const int64_t cnt = ps.cls_count[c];
+    if (cnt == 0) continue;
+    SolveArgs a = a0;
+    a.glist = one ? nullptr : a0.t.cls_freq + off;
+    a.gcount = cnt;
+    off += cnt;
+    const int64_t n_sys = a.n_cfg * cnt;
+    cudaError_t e;
+    if (c == 4) {
+      e = launch_solve_large(a, prec, n_sys, kRegMaxPorts, ps.cls_max_ports[c], a.lu, st);
+    } else if (prec == MTS_FP64) {
+      e = c == 0 ? launch_fp64<8>(a, n_sys, st)
+        : c == 1 ? launch_fp64<16>(a, n_sys, st)
+        : c == 2 ? launch_fp64<32>(a, n_sys, st)
+                 : launch_fp64<64>(a, n_sys, st);
     } else {
-      e = launch_solve_mixed(a, n_sys, m, st);
+      e = launch_solve_mixed(a, n_sys, ps.cls_max_ports[c], st);
     }
     if (e != cudaSuccess) return e;
   }
-  if (max_ports > kRegMaxPorts) {
-    if (max_ports > kMaxPorts) return cudaErrorNotSupported;
-    e = launch_solve_large(a, prec, n_sys, kRegMaxPorts, max_ports, a.lu, st);
-  }
-  return e;
+  return cudaSuccess;
 }
 
 cudaError_t launch_reduce(const ReduceArgs& a, cudaStream_t st) {

@@ -66,6 +66,14 @@ __device__ inline void argmax_shfl_d(double& key, int& idx, int width) {
   }
 }
 
+// System of launch index li: li itself, or configuration li / gcount at the frequency
+// glist[li % gcount] of the launch's port class.
+__device__ inline int64_t launch_sys(const SolveArgs& a, int64_t li) {
+  if (a.glist == nullptr) return li;
+  const int64_t b = li / a.gcount;
+  return b * a.n_freq + a.glist[li - b * a.gcount];
+}
+
 // Locate system `sys` (= b * n_freq + g).
 struct SysInfo {
   int64_t b;

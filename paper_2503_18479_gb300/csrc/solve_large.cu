@@ -137,8 +137,8 @@ __global__ void __launch_bounds__(kLargeThreads) solve_large_kernel(SolveArgs a,
                                                                      Cx<R>* __restrict__ scratch) {
   constexpr int NB = LargeCfg<R>::NB, CW = LargeCfg<R>::CW;
   constexpr int RG = kLargeThreads / CW;  // row groups of the trailing update
-  const int64_t sys = blockIdx.x;
-  if (sys >= n_sys) return;
+  if ((int64_t)blockIdx.x >= n_sys) return;
+  const int64_t sys = launch_sys(a, blockIdx.x);
   const SysInfo si = sys_info(a, sys);
   const int N = si.N;
   if (N <= min_ports) return;  // a register-resident kernel owns this system (CTA-uniform)
@@ -425,7 +425,7 @@ __global__ void __launch_bounds__(kLargeThreads) solve_large_kernel(SolveArgs a,
         a.I_out[2 * (ioff + r) + 1] = xk[r].y;
       }
     }
-    if (a.Bop != nullptr) {
+    if (a.Bop != nullptr && a.bop_off[si.s + 1] > a.bop_off[si.s]) {  // tensor-core structure
       // tensor-core operand pieces of I: rows 2 (b F_s + f) + {0: re, 1: im}, columns
       // N .. K_pad-1 zero; x = xh + xl, pieces bf16(rem), rem -= piece in FP32
       const int nkc = (N + kChunkK - 1) / kChunkK;

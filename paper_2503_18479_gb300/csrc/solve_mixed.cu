@@ -191,9 +191,10 @@ __global__ void __launch_bounds__(NM >= 64 ? NM : 128, NM >= 64 ? 5 : 1) solve_m
   const int grp = threadIdx.x / NM, r = threadIdx.x % NM;
   SmemV3<NM>& sm = reinterpret_cast<SmemV3<NM>*>(dsm)[grp];
 
-  const int64_t sys = (int64_t)blockIdx.x * G + grp;
-  const bool in_range = sys < n_sys;
-  SysInfo si = sys_info(a, in_range ? sys : 0);
+  const int64_t li = (int64_t)blockIdx.x * G + grp;
+  const bool in_range = li < n_sys;
+  const int64_t sys = in_range ? launch_sys(a, li) : 0;
+  SysInfo si = sys_info(a, sys);
   const bool valid = in_range && si.N <= NM;  // larger systems: solve_large.cu
   if (!valid) si.N = 0;
   const int N = si.N;
@@ -603,7 +604,7 @@ __global__ void __launch_bounds__(NM >= 64 ? NM : 128, NM >= 64 ? 5 : 1) solve_m
           a.I_out[2 * (ioff + r) + 1] = x.y;
         }
       }
-      if (valid && a.Bop != nullptr) {
+      if (valid && a.Bop != nullptr && a.bop_off[si.s + 1] > a.bop_off[si.s]) {
         // tensor-core operand pieces of I: rows 2 (b F_s + f) + {0: re, 1: im}; thread r
         // owns column r, columns N .. K_pad-1 are zero
         const int F = a.freq_off[si.s + 1] - a.freq_off[si.s];

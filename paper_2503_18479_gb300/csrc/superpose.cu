@@ -4,7 +4,7 @@
 //   plan_kernel          per-call tables: bases of the tensor-core operand of I, the
 //                        prefix of GEMM work units and the bases of the LU factor scratch
 //                        per structure
-//   superpose_fp64_kernel  FP64 SIMT (MTS_FP64): CTA = 128 points x 64 systems
+//   superpose_simt_kernel  SIMT: MTS_FP64, and structures with at most 16 systems
 //   The tensor-core kernel for MTS_MIXED / MTS_BF16 lives in superpose_tc.cu.
 #include <cuda_runtime.h>
 
@@ -16,112 +16,171 @@ namespace mts {
 __global__ void plan_kernel(int n_struct, int64_t n_cfg, const int32_t* __restrict__ port_off,
                             const int64_t* __restrict__ point_off,
                             const int32_t* __restrict__ freq_off, int npieces,
-                            int64_t* bop_off, int64_t* unit_off, int64_t* lu_off) {
+                            int64_t* bop_off, int64_t* unit_off, int64_t* lu_off,
+                            int64_t* simt_off) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  int64_t a = 0, u = 0, f = 0;
+  int64_t a = 0, u = 0, f = 0, v = 0;
   for (int s = 0; s < n_struct; ++s) {
     bop_off[s] = a;
     unit_off[s] = u;
     lu_off[s] = f;
+    simt_off[s] = v;
     int64_t N = port_off[s + 1] - port_off[s];
     int64_t P = point_off[s + 1] - point_off[s];
     int64_t F = freq_off[s + 1] - freq_off[s];
-    int64_t nn = (2 * n_cfg * F + kTileN - 1) / kTileN;
-    int64_t np = (P + kTileP - 1) / kTileP;
-    int64_t nkc = (N + kChunkK - 1) / kChunkK;
-    a += (int64_t)npieces * nn * nkc * kTileN * kChunkK;
-    u += np * nn;
+    if (use_tensor_path(npieces, n_cfg, F)) {
+      int64_t nn = (2 * n_cfg * F + kTileN - 1) / kTileN;
+      int64_t np = (P + kTileP - 1) / kTileP;
+      int64_t nkc = (N + kChunkK - 1) / kChunkK;
+      a += (int64_t)npieces * nn * nkc * kTileN * kChunkK;
+      u += np * nn;
+    } else {
+      v += (P + kSimtPts - 1) / kSimtPts * ((n_cfg * F + kSimtSys - 1) / kSimtSys);
+    }
     if (N > kRegMaxPorts) f += F * N * N;
   }
   bop_off[n_struct] = a;
   unit_off[n_struct] = u;
   lu_off[n_struct] = f;
+  simt_off[n_struct] = v;
 }
 
 cudaError_t launch_plan(const mts_problem* pb, int64_t n_cfg, int npieces, int64_t* bop_off,
-                        int64_t* unit_off, int64_t* lu_off, cudaStream_t st) {
+                        int64_t* unit_off, int64_t* lu_off, int64_t* simt_off, cudaStream_t st) {
   plan_kernel<<<1, 32, 0, st>>>(pb->n_struct, n_cfg, pb->port_off, pb->point_off, pb->freq_off,
-                                npieces, bop_off, unit_off, lu_off);
+                                npieces, bop_off, unit_off, lu_off, simt_off);
   note_launch();
   return cudaGetLastError();
 }
 
-// FP64 SIMT superposition. A unit is 128 points x 64 systems (the GEMM unit of 128 x 128
-// real columns); 512 threads: point = t % 128, 16 systems per thread. I tile staged in
-// shared memory in K chunks of 32 ports.
-constexpr int kSupSys = 64;
-constexpr int kSupK = 32;
+// SIMT superposition. A unit is 128 points x up to 16 systems of one structure; thread t owns
+// point t of the tile and accumulates its systems in registers. H arrives in K chunks staged
+// in shared memory (one coalesced read of the tile), the currents of the unit's systems in
+// the working precision beside it (k-major: the systems of one k are contiguous, read as
+// broadcasts). Used for MTS_FP64 (T = double, FP64 basis) and, in the other precisions, for
+// structures with at most 16 systems (T = float, FP32 basis; FP32 accumulation), where
+// tensor-core column tiles would be mostly padding and the work is a read of H.
+template <typename T>
+struct SimtCfg;
+template <>
+struct SimtCfg<float> {
+  static constexpr int KC = 64;
+  using C2 = float2;
+};
+template <>
+struct SimtCfg<double> {
+  static constexpr int KC = 32;
+  using C2 = double2;
+};
 
-__global__ void __launch_bounds__(512) superpose_fp64_kernel(SuperposeArgs a) {
-  __shared__ double2 sI[kSupSys][kSupK + 1];
-  int64_t unit = blockIdx.x;
-  int s = find_struct_i64(a.unit_off, a.n_struct, unit);
-  int N = a.port_off[s + 1] - a.port_off[s];
-  int64_t P = a.point_off[s + 1] - a.point_off[s];
-  int F = a.freq_off[s + 1] - a.freq_off[s];
-  int64_t nsys = a.n_cfg * F;
-  int64_t np = (P + kTileP - 1) / kTileP;
-  int64_t lu = unit - a.unit_off[s];
-  int64_t pt = lu % np, nt = lu / np;
-  int t = threadIdx.x;
-  int pl = t % kTileP, sg = t / kTileP;  // sg in 0..3
-  int64_t p = pt * kTileP + pl;
-  const double* H = static_cast<const double*>(a.H) + a.t.pn_off[s];
-  double2 acc[16];
+template <typename T>
+constexpr size_t simt_smem_bytes() {
+  return sizeof(T) * (size_t)kSimtPts * (SimtCfg<T>::KC + 1) +
+         sizeof(T) * 2 * (size_t)SimtCfg<T>::KC * kSimtSys;
+}
+
+template <typename T, int SC>
+__device__ inline void simt_accumulate(const T* __restrict__ hrow, const T* __restrict__ sI,
+                                       int kn, T (&ax)[kSimtSys], T (&ay)[kSimtSys]) {
+  for (int k = 0; k < kn; ++k) {
+    const T h = hrow[k];
+    const T* ik = sI + 2 * kSimtSys * k;
 #pragma unroll
-  for (int i = 0; i < 16; ++i) acc[i] = make_double2(0.0, 0.0);
-  for (int k0 = 0; k0 < N; k0 += kSupK) {
-    __syncthreads();
-    for (int e = t; e < kSupSys * kSupK; e += 512) {
-      int ls = e / kSupK, kk = e % kSupK;
-      int64_t sysl = nt * kSupSys + ls;  // local system index = b * F + f
-      double2 v = make_double2(0.0, 0.0);
-      if (sysl < nsys && k0 + kk < N) {
-        int64_t b = sysl / F;
-        int f = (int)(sysl - b * F);
-        const double* Ip = a.I + 2 * (b * a.sumFN + a.t.fn_off[s] + (int64_t)f * N + k0 + kk);
-        v = make_double2(Ip[0], Ip[1]);
-      }
-      sI[ls][kk] = v;
-    }
-    __syncthreads();
-    int kn = min(kSupK, N - k0);
-    if (p < P) {
-      for (int kk = 0; kk < kn; ++kk) {
-        double h = H[p * N + k0 + kk];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          double2 v = sI[sg * 16 + i][kk];
-          acc[i].x = fma(h, v.x, acc[i].x);
-          acc[i].y = fma(h, v.y, acc[i].y);
-        }
-      }
+    for (int i = 0; i < SC; ++i) {
+      ax[i] = fma(h, ik[2 * i], ax[i]);
+      ay[i] = fma(h, ik[2 * i + 1], ay[i]);
     }
   }
-  if (p < P) {
-    double2* out = static_cast<double2*>(a.B_out);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSimtPts) superpose_simt_kernel(SuperposeArgs a) {
+  constexpr int KC = SimtCfg<T>::KC;
+  using C2 = typename SimtCfg<T>::C2;
+  extern __shared__ __align__(16) unsigned char sm_simt[];
+  T* sH = reinterpret_cast<T*>(sm_simt);  // [kSimtPts][KC + 1]
+  T* sI = sH + kSimtPts * (KC + 1);       // [KC][kSimtSys][re, im]
+  const int64_t unit = blockIdx.x;
+  const int s = find_struct_i64(a.simt_off, a.n_struct, unit);
+  const int N = a.port_off[s + 1] - a.port_off[s];
+  const int64_t P = a.point_off[s + 1] - a.point_off[s];
+  const int F = a.freq_off[s + 1] - a.freq_off[s];
+  const int64_t nsys = a.n_cfg * F;
+  const int64_t np = (P + kSimtPts - 1) / kSimtPts;
+  const int64_t lu = unit - a.simt_off[s];
+  const int64_t pt = lu % np, sys0 = (lu / np) * kSimtSys;
+  const int nsv = (int)min((int64_t)kSimtSys, nsys - sys0);
+  const int t = threadIdx.x;
+  const int64_t p0 = pt * kSimtPts;
+  const T* H = static_cast<const T*>(a.H) + a.t.pn_off[s];
+  T ax[kSimtSys], ay[kSimtSys];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      int64_t sysl = nt * kSupSys + sg * 16 + i;
-      if (sysl < nsys) {
-        int64_t b = sysl / F;
-        int f = (int)(sysl - b * F);
-        out[b * a.sumFP + a.t.fp_off[s] + (int64_t)f * P + p] = acc[i];
-      }
+  for (int i = 0; i < kSimtSys; ++i) ax[i] = ay[i] = T(0);
+  for (int k0 = 0; k0 < N; k0 += KC) {
+    const int kn = min(KC, N - k0);
+    __syncthreads();
+    for (int e = t; e < kSimtPts * kn; e += kSimtPts) {
+      const int r = e / kn, c = e - r * kn;
+      const int64_t pr = p0 + r;
+      sH[r * (KC + 1) + c] = pr < P ? H[pr * N + k0 + c] : T(0);
     }
+    for (int e = t; e < kn * kSimtSys; e += kSimtPts) {
+      const int k = e / kSimtSys, i = e - k * kSimtSys;
+      T re = T(0), im = T(0);
+      if (i < nsv) {
+        const int64_t sl = sys0 + i, b = sl / F;
+        const int f = (int)(sl - b * F);
+        const double* Ip = a.I + 2 * (b * a.sumFN + a.t.fn_off[s] + (int64_t)f * N + k0 + k);
+        re = (T)Ip[0];
+        im = (T)Ip[1];
+      }
+      sI[2 * (k * kSimtSys + i)] = re;
+      sI[2 * (k * kSimtSys + i) + 1] = im;
+    }
+    __syncthreads();
+    const T* hrow = sH + t * (KC + 1);
+    if (nsv <= 4) simt_accumulate<T, 4>(hrow, sI, kn, ax, ay);
+    else if (nsv <= 8) simt_accumulate<T, 8>(hrow, sI, kn, ax, ay);
+    else simt_accumulate<T, 16>(hrow, sI, kn, ax, ay);
+  }
+  const int64_t p = p0 + t;
+  if (p < P) {
+    C2* out = static_cast<C2*>(a.B_out);
+    const int64_t fpo = a.t.fp_off[s];
+#pragma unroll
+    for (int i = 0; i < kSimtSys; ++i)
+      if (i < nsv) {
+        const int64_t sl = sys0 + i, b = sl / F;
+        const int f = (int)(sl - b * F);
+        C2 v;
+        v.x = ax[i];
+        v.y = ay[i];
+        out[b * a.sumFP + fpo + (int64_t)f * P + p] = v;
+      }
   }
 }
 
 cudaError_t launch_superpose_tc(const SuperposeArgs& a, mts_precision prec, cudaStream_t st);
 
+template <typename T>
+static cudaError_t launch_simt(const SuperposeArgs& a, cudaStream_t st) {
+  constexpr size_t sm = simt_smem_bytes<T>();
+  cudaError_t e = cudaFuncSetAttribute(superpose_simt_kernel<T>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  superpose_simt_kernel<T><<<(unsigned)a.total_simt, kSimtPts, sm, st>>>(a);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_superpose(const SuperposeArgs& a, mts_precision prec, cudaStream_t st) {
-  if (a.total_units == 0) return cudaSuccess;
-  if (prec == MTS_FP64) {
-    superpose_fp64_kernel<<<(unsigned)a.total_units, 512, 0, st>>>(a);
-    note_launch();
-    return cudaGetLastError();
+  if (a.total_units > 0) {
+    cudaError_t e = launch_superpose_tc(a, prec, st);
+    if (e != cudaSuccess) return e;
   }
-  return launch_superpose_tc(a, prec, st);
+  if (a.total_simt > 0)
+    return prec == MTS_FP64 ? launch_simt<double>(a, st) : launch_simt<float>(a, st);
+  return cudaSuccess;
 }
 
 }  // namespace mts
