@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--no-fp64-path", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--n-cfg", type=int, default=N_CFG, help="configurations per GPU (profiling runs)")
+    ap.add_argument("--other-workloads", default="loop,line",
+                    help="comma list of extra workloads timed after the headline (loop, line, "
+                         "ragged, 32x32; empty for none); reported under other_workloads")
     return ap.parse_args()
 
 
@@ -360,6 +363,7 @@ def run_ours(args, rank, world, local):
         "wall_s_timed_loop": t_wall,
         "status": {"code": code, "systems_flagged": n_bad},
         "fp64_path": fp64_path,
+        "other_workloads": other_workloads(args, dev, prec) if rank == 0 else None,
     }
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"], out["accuracy"] = cpu_baseline_and_accuracy(wl, sim, C, B, loss, grad_C, gl, tape, ev)
@@ -367,6 +371,71 @@ def run_ours(args, rank, world, local):
         tdist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out))
+
+
+def other_workloads(args, dev, prec):
+    """The same step (solve + objective + adjoint, superposition, gradient) on the other
+    synthetic workloads: configs/s, systems/s and field points/s at one GPU, CUDA events
+    over a few steps with the L2 flushed between them."""
+    import torch
+
+    from paper_2503_18479_gb300 import native as nv
+    from paper_2503_18479_gb300 import workloads as W
+    from paper_2503_18479_gb300.simulator import Simulator
+    makers = {
+        "loop": ("single_loop: circular 64-gon, 1 config, 101 freqs, 32x32 grid", lambda: W.single_loop(seed=0)),
+        "line": ("line_8x1: 8x1 square loops, 1024 configs, 201 freqs, 64x64 grid", lambda: W.line_8x1(seed=0)),
+        "ragged": ("ragged: 10,000 structures of 1..128 ports, 1-16 freqs, 64x64 grid each", lambda: W.ragged(seed=0)),
+        "32x32": ("array_32x32: 1024 ports, 256 configs, 4x512x512 grid", lambda: W.array_32x32(seed=0)),
+    }
+    res = {}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream()
+    for name in [x for x in args.other_workloads.split(",") if x]:
+        desc, make = makers[name]
+        wl = make()
+        if wl.target is None:  # timing only: a zero target costs the same work
+            wl.target = np.zeros(sum(s.n_freq * s.n_loss for s in wl.structures))
+        sim = Simulator(wl, prec, device=dev)
+        n = wl.n_cfg
+        C = torch.from_numpy(wl.C).to(dev)
+        ev = sim.make_eval(C, True)
+        tape = sim.alloc_tape(n)
+        B = torch.empty((n, sim.sumFP), dtype=sim.b_dtype, device=dev)
+        loss = torch.empty((n, sim.n_struct), dtype=torch.float64, device=dev)
+        g = torch.empty((n, sim.n_ports), dtype=torch.float64, device=dev)
+        gl = torch.ones((n, sim.n_struct), dtype=torch.float64, device=dev)
+
+        def step():
+            nv.mts_solve(sim.pb, sim.prec, sim.basis, ev, None, loss, tape)
+            nv.mts_superpose(sim.pb, sim.prec, sim.basis, ev, tape, B)
+            nv.mts_backward(sim.pb, sim.prec, sim.basis, ev, tape, None, gl, g)
+
+        for _ in range(3):
+            flush.fill_(1)
+            step()
+        torch.cuda.synchronize()
+        code, bad = sim.status(tape, n)
+        K = 10
+        ms = 0.0
+        for _ in range(K):
+            flush.fill_(1)
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(st)
+            step()
+            a1.record(st)
+            a1.synchronize()
+            ms += a0.elapsed_time(a1)
+        ms /= K
+        n_sys = n * sum(s.n_freq for s in wl.structures)
+        res[name] = {"workload": desc, "precision": prec, "ms_per_step": ms,
+                     "configs_per_s": n / (ms / 1e3), "systems_per_s": n_sys / (ms / 1e3),
+                     "field_points_per_s": n * sim.sumFP / (ms / 1e3), "steps": K,
+                     "status": {"code": code, "systems_flagged": bad}}
+        del sim, B, tape
+        torch.cuda.empty_cache()
+    return res
 
 
 def cpu_baseline_and_accuracy(wl, sim, C, B, loss, grad_C, gl, tape, ev):

@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(NM >= 128 ? NM : 128) solve_fp64_kernel(SolveA
   int pivstep = NM;  // step at which this row became the pivot
   for (int k = 0; k < NM; ++k) {
     double key = (pivstep < NM) ? -1.0 : cabs2(A[r * P + k]);
+    if (!(key >= -1.0)) key = 0.0;  // NaN: still a candidate, never below a chosen row
     int idx = r;
     if (NM <= 32) {
       argmax_shfl_d(key, idx, NM);

@@ -1,9 +1,10 @@
 // solve_large.cu -- (b) port solve, (d) objective and (adj) adjoint for structures with more
 // ports than the register-resident kernels hold (64 < N <= 1024).
 //
-// One system (configuration b, frequency g) per 256-thread CTA. The matrix
-// A = diag(R) + j w M + diag(1/(j w C)) (paper Eq. 2, 11) is assembled into the tape's
-// factor scratch (global memory) and factorised there by a blocked right-looking LU with
+// One system (configuration b, frequency g) per CTA of 128 (N <= 128) or 256 threads. The
+// matrix A = diag(R) + j w M + diag(1/(j w C)) (paper Eq. 2, 11) is assembled into the tape's
+// factor scratch (global memory, L2-resident while in use) and factorised there by a blocked
+// right-looking LU with
 // partial pivoting, without moving rows (the pivot of column k is the largest |a_rk| among
 // rows not chosen yet; chosen rows keep U in place, the others keep their multipliers):
 //   panel   the NB columns [c0, c0+NB) of every row, staged column-major in shared memory,
@@ -29,8 +30,7 @@
 
 namespace mts {
 
-constexpr int kLargeThreads = 256;
-constexpr int kLargeWarps = kLargeThreads / 32;
+constexpr int kLargeMaxWarps = 8;  // CTAs of 128 (N <= 128) or 256 threads
 
 template <typename R>
 struct Cx {
@@ -60,8 +60,8 @@ struct LargeCfg<double> {
 };
 
 struct BlockRed {
-  double key[kLargeWarps];
-  int idx[kLargeWarps];
+  double key[kLargeMaxWarps];
+  int idx[kLargeMaxWarps];
 };
 
 // Shared-memory carve-up for systems of up to n ports (host and device agree on it).
@@ -89,7 +89,9 @@ struct LargeSmem {
   }
 };
 
-// block-wide arg-max of (key, idx), ties to the smaller index; every thread gets idx.
+// block-wide arg-max of (key, idx) over W warps, ties to the smaller index; every thread
+// gets idx.
+template <int W>
 __device__ inline int block_argmax(double key, int idx, BlockRed* red) {
   argmax_shfl_d(key, idx, 32);
   __syncthreads();
@@ -101,7 +103,7 @@ __device__ inline int block_argmax(double key, int idx, BlockRed* red) {
   double kb = red->key[0];
   int ib = red->idx[0];
 #pragma unroll
-  for (int q = 1; q < kLargeWarps; ++q)
+  for (int q = 1; q < W; ++q)
     if (red->key[q] > kb || (red->key[q] == kb && red->idx[q] < ib)) {
       kb = red->key[q];
       ib = red->idx[q];
@@ -109,6 +111,7 @@ __device__ inline int block_argmax(double key, int idx, BlockRed* red) {
   return ib;
 }
 
+template <int W>
 __device__ inline double block_max(double v, BlockRed* red) {
   for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
   __syncthreads();
@@ -116,10 +119,11 @@ __device__ inline double block_max(double v, BlockRed* red) {
   __syncthreads();
   double m = red->key[0];
 #pragma unroll
-  for (int q = 1; q < kLargeWarps; ++q) m = fmax(m, red->key[q]);
+  for (int q = 1; q < W; ++q) m = fmax(m, red->key[q]);
   return m;
 }
 
+template <int W>
 __device__ inline double block_sum(double v, BlockRed* red) {
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
   __syncthreads();
@@ -127,16 +131,18 @@ __device__ inline double block_sum(double v, BlockRed* red) {
   __syncthreads();
   double s = 0.0;
 #pragma unroll
-  for (int q = 0; q < kLargeWarps; ++q) s += red->key[q];
+  for (int q = 0; q < W; ++q) s += red->key[q];
   return s;
 }
 
-template <typename R>
-__global__ void __launch_bounds__(kLargeThreads) solve_large_kernel(SolveArgs a, int64_t n_sys,
+// T threads per CTA (one system): 128 for N <= 128, so that more systems share an SM, else 256.
+template <typename R, int T>
+__global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_sys,
                                                                      int min_ports, int smem_n,
                                                                      Cx<R>* __restrict__ scratch) {
   constexpr int NB = LargeCfg<R>::NB, CW = LargeCfg<R>::CW;
-  constexpr int RG = kLargeThreads / CW;  // row groups of the trailing update
+  constexpr int W = T / 32;
+  constexpr int RG = T / CW;  // row groups of the trailing update
   if ((int64_t)blockIdx.x >= n_sys) return;
   const int64_t sys = launch_sys(a, blockIdx.x);
   const SysInfo si = sys_info(a, sys);
@@ -167,23 +173,36 @@ __global__ void __launch_bounds__(kLargeThreads) solve_large_kernel(SolveArgs a,
   const int F = a.freq_off[si.s + 1] - a.freq_off[si.s];
   Cx<R>* A = scratch + si.b * a.lu_off[a.n_struct] + a.lu_off[si.s] + (int64_t)si.f * N * N;
 
-  // ---- assemble A (Eq. 2, 11) ----
-  for (int r = 0; r < N; ++r)
-    for (int j = tid; j < N; j += kLargeThreads) {
-      double im = w * M[(int64_t)r * N + j], re = 0.0;
-      if (j == r) {
-        re = Rk[r];
-        im -= 1.0 / (w * Cb[r]);
-      }
-      A[(int64_t)r * N + j] = {(R)re, (R)im};
+  // ---- assemble A (Eq. 2, 11), four independent loads of M in flight per thread ----
+  const int NN = N * N;
+  for (int e0 = 0; e0 < NN; e0 += 4 * T) {
+    double mv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = e0 + q * T + tid;
+      mv[q] = e < NN ? M[e] : 0.0;
     }
-  for (int r = tid; r < N; r += kLargeThreads) pivstep[r] = N;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = e0 + q * T + tid;
+      if (e < NN) {
+        const int r = e / N, j = e - r * N;
+        double im = w * mv[q], re = 0.0;
+        if (j == r) {
+          re = Rk[r];
+          im -= 1.0 / (w * Cb[r]);
+        }
+        A[e] = {(R)re, (R)im};
+      }
+    }
+  }
+  for (int r = tid; r < N; r += T) pivstep[r] = N;
   __syncthreads();
 
   // ---- blocked LU with partial pivoting ----
   for (int c0 = 0; c0 < N; c0 += NB) {
     const int nb = min(NB, N - c0);
-    for (int e = tid; e < N * NB; e += kLargeThreads) {
+    for (int e = tid; e < N * NB; e += T) {
       const int r = e / NB, j = e - r * NB;
       Cx<R> v = {0, 0};
       if (j < nb && pivstep[r] == N) v = A[(int64_t)r * N + c0 + j];
@@ -193,7 +212,7 @@ __global__ void __launch_bounds__(kLargeThreads) solve_large_kernel(SolveArgs a,
     for (int kk = 0; kk < nb; ++kk) {
       double best = -1.0;
       int bi = N;
-      for (int r = tid; r < N; r += kLargeThreads)
+      for (int r = tid; r < N; r += T)
         if (pivstep[r] == N) {
           const Cx<R> v = pan[kk * NP + r];
           double m = (double)v.x * v.x + (double)v.y * v.y;
@@ -203,9 +222,9 @@ __global__ void __launch_bounds__(kLargeThreads) solve_large_kernel(SolveArgs a,
             bi = r;
           }
         }
-      const int p = block_argmax(best, bi, red);
+      const int p = block_argmax<W>(best, bi, red);
       const Cx<R> piv = pan[kk * NP + p];
-      for (int r = tid; r < N; r += kLargeThreads)
+      for (int r = tid; r < N; r += T)
         if (pivstep[r] == N && r != p) {
           const Cx<R> l = cx_div(pan[kk * NP + r], piv);
           pan[kk * NP + r] = l;
@@ -219,7 +238,7 @@ __global__ void __launch_bounds__(kLargeThreads) solve_large_kernel(SolveArgs a,
       __syncthreads();
     }
     // panel back to the matrix (rows chosen in this panel or later)
-    for (int e = tid; e < N * NB; e += kLargeThreads) {
+    for (int e = tid; e < N * NB; e += T) {
       const int r = e / NB, j = e - r * NB;
       if (j < nb && pivstep[r] >= c0) A[(int64_t)r * N + c0 + j] = pan[j * NP + r];
     }
@@ -251,17 +270,18 @@ __global__ void __launch_bounds__(kLargeThreads) solve_large_kernel(SolveArgs a,
 #pragma unroll
         for (int m = 0; m < NB; ++m) uu[m] = u12[m * CW + col];
         if (j < N) {
+          constexpr int RF = 8;  // rows in flight: independent loads per thread
           int r = rg;
-          for (; r + 3 * RG < N; r += 4 * RG) {  // four rows in flight
-            bool act[4];
-            Cx<R> v[4];
+          for (; r + (RF - 1) * RG < N; r += RF * RG) {
+            bool act[RF];
+            Cx<R> v[RF];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < RF; ++q) {
               act[q] = pivstep[r + q * RG] == N;
               v[q] = act[q] ? A[(int64_t)(r + q * RG) * N + j] : Cx<R>{0, 0};
             }
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
+            for (int q = 0; q < RF; ++q)
               if (act[q]) {
 #pragma unroll
                 for (int m = 0; m < NB; ++m) cx_fnma(v[q], pan[m * NP + r + q * RG], uu[m]);
@@ -284,7 +304,7 @@ __global__ void __launch_bounds__(kLargeThreads) solve_large_kernel(SolveArgs a,
   // ---- solve A x = rhs (FP64 rhs in shared memory) into wv (by row) with the factors;
   // the unknown of column k ends in wv[order[k]] ----
   auto lu_solve = [&]() {
-    for (int r = tid; r < N; r += kLargeThreads) wv[r] = {(R)rhs[r].x, (R)rhs[r].y};
+    for (int r = tid; r < N; r += T) wv[r] = {(R)rhs[r].x, (R)rhs[r].y};
     __syncthreads();
     for (int c0 = 0; c0 < N; c0 += NB) {  // forward: L y = P rhs
       const int nb = min(NB, N - c0);
@@ -309,7 +329,7 @@ __global__ void __launch_bounds__(kLargeThreads) solve_large_kernel(SolveArgs a,
         if (lane < nb) wv[pi] = wi;
       }
       __syncthreads();
-      for (int r = tid; r < N; r += kLargeThreads)
+      for (int r = tid; r < N; r += T)
         if (pivstep[r] >= c0 + nb) {
           Cx<R> v = wv[r];
 #pragma unroll
@@ -344,7 +364,7 @@ __global__ void __launch_bounds__(kLargeThreads) solve_large_kernel(SolveArgs a,
         if (lane < nb) wv[pi] = wi;
       }
       __syncthreads();
-      for (int r = tid; r < N; r += kLargeThreads)
+      for (int r = tid; r < N; r += T)
         if (pivstep[r] < c0) {
           Cx<R> v = wv[r];
 #pragma unroll
@@ -358,21 +378,22 @@ __global__ void __launch_bounds__(kLargeThreads) solve_large_kernel(SolveArgs a,
 
   // refined solve of A x = rhs into xk (rhs is kept); returns whether it converged
   auto refined = [&]() -> bool {
-    for (int r = tid; r < N; r += kLargeThreads) sv[r] = rhs[r];
+    for (int r = tid; r < N; r += T) sv[r] = rhs[r];
     lu_solve();
     double xm = 0.0;
-    for (int k = tid; k < N; k += kLargeThreads) {
+    for (int k = tid; k < N; k += T) {
       const Cx<R> v = wv[order[k]];
       xk[k] = {(double)v.x, (double)v.y};
       xm = fmax(xm, fabs((double)v.x) + fabs((double)v.y));
     }
     bool conv = true;
     if (sizeof(R) < 8) {
-      double dprev = block_max(xm, red);  // its barriers also publish xk
+      double dprev = block_max<W>(xm, red);  // its barriers also publish xk
       conv = a.max_refine == 0;
       for (int it = 0; it < a.max_refine; ++it) {
-        for (int r = tid; r < N; r += kLargeThreads) {  // FP64 residual sv - A xk
+        for (int r = tid; r < N; r += T) {  // FP64 residual sv - A xk
           double sx = 0.0, sy = 0.0;
+#pragma unroll 8
           for (int j = 0; j < N; ++j) {
             const double m = M[(int64_t)j * N + r];  // M symmetric: column r, coalesced
             sx = fma(m, xk[j].x, sx);
@@ -386,22 +407,22 @@ __global__ void __launch_bounds__(kLargeThreads) solve_large_kernel(SolveArgs a,
         __syncthreads();
         lu_solve();
         double dm = 0.0, xm2 = 0.0;
-        for (int k = tid; k < N; k += kLargeThreads) {
+        for (int k = tid; k < N; k += T) {
           const Cx<R> d = wv[order[k]];
           xk[k].x += (double)d.x;
           xk[k].y += (double)d.y;
           dm = fmax(dm, fabs((double)d.x) + fabs((double)d.y));
           xm2 = fmax(xm2, fabs(xk[k].x) + fabs(xk[k].y));
         }
-        dm = block_max(dm, red);
-        xm2 = block_max(xm2, red);
+        dm = block_max<W>(dm, red);
+        xm2 = block_max<W>(xm2, red);
         const double est = dm * fmin(1.0, dm / fmax(dprev, 1e-300));
         conv = conv || est <= a.tol * xm2;
         const bool stop = conv || !(dm <= 0.5 * dprev);
         dprev = dm;
         if (stop) break;
       }
-      for (int r = tid; r < N; r += kLargeThreads) rhs[r] = sv[r];
+      for (int r = tid; r < N; r += T) rhs[r] = sv[r];
     }
     __syncthreads();
     return conv;
@@ -410,13 +431,13 @@ __global__ void __launch_bounds__(kLargeThreads) solve_large_kernel(SolveArgs a,
   const int64_t ioff = si.b * a.sumFN + a.t.fn_off[si.s] + (int64_t)si.f * N;
   bool conv_all = true;
   if (!bwd) {
-    for (int r = tid; r < N; r += kLargeThreads) {
+    for (int r = tid; r < N; r += T) {
       const double* Vp = a.V + 2 * (a.t.fn_off[si.s] + (int64_t)si.f * N + r);
       rhs[r] = {Vp[0], Vp[1]};
     }
     __syncthreads();
     conv_all = refined();
-    for (int r = tid; r < N; r += kLargeThreads) {
+    for (int r = tid; r < N; r += T) {
       xc[r] = xk[r];
       a.I[2 * (ioff + r)] = xk[r].x;
       a.I[2 * (ioff + r) + 1] = xk[r].y;
@@ -432,7 +453,7 @@ __global__ void __launch_bounds__(kLargeThreads) solve_large_kernel(SolveArgs a,
       const int64_t ntile = (2 * a.n_cfg * F + kTileN - 1) / kTileN;
       char* base = reinterpret_cast<char*>(a.Bop + a.bop_off[si.s]);
       const size_t tile_bytes = (size_t)kTileN * kChunkK * 2;
-      for (int kg = tid; kg < nkc * kChunkK; kg += kLargeThreads) {
+      for (int kg = tid; kg < nkc * kChunkK; kg += T) {
         const int kc = kg / kChunkK, kk = kg % kChunkK;
         for (int c = 0; c < 2; ++c) {
           const int64_t n = 2 * (si.b * F + si.f) + c;
@@ -452,7 +473,7 @@ __global__ void __launch_bounds__(kLargeThreads) solve_large_kernel(SolveArgs a,
       }
     }
   } else {
-    for (int r = tid; r < N; r += kLargeThreads) xc[r] = {a.I[2 * (ioff + r)], a.I[2 * (ioff + r) + 1]};
+    for (int r = tid; r < N; r += T) xc[r] = {a.I[2 * (ioff + r)], a.I[2 * (ioff + r) + 1]};
   }
   __syncthreads();
 
@@ -467,12 +488,13 @@ __global__ void __launch_bounds__(kLargeThreads) solve_large_kernel(SolveArgs a,
                          (a.t.fl_off[si.s] + (int64_t)si.f * Ls) * tw;
       cd* Gs = reinterpret_cast<cd*>(dsm + L.pan);  // the panel is free after the LU
       double lsum = 0.0;
-      for (int r = tid; r < N; r += kLargeThreads) rhs[r] = {0.0, 0.0};
-      for (int c0 = 0; c0 < Ls; c0 += kLargeThreads) {
+      for (int r = tid; r < N; r += T) rhs[r] = {0.0, 0.0};
+      for (int c0 = 0; c0 < Ls; c0 += T) {
         const int l = c0 + tid;
         cd Gl = {0.0, 0.0};
         if (l < Ls) {
           double bx = 0.0, by = 0.0;
+#pragma unroll 8
           for (int k = 0; k < N; ++k) {
             const double h = Hl[(int64_t)l * N + k];
             bx = fma(h, xc[k].x, bx);
@@ -482,9 +504,10 @@ __global__ void __launch_bounds__(kLargeThreads) solve_large_kernel(SolveArgs a,
         }
         Gs[tid] = {Gl.x, -Gl.y};  // conj(G)
         __syncthreads();
-        const int lc = min(kLargeThreads, Ls - c0);
-        for (int r = tid; r < N; r += kLargeThreads) {
+        const int lc = min(T, Ls - c0);
+        for (int r = tid; r < N; r += T) {
           double ux = rhs[r].x, uy = rhs[r].y;
+#pragma unroll 8
           for (int q = 0; q < lc; ++q) {
             const double h = Hl[(int64_t)(c0 + q) * N + r];
             ux = fma(h, Gs[q].x, ux);
@@ -494,50 +517,56 @@ __global__ void __launch_bounds__(kLargeThreads) solve_large_kernel(SolveArgs a,
         }
         __syncthreads();
       }
-      const double tot = block_sum(lsum, red);
+      const double tot = block_sum<W>(lsum, red);
       if (tid == 0) a.loss_part[sys] = tot;
     } else {
-      for (int r = tid; r < N; r += kLargeThreads)
+      for (int r = tid; r < N; r += T)
         rhs[r] = {a.rhs_in[2 * (ioff + r)], a.rhs_in[2 * (ioff + r) + 1]};
     }
     __syncthreads();
     conv_all = refined() && conv_all;
-    for (int r = tid; r < N; r += kLargeThreads) {
+    for (int r = tid; r < N; r += T) {
       const cd mu = xk[r], x = xc[r];
       a.grad_part[ioff + r] = (mu.x * x.y + mu.y * x.x) / (w * Cb[r] * Cb[r]);
     }
   }
   double bad = 0.0;
-  for (int r = tid; r < N; r += kLargeThreads)
+  for (int r = tid; r < N; r += T)
     if (!(isfinite(xc[r].x) && isfinite(xc[r].y) && isfinite(xk[r].x) && isfinite(xk[r].y)))
       bad = 1.0;
-  bad = block_max(bad, red);
+  bad = block_max<W>(bad, red);
   if (tid == 0 && !bwd) a.status[sys] = bad > 0.0 ? 2 : (conv_all ? 0 : 1);
 }
+
+// CTA size for a class whose largest system has max_ports ports
+static int large_threads(int max_ports) { return max_ports <= 128 ? 128 : 256; }
 
 size_t large_solve_smem(mts_precision prec, int max_ports) {
   return prec == MTS_FP64 ? LargeSmem<double>(max_ports).bytes : LargeSmem<float>(max_ports).bytes;
 }
 
+template <typename R, int T>
+static cudaError_t launch_large(const SolveArgs& a, int64_t n_sys, int min_ports, int max_ports,
+                                void* scratch, cudaStream_t st) {
+  const size_t sm = LargeSmem<R>(max_ports).bytes;
+  cudaError_t e = cudaFuncSetAttribute(solve_large_kernel<R, T>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  solve_large_kernel<R, T><<<(unsigned)n_sys, T, sm, st>>>(a, n_sys, min_ports, max_ports,
+                                                           static_cast<Cx<R>*>(scratch));
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_solve_large(const SolveArgs& a, mts_precision prec, int64_t n_sys, int min_ports,
                                int max_ports, void* scratch, cudaStream_t st) {
   if (n_sys == 0) return cudaSuccess;
-  const size_t sm = large_solve_smem(prec, max_ports);
-  if (prec == MTS_FP64) {
-    cudaError_t e = cudaFuncSetAttribute(solve_large_kernel<double>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    solve_large_kernel<double><<<(unsigned)n_sys, kLargeThreads, sm, st>>>(
-        a, n_sys, min_ports, max_ports, static_cast<Cx<double>*>(scratch));
-  } else {
-    cudaError_t e = cudaFuncSetAttribute(solve_large_kernel<float>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    solve_large_kernel<float><<<(unsigned)n_sys, kLargeThreads, sm, st>>>(
-        a, n_sys, min_ports, max_ports, static_cast<Cx<float>*>(scratch));
-  }
-  note_launch();
-  return cudaGetLastError();
+  const bool small = large_threads(max_ports) == 128;
+  if (prec == MTS_FP64)
+    return small ? launch_large<double, 128>(a, n_sys, min_ports, max_ports, scratch, st)
+                 : launch_large<double, 256>(a, n_sys, min_ports, max_ports, scratch, st);
+  return small ? launch_large<float, 128>(a, n_sys, min_ports, max_ports, scratch, st)
+               : launch_large<float, 256>(a, n_sys, min_ports, max_ports, scratch, st);
 }
 
 }  // namespace mts

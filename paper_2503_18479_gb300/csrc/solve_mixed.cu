@@ -141,7 +141,7 @@ __device__ __forceinline__ void cma(float2& c, float2 a, float2 b) {
   c.y = fmaf(a.x, b.y, fmaf(a.y, b.x, c.y));
 }
 __device__ __forceinline__ float2 crecip(float2 a) {
-  float inv = 1.0f / (a.x * a.x + a.y * a.y);
+  const float inv = __frcp_rn(a.x * a.x + a.y * a.y);  // no division slow path
   return make_float2(a.x * inv, -a.y * inv);
 }
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
@@ -684,7 +684,8 @@ __global__ void __launch_bounds__(NM >= 64 ? NM : 128, NM >= 64 ? 5 : 1) solve_m
       }
     } else {
       const cd mu = xk;
-      if (valid && real_row) a.grad_part[ioff + r] = (mu.x * x.y + mu.y * x.x) / (w * Cr * Cr);
+      // Im(mu x)/(w C^2) = Im(mu x) w (1/(w C))^2, without a second division
+      if (valid && real_row) a.grad_part[ioff + r] = (mu.x * x.y + mu.y * x.x) * w * (Dr.y * Dr.y);
     }
   }
   const float fb = gmax<NM>(bad ? 2.0f : (conv_all ? 0.0f : 1.0f), sm, r);

@@ -114,3 +114,19 @@ def small_loop(n_cfg=16, n_freq=11, grid=16, seed=0):
 
 def small_ragged(n_struct=12, seed=3, grid=12, max_freq=4, ports=(1, 8, 16, 32, 64)):
     return W.ragged(seed=seed, n_struct=n_struct, grid=grid, max_freq=max_freq, port_choices=ports)
+
+
+def small_rect(nx, ny, n_cfg=20, n_freq=2, grid=10, seed=0):
+    """An nx x ny array of the standard square cells (any port count), grid at z = 20 mm,
+    loss points above the cell centres, random targets."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    loops = W.square_array(nx, ny)
+    omega = 2 * np.pi * np.linspace(60e6, 68e6, n_freq)
+    hx, hy = (nx + 1) * 0.055 / 2.0, (ny + 1) * 0.055 / 2.0
+    pts = W._concat_points(W.grid_plane(grid, hx, 0.020, half_span_y=hy),
+                           W._cell_centre_points(nx, ny, 0.055, 0.040))
+    loss_idx = np.arange(grid * grid, grid * grid + nx * ny)
+    st = W._structure_from(loops, pts, omega, 0.1, loss_idx, label=f"rect_{nx}x{ny}")
+    C = rng.uniform(20e-12, 200e-12, size=(n_cfg, nx * ny))
+    target = rng.standard_normal(n_freq * nx * ny) * 1e-6
+    return W.Workload(f"rect_{nx}x{ny}", [st], C, 0.001, target=target, meta=dict(seed=seed))

@@ -8,7 +8,8 @@ import pytest
 import torch
 
 from helpers import (apply_target_rule, cosine, oracle_reference, rel, small_8x8, small_line,
-                     small_loop, small_ragged, split_B, split_I, split_ports, structure_basis)
+                     small_loop, small_ragged, small_rect, split_B, split_I, split_ports,
+                     structure_basis)
 from paper_2503_18479_gb300 import build_lib
 from paper_2503_18479_gb300 import workloads as W
 
@@ -44,6 +45,8 @@ _CASES = {
     # configurations take the tensor-core superposition, 3 the SIMT one
     "32x32": lambda: W.array_32x32(seed=2, n_cfg=20, grid=12, planes=(0.02,), seg_per_side=2),
     "32x32few": lambda: W.array_32x32(seed=3, n_cfg=3, grid=12, planes=(0.02,), seg_per_side=2),
+    # 80 ports: the large-system kernel with the matrix in shared memory in FP64 as well
+    "10x8": lambda: small_rect(10, 8, n_cfg=20, n_freq=2, grid=10, seed=4),
 }
 _cache = {}
 
