@@ -70,7 +70,7 @@ def parse():
     ap.add_argument("--no-fp64-path", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--n-cfg", type=int, default=N_CFG, help="configurations per GPU (profiling runs)")
-    ap.add_argument("--other-workloads", default="loop,line",
+    ap.add_argument("--other-workloads", default="loop,line,fit",
                     help="comma list of extra workloads timed after the headline (loop, line, "
                          "ragged, 32x32; empty for none); reported under other_workloads")
     return ap.parse_args()
@@ -387,12 +387,17 @@ def other_workloads(args, dev, prec):
         "line": ("line_8x1: 8x1 square loops, 1024 configs, 201 freqs, 64x64 grid", lambda: W.line_8x1(seed=0)),
         "ragged": ("ragged: 10,000 structures of 1..128 ports, 1-16 freqs, 64x64 grid each", lambda: W.ragged(seed=0)),
         "32x32": ("array_32x32: 1024 ports, 256 configs, 4x512x512 grid", lambda: W.array_32x32(seed=0)),
+        "fit": ("loop_sweep: Adam fits (lr 1e-13) of 100 initial C x 100 target fields on the "
+                "single loop at 63.6 MHz, 200 epochs replayed from one CUDA graph", None),
     }
     res = {}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     st = torch.cuda.current_stream()
     for name in [x for x in args.other_workloads.split(",") if x]:
         desc, make = makers[name]
+        if name == "fit":
+            res[name] = fit_sweep(desc, dev, prec)
+            continue
         wl = make()
         if wl.target is None:  # timing only: a zero target costs the same work
             wl.target = np.zeros(sum(s.n_freq * s.n_loss for s in wl.structures))
@@ -436,6 +441,38 @@ def other_workloads(args, dev, prec):
         del sim, B, tape
         torch.cuda.empty_cache()
     return res
+
+
+def fit_sweep(desc, dev, prec, epochs=200):
+    """The optimisation loop on the initialisation sweep: fit-epochs per second."""
+    import torch
+
+    from paper_2503_18479_gb300 import workloads as W
+    from paper_2503_18479_gb300.optimize import AdamFit
+    from paper_2503_18479_gb300.simulator import Simulator
+    wl = W.loop_sweep()
+    st = wl.structures[0]
+    # targets: |Bz| at the loss points for the target capacitances (forward map on the GPU)
+    sim0 = Simulator(wl, prec, device=dev)
+    Ct = torch.from_numpy(wl.target_rule[1]).to(dev)
+    B = sim0.forward(Ct, want_B=True, want_loss=False)["B"]
+    t = B.reshape(wl.n_cfg, st.n_freq, st.n_points)[:, :, torch.as_tensor(st.loss_idx, device=dev)].abs()
+    sim = Simulator(wl, prec, device=dev, target=t.reshape(-1).double().cpu().numpy(), target_per_cfg=True)
+    fit = AdamFit(sim, torch.from_numpy(wl.C), lr=1e-13, max_epochs=epochs + 2)
+    fit.run(2)  # warm-up: one eager epoch, the graph capture and one replay
+    torch.cuda.synchronize()
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record()
+    fit.run(epochs)
+    a1.record()
+    a1.synchronize()
+    ms = a0.elapsed_time(a1)
+    h = fit.history[: epochs + 2].cpu().numpy()[:, :, 0]
+    improved = float(((h[-1] < 1e-2 * h[0]) | (h[0] == 0)).mean())
+    return {"workload": desc, "precision": prec, "fits": wl.n_cfg, "epochs": epochs,
+            "ms": ms, "fit_epochs_per_s": wl.n_cfg * epochs / (ms / 1e3),
+            "share_of_fits_loss_down_100x": improved}
 
 
 def cpu_baseline_and_accuracy(wl, sim, C, B, loss, grad_C, gl, tape, ev):

@@ -258,6 +258,45 @@ mts_status mts_solve_static(const mts_problem* pb, mts_precision prec, const voi
                             const mts_eval* ev, double* I_out, double* loss_out,
                             double* dloss_dC_out, mts_stream stream);
 
+/* ---------------------------------------------------------------------------------
+ * Optimisation loop (paper Sec. III-C: the capacitances are fitted by gradient descent with
+ * Adam, at most 2000 epochs, learning rate 1e-13 for values of order 1e-12 F; Sec. V-B:
+ * clipping to the tuning range, or a bounded tanh projection, keeps them realisable).
+ *
+ * mts_adam_step applies one Adam update (Kingma and Ba; the update order of PyTorch's Adam
+ * without weight decay) to n parameters, with the step counter t in device memory so that
+ * an epoch (mts_solve, mts_backward, mts_adam_step) can be captured once in a CUDA graph and
+ * replayed:
+ *   t  = *step + 1;  m = b1 m + (1 - b1) g;  v = b2 v + (1 - b2) g^2
+ *   th = th - (lr / (1 - b1^t)) m / (sqrt(v) / sqrt(1 - b2^t) + eps);  *step = t
+ * MTS_PROJ_NONE : th = C (device [n]), g = grad_C.
+ * MTS_PROJ_CLIP : th = C, and C is clipped to [c_min, c_max] after the update.
+ * MTS_PROJ_TANH : th = u (device [n], unconstrained), C = c_mid + c_half tanh(u) with
+ *                 c_mid = (c_max + c_min)/2, c_half = (c_max - c_min)/2, and
+ *                 g = grad_C c_half (1 - tanh(u)^2); C is rewritten from u after the update.
+ * m, v: device [n] moment estimates (zero them before the first step); step: device int64
+ * (zero before the first step). If loss_history is not NULL, the n_loss values of `loss`
+ * (device; the objective the gradient came from) are copied to loss_history[(t-1) n_loss ..]
+ * while t <= history_len. Returns MTS_EINVAL (nothing launched) for n < 0, a NULL buffer
+ * the mode needs, lr or eps not finite and >= 0, betas outside [0, 1), or c_min >= c_max in
+ * a bounded mode.
+ * --------------------------------------------------------------------------------- */
+typedef enum { MTS_PROJ_NONE = 0, MTS_PROJ_CLIP = 1, MTS_PROJ_TANH = 2 } mts_projection;
+
+typedef struct mts_adam {
+  double lr;      /* learning rate (the paper: 1e-13) */
+  double beta1;   /* 0.9 */
+  double beta2;   /* 0.999 */
+  double eps;     /* 1e-8 */
+  int32_t projection; /* mts_projection */
+  double c_min, c_max; /* tuning range for MTS_PROJ_CLIP and MTS_PROJ_TANH, farad */
+} mts_adam;
+
+mts_status mts_adam_step(int64_t n, const mts_adam* opt, double* C, double* u,
+                         const double* grad_C, double* m, double* v, int64_t* step,
+                         const double* loss, int64_t n_loss, double* loss_history,
+                         int64_t history_len, mts_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,7 +30,8 @@ ProblemSums problem_sums(const mts_problem* pb, mts_precision prec) {
     ps.cls_count[c] += F;
     if (N > ps.cls_max_ports[c]) ps.cls_max_ports[c] = (int)N;
     ps.sumNN += N * N;
-    ps.sumPN += P * N;
+    ps.sumPN += round_up(P * N, kHAlign);
+    ps.sumPNraw += P * N;
     ps.sumLN += L * N;
     ps.sumFN += F * N;
     ps.sumFP += F * P;
@@ -46,6 +47,7 @@ TableLayout table_layout(int n_struct, int n_freq) {
   size_t arr = align256(sizeof(int64_t) * (size_t)(n_struct + 1));
   t.nn_off = o; o += arr;
   t.pn_off = o; o += arr;
+  t.pnr_off = o; o += arr;
   t.ln_off = o; o += arr;
   t.fn_off = o; o += arr;
   t.fp_off = o; o += arr;
@@ -498,6 +500,26 @@ mts_status mts_tape_status(const mts_problem* pb, int64_t n_cfg, mts_precision p
   if (n_bad) *n_bad = h[1];
   if (h[0] != 0) return MTS_ECUDA;  // a kernel gave up on a bounded wait
   return h[1] ? MTS_ENOCONV : MTS_OK;
+}
+
+mts_status mts_adam_step(int64_t n, const mts_adam* opt, double* C, double* u,
+                         const double* grad_C, double* m, double* v, int64_t* step,
+                         const double* loss, int64_t n_loss, double* loss_history,
+                         int64_t history_len, mts_stream stream) {
+  if (n < 0 || !opt || n_loss < 0 || history_len < 0) return MTS_EINVAL;
+  const mts_adam& o = *opt;
+  if (!(std::isfinite(o.lr) && o.lr >= 0.0) || !(std::isfinite(o.eps) && o.eps >= 0.0))
+    return MTS_EINVAL;
+  if (!(o.beta1 >= 0.0 && o.beta1 < 1.0) || !(o.beta2 >= 0.0 && o.beta2 < 1.0)) return MTS_EINVAL;
+  if (o.projection != MTS_PROJ_NONE && o.projection != MTS_PROJ_CLIP && o.projection != MTS_PROJ_TANH)
+    return MTS_EINVAL;
+  if (o.projection != MTS_PROJ_NONE && !(o.c_min < o.c_max && std::isfinite(o.c_min) && std::isfinite(o.c_max)))
+    return MTS_EINVAL;
+  if (!step || (n > 0 && (!C || !grad_C || !m || !v))) return MTS_EINVAL;
+  if (n > 0 && o.projection == MTS_PROJ_TANH && !u) return MTS_EINVAL;
+  if (loss_history && n_loss > 0 && !loss) return MTS_EINVAL;
+  return cuda_status(launch_adam(n, o, C, u, grad_C, m, v, step, loss, loss_history ? n_loss : 0,
+                                 loss_history, history_len, (cudaStream_t)stream));
 }
 
 }  // extern "C"

@@ -29,26 +29,28 @@ __global__ void tables_kernel(int n_struct, int n_freq, const int32_t* __restric
                               const int64_t* __restrict__ point_off,
                               const int32_t* __restrict__ freq_off,
                               const int32_t* __restrict__ loss_off, int npieces, int64_t* nn,
-                              int64_t* pn, int64_t* ln, int64_t* fn, int64_t* fp, int64_t* fl,
-                              int64_t* aop, int64_t* ptile, int64_t* pair,
+                              int64_t* pn, int64_t* pnr, int64_t* ln, int64_t* fn, int64_t* fp,
+                              int64_t* fl, int64_t* aop, int64_t* ptile, int64_t* pair,
                               int32_t* freq_struct, int32_t* cls_freq) {
   __shared__ int cls_base[kNumPortClasses];
   __shared__ int wcnt[8][kNumPortClasses];
   if (threadIdx.x == 0) {
-    int64_t a = 0, b = 0, c = 0, d = 0, e = 0, f = 0, g = 0, h = 0, q = 0;
+    int64_t a = 0, b = 0, br = 0, c = 0, d = 0, e = 0, f = 0, g = 0, h = 0, q = 0;
     for (int s = 0; s < n_struct; ++s) {
-      nn[s] = a; pn[s] = b; ln[s] = c; fn[s] = d; fp[s] = e; fl[s] = f; aop[s] = g;
+      nn[s] = a; pn[s] = b; pnr[s] = br; ln[s] = c; fn[s] = d; fp[s] = e; fl[s] = f; aop[s] = g;
       ptile[s] = h; pair[s] = q;
       int64_t N = port_off[s + 1] - port_off[s];
       int64_t P = point_off[s + 1] - point_off[s];
       int64_t F = freq_off[s + 1] - freq_off[s];
       int64_t L = loss_off ? (loss_off[s + 1] - loss_off[s]) : 0;
-      a += N * N; b += P * N; c += L * N; d += F * N; e += F * P; f += F * L;
+      a += N * N; b += round_up(P * N, kHAlign); br += P * N; c += L * N; d += F * N; e += F * P;
+      f += F * L;
       g += (int64_t)npieces * ((P + kTileP - 1) / kTileP * kTileP) * ((N + kChunkK - 1) / kChunkK * kChunkK);
       h += (P + kTileP - 1) / kTileP;
       q += N * (N + 1) / 2;
     }
-    nn[n_struct] = a; pn[n_struct] = b; ln[n_struct] = c; fn[n_struct] = d; fp[n_struct] = e;
+    nn[n_struct] = a; pn[n_struct] = b; pnr[n_struct] = br; ln[n_struct] = c; fn[n_struct] = d;
+    fp[n_struct] = e;
     fl[n_struct] = f; aop[n_struct] = g; ptile[n_struct] = h; pair[n_struct] = q;
   }
   for (int gi = threadIdx.x; gi < n_freq; gi += blockDim.x) {
@@ -457,9 +459,13 @@ __global__ void pack_a_kernel(int n_struct, const int64_t* __restrict__ ptile_of
 }
 
 template <typename HT>
-__global__ void export_h_kernel(int64_t n, const HT* __restrict__ H, double* __restrict__ out) {
+__global__ void export_h_kernel(int64_t n, int n_struct, const int64_t* __restrict__ pn_off,
+                                const int64_t* __restrict__ pnr_off, const HT* __restrict__ H,
+                                double* __restrict__ out) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = (double)H[i];
+  if (i >= n) return;
+  const int s = find_struct_i64(pnr_off, n_struct, i);  // unpadded position -> structure
+  out[i] = (double)H[pn_off[s] + (i - pnr_off[s])];
 }
 
 // ---------------------------------------------------------------------------------------
@@ -476,7 +482,8 @@ cudaError_t launch_build_basis(const mts_problem* pb, mts_precision prec, void* 
   cudaMemsetAsync(B + bl.status, 0, 16, st);
   tables_kernel<<<1, 256, 0, st>>>(
       pb->n_struct, pb->n_freq, pb->port_off, pb->point_off, pb->freq_off, pb->loss_off, npieces,
-      (int64_t*)(T + tl.nn_off), (int64_t*)(T + tl.pn_off), (int64_t*)(T + tl.ln_off),
+      (int64_t*)(T + tl.nn_off), (int64_t*)(T + tl.pn_off), (int64_t*)(T + tl.pnr_off),
+      (int64_t*)(T + tl.ln_off),
       (int64_t*)(T + tl.fn_off), (int64_t*)(T + tl.fp_off), (int64_t*)(T + tl.fl_off),
       (int64_t*)(T + tl.aop_off), (int64_t*)(T + tl.ptile_off), (int64_t*)(T + tl.pair_off),
       (int32_t*)(T + tl.freq_struct), (int32_t*)(T + tl.cls_freq));
@@ -539,14 +546,15 @@ cudaError_t launch_export_basis(const mts_problem* pb, mts_precision prec, const
                                 const BasisLayout& bl, const ProblemSums& ps, double* H_out,
                                 double* M_out, cudaStream_t st) {
   const char* B = static_cast<const char*>(basis);
-  if (H_out) {
+  if (H_out && ps.sumPNraw > 0) {
+    DevTables t = dev_tables(basis, bl, pb->n_struct, pb->n_freq);
     if (prec == MTS_FP64)
-      cudaMemcpyAsync(H_out, B + bl.H, sizeof(double) * ps.sumPN, cudaMemcpyDeviceToDevice, st);
-    else {
-      export_h_kernel<float><<<nblk(ps.sumPN, 256), 256, 0, st>>>(ps.sumPN, (const float*)(B + bl.H),
-                                                                  H_out);
-      note_launch();
-    }
+      export_h_kernel<double><<<nblk(ps.sumPNraw, 256), 256, 0, st>>>(
+          ps.sumPNraw, pb->n_struct, t.pn_off, t.pnr_off, (const double*)(B + bl.H), H_out);
+    else
+      export_h_kernel<float><<<nblk(ps.sumPNraw, 256), 256, 0, st>>>(
+          ps.sumPNraw, pb->n_struct, t.pn_off, t.pnr_off, (const float*)(B + bl.H), H_out);
+    note_launch();
   }
   if (M_out)
     cudaMemcpyAsync(M_out, B + bl.M64, sizeof(double) * ps.sumNN, cudaMemcpyDeviceToDevice, st);

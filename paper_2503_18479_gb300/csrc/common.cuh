@@ -6,7 +6,8 @@
 //   tables     int64 per-structure prefix tables (device copies, written by a kernel), the
 //              structure of every frequency, and the frequencies grouped by port class
 //   M64        FP64 [sum_s N_s^2]               inductance matrix blocks
-//   H          FP64 (MTS_FP64) or FP32 [sum_s P_s N_s]   field basis, points x loops
+//   H          FP64 (MTS_FP64) or FP32, structure s a [P_s][N_s] block starting at a
+//              multiple of 32 elements: field basis, points x loops
 //   Hloss64    FP64 [sum_s L_s N_s]             rows of H at the loss points
 //   Hloss32    FP32 [sum_s L_s N_s]
 //   M32hi/lo   FP32 [sum_s N_s^2]               M = hi + lo (double-float split)
@@ -66,6 +67,13 @@ inline bool use_tensor_path(int npieces, int64_t n_cfg, int64_t F) {
   return npieces > 0 && n_cfg * F > kSimtSys;
 }
 
+// Each structure's H block starts at a multiple of 32 elements (128 bytes), so that its rows
+// are 16-byte aligned whenever N_s is a multiple of 4 (vector loads in the SIMT kernel).
+constexpr int64_t kHAlign = 32;
+
+#ifdef __CUDACC__
+__host__ __device__
+#endif
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 inline size_t align256(size_t a) { return (a + 255) / 256 * 256; }
 
@@ -79,7 +87,9 @@ struct ProblemSums {
   int64_t sumLU = 0;  // sum over structures with N_s > kRegMaxPorts of F_s N_s^2 (factor scratch)
   int64_t cls_count[kNumPortClasses] = {0, 0, 0, 0, 0};  // frequencies per port class
   int cls_max_ports[kNumPortClasses] = {0, 0, 0, 0, 0};
-  int64_t sumNN = 0, sumPN = 0, sumLN = 0, sumFN = 0, sumFP = 0, sumFL = 0;
+  int64_t sumNN = 0, sumLN = 0, sumFN = 0, sumFP = 0, sumFL = 0;
+  int64_t sumPN = 0;     // H elements with each structure's block padded to kHAlign
+  int64_t sumPNraw = 0;  // sum_s P_s N_s (exported layout)
   int64_t sumAop = 0;  // bf16 elements per piece-set of the H operand (all pieces)
 };
 
@@ -91,7 +101,7 @@ struct BasisLayout {
 
 // Device-side table block inside the basis (arrays of n_struct+1 int64 unless noted).
 struct TableLayout {
-  size_t nn_off, pn_off, ln_off, fn_off, fp_off, fl_off, aop_off, ptile_off, pair_off,
+  size_t nn_off, pn_off, pnr_off, ln_off, fn_off, fp_off, fl_off, aop_off, ptile_off, pair_off,
       freq_struct /* int32 [n_freq] */, cls_freq /* int32 [n_freq] */, bytes;
 };
 
@@ -114,7 +124,8 @@ TapeLayout tape_layout(const mts_problem* pb, int64_t n_cfg, mts_precision prec)
 // Device pointers of the basis tables.
 struct DevTables {
   const int64_t* nn_off;
-  const int64_t* pn_off;
+  const int64_t* pn_off;   // H block of structure s (padded to kHAlign)
+  const int64_t* pnr_off;  // unpadded prefix of P_s N_s (exported layout)
   const int64_t* ln_off;
   const int64_t* fn_off;
   const int64_t* fp_off;
@@ -132,6 +143,7 @@ inline DevTables dev_tables(const void* basis, const BasisLayout& bl, int n_stru
   DevTables t;
   t.nn_off = reinterpret_cast<const int64_t*>(b + tl.nn_off);
   t.pn_off = reinterpret_cast<const int64_t*>(b + tl.pn_off);
+  t.pnr_off = reinterpret_cast<const int64_t*>(b + tl.pnr_off);
   t.ln_off = reinterpret_cast<const int64_t*>(b + tl.ln_off);
   t.fn_off = reinterpret_cast<const int64_t*>(b + tl.fn_off);
   t.fp_off = reinterpret_cast<const int64_t*>(b + tl.fp_off);

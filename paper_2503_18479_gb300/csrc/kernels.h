@@ -138,4 +138,8 @@ cudaError_t launch_grad_combine(int64_t n_cfg, int n_struct, int n_ports,
 
 cudaError_t launch_count_bad(const int32_t* status, int64_t n, int32_t* out, cudaStream_t st);
 
+cudaError_t launch_adam(int64_t n, const mts_adam& o, double* C, double* u, const double* g,
+                        double* m, double* v, int64_t* step, const double* loss, int64_t n_loss,
+                        double* history, int64_t history_len, cudaStream_t st);
+
 }  // namespace mts

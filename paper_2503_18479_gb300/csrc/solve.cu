@@ -219,8 +219,13 @@ __global__ void __launch_bounds__(NM >= 128 ? NM : 128) solve_fp64_kernel(SolveA
     }
   }
   // status
-  int nb = __syncthreads_or(bad ? 1 : 0);
-  if (valid && r == 0 && !bwd) a.status[sys] = nb ? 2 : 0;
+  // non-finite flag of this group's system only (a CTA holds G systems)
+  __syncthreads();
+  if (r == 0) redi[0] = 0;
+  __syncthreads();
+  if (bad) redi[0] = 1;
+  __syncthreads();
+  if (valid && r == 0 && !bwd) a.status[sys] = redi[0] ? 2 : 0;
 }
 
 // ---------------------------------------------------------------------------------------

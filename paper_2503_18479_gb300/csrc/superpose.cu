@@ -54,52 +54,59 @@ cudaError_t launch_plan(const mts_problem* pb, int64_t n_cfg, int npieces, int64
 }
 
 // SIMT superposition. A unit is 128 points x up to 16 systems of one structure; thread t owns
-// point t of the tile and accumulates its systems in registers. H arrives in K chunks staged
-// in shared memory (one coalesced read of the tile), the currents of the unit's systems in
-// the working precision beside it (k-major: the systems of one k are contiguous, read as
-// broadcasts). Used for MTS_FP64 (T = double, FP64 basis) and, in the other precisions, for
-// structures with at most 16 systems (T = float, FP32 basis; FP32 accumulation), where
-// tensor-core column tiles would be mostly padding and the work is a read of H.
+// point t of the tile, reads its own row of H straight from global memory (16-byte vector
+// loads when N is a multiple of 4: every structure's block starts on a 128-byte boundary;
+// all of a chunk's loads are in flight together) and accumulates its systems in registers.
+// The currents of the unit's systems are staged per K chunk in shared memory (k-major: the
+// systems of one k are contiguous, read as broadcasts). Used for MTS_FP64 (T = double, FP64
+// basis) and, in the other precisions, for structures with at most 16 systems (T = float,
+// FP32 basis, FP32 accumulation), where tensor-core column tiles would be mostly padding and
+// the work is a read of H.
 template <typename T>
 struct SimtCfg;
 template <>
 struct SimtCfg<float> {
-  static constexpr int KC = 64;
+  static constexpr int KC = 64;  // K chunk (registers of H per thread)
+  static constexpr int VEC = 4;  // elements per 16-byte load
   using C2 = float2;
+  using V = float4;
 };
 template <>
 struct SimtCfg<double> {
   static constexpr int KC = 32;
+  static constexpr int VEC = 2;
   using C2 = double2;
+  using V = double2;
 };
 
 template <typename T>
 constexpr size_t simt_smem_bytes() {
-  return sizeof(T) * (size_t)kSimtPts * (SimtCfg<T>::KC + 1) +
-         sizeof(T) * 2 * (size_t)SimtCfg<T>::KC * kSimtSys;
+  return sizeof(T) * 2 * (size_t)SimtCfg<T>::KC * kSimtSys;
 }
 
 template <typename T, int SC>
-__device__ inline void simt_accumulate(const T* __restrict__ hrow, const T* __restrict__ sI,
+__device__ inline void simt_accumulate(const T (&h)[SimtCfg<T>::KC], const T* __restrict__ sI,
                                        int kn, T (&ax)[kSimtSys], T (&ay)[kSimtSys]) {
-  for (int k = 0; k < kn; ++k) {
-    const T h = hrow[k];
-    const T* ik = sI + 2 * kSimtSys * k;
 #pragma unroll
-    for (int i = 0; i < SC; ++i) {
-      ax[i] = fma(h, ik[2 * i], ax[i]);
-      ay[i] = fma(h, ik[2 * i + 1], ay[i]);
+  for (int k = 0; k < SimtCfg<T>::KC; ++k) {
+    if (k < kn) {
+      const T* ik = sI + 2 * kSimtSys * k;
+#pragma unroll
+      for (int i = 0; i < SC; ++i) {
+        ax[i] = fma(h[k], ik[2 * i], ax[i]);
+        ay[i] = fma(h[k], ik[2 * i + 1], ay[i]);
+      }
     }
   }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kSimtPts) superpose_simt_kernel(SuperposeArgs a) {
-  constexpr int KC = SimtCfg<T>::KC;
+  constexpr int KC = SimtCfg<T>::KC, VEC = SimtCfg<T>::VEC;
   using C2 = typename SimtCfg<T>::C2;
+  using V = typename SimtCfg<T>::V;
   extern __shared__ __align__(16) unsigned char sm_simt[];
-  T* sH = reinterpret_cast<T*>(sm_simt);  // [kSimtPts][KC + 1]
-  T* sI = sH + kSimtPts * (KC + 1);       // [KC][kSimtSys][re, im]
+  T* sI = reinterpret_cast<T*>(sm_simt);  // [KC][kSimtSys][re, im]
   const int64_t unit = blockIdx.x;
   const int s = find_struct_i64(a.simt_off, a.n_struct, unit);
   const int N = a.port_off[s + 1] - a.port_off[s];
@@ -111,19 +118,34 @@ __global__ void __launch_bounds__(kSimtPts) superpose_simt_kernel(SuperposeArgs 
   const int64_t pt = lu % np, sys0 = (lu / np) * kSimtSys;
   const int nsv = (int)min((int64_t)kSimtSys, nsys - sys0);
   const int t = threadIdx.x;
-  const int64_t p0 = pt * kSimtPts;
-  const T* H = static_cast<const T*>(a.H) + a.t.pn_off[s];
+  const int64_t p = pt * kSimtPts + t;
+  const bool live = p < P;
+  const T* hrow = static_cast<const T*>(a.H) + a.t.pn_off[s] + (live ? p : 0) * N;
+  const bool vec = (N % VEC) == 0;
   T ax[kSimtSys], ay[kSimtSys];
 #pragma unroll
   for (int i = 0; i < kSimtSys; ++i) ax[i] = ay[i] = T(0);
   for (int k0 = 0; k0 < N; k0 += KC) {
     const int kn = min(KC, N - k0);
-    __syncthreads();
-    for (int e = t; e < kSimtPts * kn; e += kSimtPts) {
-      const int r = e / kn, c = e - r * kn;
-      const int64_t pr = p0 + r;
-      sH[r * (KC + 1) + c] = pr < P ? H[pr * N + k0 + c] : T(0);
+    T h[KC];
+    if (vec) {  // kn is a multiple of VEC here
+#pragma unroll
+      for (int q = 0; q < KC / VEC; ++q) {
+        V v;
+        if (live && q * VEC < kn) {
+          v = *reinterpret_cast<const V*>(hrow + k0 + q * VEC);
+        } else {
+          v = V{};
+        }
+        const T* pv = reinterpret_cast<const T*>(&v);
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) h[q * VEC + e] = pv[e];
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < KC; ++k) h[k] = (live && k < kn) ? hrow[k0 + k] : T(0);
     }
+    __syncthreads();
     for (int e = t; e < kn * kSimtSys; e += kSimtPts) {
       const int k = e / kSimtSys, i = e - k * kSimtSys;
       T re = T(0), im = T(0);
@@ -138,13 +160,11 @@ __global__ void __launch_bounds__(kSimtPts) superpose_simt_kernel(SuperposeArgs 
       sI[2 * (k * kSimtSys + i) + 1] = im;
     }
     __syncthreads();
-    const T* hrow = sH + t * (KC + 1);
-    if (nsv <= 4) simt_accumulate<T, 4>(hrow, sI, kn, ax, ay);
-    else if (nsv <= 8) simt_accumulate<T, 8>(hrow, sI, kn, ax, ay);
-    else simt_accumulate<T, 16>(hrow, sI, kn, ax, ay);
+    if (nsv <= 4) simt_accumulate<T, 4>(h, sI, kn, ax, ay);
+    else if (nsv <= 8) simt_accumulate<T, 8>(h, sI, kn, ax, ay);
+    else simt_accumulate<T, 16>(h, sI, kn, ax, ay);
   }
-  const int64_t p = p0 + t;
-  if (p < P) {
+  if (live) {
     C2* out = static_cast<C2*>(a.B_out);
     const int64_t fpo = a.t.fp_off[s];
 #pragma unroll

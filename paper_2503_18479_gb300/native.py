@@ -26,7 +26,9 @@ PRECISIONS = {"fp64": MTS_FP64, "mixed": MTS_MIXED, "bf16": MTS_BF16}
 EXPORTED = ["mts_status_string", "mts_version", "mts_launch_count", "mts_basis_bytes",
             "mts_build_basis", "mts_basis_export", "mts_basis_status", "mts_tape_bytes",
             "mts_solve", "mts_superpose", "mts_forward", "mts_backward", "mts_tape_status",
-            "mts_solve_static"]
+            "mts_solve_static", "mts_adam_step"]
+MTS_PROJ_NONE, MTS_PROJ_CLIP, MTS_PROJ_TANH = 0, 1, 2
+PROJECTIONS = {None: MTS_PROJ_NONE, "none": MTS_PROJ_NONE, "clip": MTS_PROJ_CLIP, "tanh": MTS_PROJ_TANH}
 
 
 class MtsProblem(ct.Structure):
@@ -50,6 +52,12 @@ class MtsEval(ct.Structure):
         ("target", ct.c_void_p), ("target_per_cfg", ct.c_int32), ("loss_mode", ct.c_int32),
         ("refine_tol", ct.c_double), ("max_refine", ct.c_int32),
     ]
+
+
+class MtsAdam(ct.Structure):
+    _fields_ = [("lr", ct.c_double), ("beta1", ct.c_double), ("beta2", ct.c_double),
+                ("eps", ct.c_double), ("projection", ct.c_int32), ("c_min", ct.c_double),
+                ("c_max", ct.c_double)]
 
 
 _lock = threading.Lock()
@@ -93,6 +101,8 @@ def lib():
             L.mts_backward.argtypes = [PP, ct.c_int, p, PE, p, sz, p, p, p, p]
             L.mts_solve_static.restype = ct.c_int
             L.mts_solve_static.argtypes = [PP, ct.c_int, p, PE, p, p, p, p]
+            L.mts_adam_step.restype = ct.c_int
+            L.mts_adam_step.argtypes = [i64, ct.POINTER(MtsAdam), p, p, p, p, p, p, p, i64, p, i64, p]
             L.mts_tape_status.restype = ct.c_int
             L.mts_tape_status.argtypes = [PP, i64, ct.c_int, p, ct.POINTER(ct.c_int64), p]
             _lib = L
@@ -288,3 +298,13 @@ def alloc_bytes(nbytes: int, device="cuda") -> torch.Tensor:
     t = torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
     assert t.data_ptr() % 256 == 0
     return t
+
+
+def mts_adam_step(n: int, opt: MtsAdam, C, u, grad_C, m, v, step, loss=None, loss_history=None,
+                  stream=None):
+    """One Adam update of n parameters (device tensors; step is a device int64 counter)."""
+    n_loss = 0 if loss is None else loss.numel()
+    hist_len = 0 if loss_history is None or n_loss == 0 else loss_history.numel() // n_loss
+    _check(lib().mts_adam_step(int(n), ct.byref(opt), _ptr(C), _ptr(u), _ptr(grad_C), _ptr(m),
+                               _ptr(v), _ptr(step), _ptr(loss), int(n_loss), _ptr(loss_history),
+                               int(hist_len), _stream(stream)), "mts_adam_step")

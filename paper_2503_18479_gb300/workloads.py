@@ -271,6 +271,28 @@ def single_loop(seed: int = 0, n_cfg: int = 1, n_freq: int = 101, grid: int = 32
                     meta=dict(seed=seed))
 
 
+def loop_sweep(n_init: int = 100, n_target: int = 100, grid: int = 32,
+               c_init_pf=(0.1, 30.0), c_target_pf=(5.0, 30.0)) -> Workload:
+    """Initialisation sweep on the single loop at 63.6 MHz (the paper's Sec. V-A study:
+    100 initial capacitances x 100 targets): configuration i * n_target + j starts from the
+    i-th initial value and fits the field made by the j-th target capacitance
+    (target_rule "field_at_C_per_cfg": the caller evaluates the forward map there)."""
+    a, rw = 0.050, 0.001
+    loops = [circular_loop(a, 64)]
+    omega = 2 * np.pi * np.array([63.6 * MHZ])
+    pts = grid_plane(grid, 0.100, 0.020)
+    q = [grid // 4, grid - 1 - grid // 4]
+    loss_idx = [iy * grid + ix for iy in q for ix in q]
+    st = _structure_from(loops, pts, omega, 0.1, loss_idx,
+                         L_self=np.array([circular_loop_inductance(a, rw)]), label="loop_sweep")
+    c0 = np.linspace(c_init_pf[0], c_init_pf[1], n_init) * PF
+    ct = np.linspace(c_target_pf[0], c_target_pf[1], n_target) * PF
+    C = np.repeat(c0, n_target)[:, None]
+    Ct = np.tile(ct, n_init)[:, None]
+    return Workload("loop_sweep", [st], C, rw, target_rule=("field_at_C_per_cfg", Ct),
+                    target_per_cfg=True, meta=dict(n_init=n_init, n_target=n_target))
+
+
 def line_8x1(seed: int = 0, n_cfg: int = 1024, n_freq: int = 201, grid: int = 64) -> Workload:
     rng = np.random.Generator(np.random.PCG64(seed))
     loops = square_array(8, 1)

@@ -190,3 +190,25 @@ def test_tape_holds_factors_of_large_systems(nv):
         # per-configuration growth: the factor block plus the small per-port arrays
         assert t1 - elem * 3 * 128 * 128 > 0
         assert t1 - elem * 3 * 128 * 128 < 4 * t0 + 4096
+
+
+def test_adam_step_validation(nv):
+    """Invalid optimiser settings are rejected before any launch."""
+    L = nv.lib()
+    good = nv.MtsAdam(1e-13, 0.9, 0.999, 1e-8, nv.MTS_PROJ_NONE, 0.0, 0.0)
+    fp = ct.c_void_p(FAKE)
+
+    def call(opt, n=4, C=fp, u=None, step=fp):
+        return L.mts_adam_step(n, ct.byref(opt), C, u, fp, fp, fp, step, None, 0, None, 0, None)
+
+    for bad in (nv.MtsAdam(-1.0, 0.9, 0.999, 1e-8, 0, 0.0, 0.0),
+                nv.MtsAdam(1e-13, 1.0, 0.999, 1e-8, 0, 0.0, 0.0),
+                nv.MtsAdam(1e-13, 0.9, -0.1, 1e-8, 0, 0.0, 0.0),
+                nv.MtsAdam(1e-13, 0.9, 0.999, float("nan"), 0, 0.0, 0.0),
+                nv.MtsAdam(1e-13, 0.9, 0.999, 1e-8, nv.MTS_PROJ_CLIP, 2e-10, 1e-10),
+                nv.MtsAdam(1e-13, 0.9, 0.999, 1e-8, 7, 0.0, 1.0)):
+        assert call(bad) == nv.MTS_EINVAL
+    assert call(good, n=-1) == nv.MTS_EINVAL
+    assert call(good, step=None) == nv.MTS_EINVAL
+    tanh = nv.MtsAdam(1e-13, 0.9, 0.999, 1e-8, nv.MTS_PROJ_TANH, 1e-11, 2e-10)
+    assert call(tanh, u=None) == nv.MTS_EINVAL
