@@ -69,6 +69,9 @@ def _load():
                                                     p, i32, i32, p]
             lib.oracle_gradient_field.restype = ct.c_int
             lib.oracle_gradient_field.argtypes = [i32, i64, p, p, p, i64, p, i32, p, p, p, p]
+            lib.oracle_gradient_rl.restype = ct.c_int
+            lib.oracle_gradient_rl.argtypes = [i32, p, p, p, i64, p, i32, p, p, i32, p, p, i32,
+                                               i32, p, p]
             lib.oracle_dcurrents_dC.restype = ct.c_int
             lib.oracle_dcurrents_dC.argtypes = [i32, p, p, d, p, p, p]
             lib.oracle_sroute.restype = ct.c_int
@@ -213,6 +216,22 @@ def gradient(H, M, R, C, omega, V, loss_idx, target, mode: int = 0, target_per_c
                                     _ptr(omega), _ptr(V), len(li), _ptr(li), _ptr(t),
                                     int(target_per_cfg), int(mode), _ptr(g))
     return g
+
+
+def gradient_rl(H, M, R, C, omega, V, loss_idx, target, mode: int = 0, target_per_cfg: bool = False):
+    """(d loss / d R, d loss / d L) with L_k = M_kk the self inductances, shapes [n_cfg, N]."""
+    H, M, R, C, omega = _f64(H), _f64(M), _f64(R), _f64(np.atleast_2d(C)), _f64(np.atleast_1d(omega))
+    V = _c128(np.atleast_2d(V))
+    P, N = H.shape
+    n_cfg, F = C.shape[0], len(omega)
+    li = _i64(loss_idx)
+    t = _target_arr(np.asarray(target), mode)
+    gR = np.zeros((n_cfg, N))
+    gL = np.zeros((n_cfg, N))
+    _load().oracle_gradient_rl(N, _ptr(H), _ptr(M), _ptr(R), n_cfg, _ptr(C), F, _ptr(omega),
+                               _ptr(V), len(li), _ptr(li), _ptr(t), int(target_per_cfg), int(mode),
+                               _ptr(gR), _ptr(gL))
+    return gR, gL
 
 
 def gradient_field(H, M, R, C, omega, V, gB):

@@ -437,6 +437,62 @@ int oracle_gradient_adjoint(int32_t N, int64_t P, const double* H, const double*
   return n_bad;
 }
 
+/* Gradients of the same objective with respect to the loop resistances R_k and the self
+ * inductances L_k = M_kk (Fig. 2 names R and L as optimisation variables beside C). From
+ * d(A^-1) = -A^-1 dA A^-1 (Eq. 8-9) with dA/dR_k = e_k e_k^T and dA/dM_kk = j w e_k e_k^T:
+ *   dloss/dR_k = -Re(mu_k I_k),   dloss/dL_k = -Re(j w mu_k I_k) = w Im(mu_k I_k),
+ * summed over frequencies and divided by F*L like the loss. Writes gR[b][N], gL[b][N].
+ * Returns the number of singular systems. */
+int oracle_gradient_rl(int32_t N, const double* H, const double* M, const double* R,
+                       int64_t n_cfg, const double* C, int32_t F, const double* omega,
+                       const double complex* V, int32_t L, const int64_t* loss_idx,
+                       const double* target, int32_t target_per_cfg, int32_t mode, double* gR,
+                       double* gL) {
+  int n_bad = 0;
+  const int64_t tw = (mode == 0) ? 1 : 2;
+#pragma omp parallel for schedule(static) reduction(+ : n_bad)
+  for (int64_t b = 0; b < n_cfg; ++b) {
+    double complex* A = malloc(sizeof(double complex) * (size_t)N * N);
+    int32_t* piv = malloc(sizeof(int32_t) * (size_t)N);
+    double complex* x = malloc(sizeof(double complex) * (size_t)N);
+    double complex* mu = malloc(sizeof(double complex) * (size_t)N);
+    const double* Cb = C + b * N;
+    for (int32_t k = 0; k < N; ++k) gR[b * N + k] = gL[b * N + k] = 0.0;
+    for (int32_t f = 0; f < F; ++f) {
+      oracle_assemble(N, M, R, omega[f], Cb, A);
+      if (oracle_lu(N, A, piv) != 0) {
+        n_bad += 1;
+        continue;
+      }
+      memcpy(x, V + (int64_t)f * N, sizeof(double complex) * (size_t)N);
+      oracle_lu_solve(N, A, piv, x);
+      const double* t = target + (target_per_cfg ? b * (int64_t)F * L * tw : 0);
+      for (int32_t k = 0; k < N; ++k) mu[k] = 0.0;
+      for (int32_t l = 0; l < L; ++l) {
+        double complex s = 0.0, G;
+        for (int32_t k = 0; k < N; ++k) s += H[loss_idx[l] * N + k] * x[k];
+        oracle_point_loss(mode, s, t + ((int64_t)f * L + l) * tw, &G);
+        for (int32_t k = 0; k < N; ++k) mu[k] += H[loss_idx[l] * N + k] * conj(G);
+      }
+      oracle_lu_solve(N, A, piv, mu); /* A^T = A */
+      for (int32_t k = 0; k < N; ++k) {
+        gR[b * N + k] += -creal(mu[k] * x[k]);
+        gL[b * N + k] += omega[f] * cimag(mu[k] * x[k]);
+      }
+    }
+    const double nrm = (F * L > 0) ? 1.0 / ((double)F * L) : 0.0;
+    for (int32_t k = 0; k < N; ++k) {
+      gR[b * N + k] *= nrm;
+      gL[b * N + k] *= nrm;
+    }
+    free(A);
+    free(piv);
+    free(x);
+    free(mu);
+  }
+  return n_bad;
+}
+
 /* Gradient with respect to C for an arbitrary field cotangent (the torch convention
  * gB = dL/dRe B + j dL/dIm B over the full field B[b][f][P]):
  * dL/dC_k = sum_f Im(mu_k I_k)/(w C_k^2) with mu = A^-1 H^T conj(gB[b][f]). */

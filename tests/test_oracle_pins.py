@@ -539,3 +539,54 @@ def test_forward_threads_do_not_change_bits():
     for b in range(5):
         o1 = oracle.forward(H, M, R, C[b:b + 1], omega, V, li, t)
         assert np.array_equal(o1["B"][0], out["B"][b]) and o1["loss"][0] == out["loss"][b]
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_gradient_rl_central_differences(mode):
+    """dloss/dR_k and dloss/dL_k (L_k = M_kk) from the adjoint versus Richardson-extrapolated
+    central differences of the oracle loss in R_k and M_kk."""
+    H, M, R, C, omega, V, li, t = _grad_case(mode)
+    gR, gL = oracle.gradient_rl(H, M, R, C, omega, V, li, t, mode=mode)
+    N = C.shape[1]
+
+    def cd_R(h):
+        fd = np.zeros_like(gR)
+        for k in range(N):
+            Rp, Rm = np.array(R, float), np.array(R, float)
+            Rp[k] += h
+            Rm[k] -= h
+            lp = oracle.forward(H, M, Rp, C, omega, V, li, t, mode=mode, want_B=False)["loss"]
+            lm = oracle.forward(H, M, Rm, C, omega, V, li, t, mode=mode, want_B=False)["loss"]
+            fd[:, k] = (lp - lm) / (2 * h)
+        return fd
+
+    def cd_L(h):
+        fd = np.zeros_like(gL)
+        for k in range(N):
+            Mp, Mm = M.copy(), M.copy()
+            Mp[k, k] += h
+            Mm[k, k] -= h
+            lp = oracle.forward(H, Mp, R, C, omega, V, li, t, mode=mode, want_B=False)["loss"]
+            lm = oracle.forward(H, Mm, R, C, omega, V, li, t, mode=mode, want_B=False)["loss"]
+            fd[:, k] = (lp - lm) / (2 * h)
+        return fd
+
+    r1, r2 = cd_R(1e-4), cd_R(0.5e-4)      # R ~ 0.1 ohm
+    l1, l2 = cd_L(1e-12), cd_L(0.5e-12)    # L ~ 1e-7 H
+    assert _rel(gR, (4 * r2 - r1) / 3) < 1e-6
+    assert _rel(gL, (4 * l2 - l1) / 3) < 1e-6
+
+
+def test_gradient_rl_single_loop_closed_form():
+    """N = 1: dI/dR = -I^2/V and dI/dL = -j w I^2/V, chained through (|b| - t)^2, b = h I."""
+    L, R, C, w, h, t = 250.79e-9, 0.1, 30e-12, 2 * np.pi * 63.6e6, 2e-5, 1e-7
+    V = np.array([[-1j * w * 1e-6 * 7.8e-3]])
+    I_ = V[0, 0] / (R + 1j * w * L + 1 / (1j * w * C))
+    b = h * I_
+    def d(db):
+        return 2 * (abs(b) - t) * np.real(np.conj(b) * db) / abs(b)
+    wantR = d(h * (-(I_ ** 2) / V[0, 0]))
+    wantL = d(h * (-1j * w * I_ ** 2 / V[0, 0]))
+    gR, gL = oracle.gradient_rl(np.array([[h]]), np.array([[L]]), [R], [[C]], [w], V, [0], np.array([[t]]))
+    assert abs(gR[0, 0] / wantR - 1) < 1e-12
+    assert abs(gL[0, 0] / wantL - 1) < 1e-12
