@@ -225,6 +225,21 @@ mts_status mts_backward(const mts_problem* pb, mts_precision prec, const void* b
                         const void* grad_B, const double* grad_loss, double* grad_C,
                         mts_stream stream);
 
+/* mts_param_grad: gradients of the objective with respect to the loop resistances R_k and
+ * the self inductances L_k = M_kk (Fig. 2 of the paper names R, L, C and w as optimisation
+ * variables), from the adjoint solution mu the forward kept in the tape:
+ *   grad_R[b][port] = grad_loss[b][s] * sum_f -Re(mu_k I_k) / (F_s L_s)
+ *   grad_L[b][port] = grad_loss[b][s] * sum_f  w Im(mu_k I_k) / (F_s L_s)
+ * (dA/dR_k = e_k e_k^T and dA/dM_kk = j w e_k e_k^T in d(A^-1) = -A^-1 dA A^-1, Eq. 8-9).
+ * Needs a preceding mts_solve / mts_forward on this tape with ev->target (the objective's
+ * adjoint); covers the loss cotangent only (not a field cotangent grad_B). grad_loss device
+ * [n_cfg][n_struct] or NULL (all ones); grad_R, grad_L device [n_cfg][n_ports] or NULL (at
+ * least one given). MTS_EINVAL if ev has no target or both outputs are NULL. */
+mts_status mts_param_grad(const mts_problem* pb, mts_precision prec, const void* basis,
+                          const mts_eval* ev, const void* tape, size_t tape_bytes,
+                          const double* grad_loss, double* grad_R, double* grad_L,
+                          mts_stream stream);
+
 /* Synchronises `stream` and summarises the per-system status of the last forward on
  * this tape: MTS_OK, or MTS_ENOCONV if any system missed the refinement tolerance or
  * met a non-finite value. If n_bad is not NULL it receives the number of such systems. */

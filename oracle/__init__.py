@@ -69,6 +69,10 @@ def _load():
                                                     p, i32, i32, p]
             lib.oracle_gradient_field.restype = ct.c_int
             lib.oracle_gradient_field.argtypes = [i32, i64, p, p, p, i64, p, i32, p, p, p, p]
+            lib.oracle_segment_pair_quadrature.restype = d
+            lib.oracle_segment_pair_quadrature.argtypes = [p, p, p, p, ct.c_int]
+            lib.oracle_gauss_legendre.restype = None
+            lib.oracle_gauss_legendre.argtypes = [ct.c_int, p, p]
             lib.oracle_gradient_rl.restype = ct.c_int
             lib.oracle_gradient_rl.argtypes = [i32, p, p, p, i64, p, i32, p, p, i32, p, p, i32,
                                                i32, p, p]
@@ -130,6 +134,20 @@ def segment_pair_inductance(a0, a1, b0, b1, wire_radius: float, same_segment: bo
     st = _load().oracle_segment_pair_inductance(_ptr(a0), _ptr(a1), _ptr(b0), _ptr(b1),
                                                 float(wire_radius), int(same_segment), _ptr(out))
     return int(st), float(out[0])
+
+
+def segment_pair_quadrature(a0, a1, b0, b1, order: int = 16):
+    """Neumann integral of two straight filaments by Gauss-Legendre (inner integral exact)."""
+    a0, a1, b0, b1 = map(_f64, (a0, a1, b0, b1))
+    return float(_load().oracle_segment_pair_quadrature(_ptr(a0), _ptr(a1), _ptr(b0), _ptr(b1),
+                                                         int(order)))
+
+
+def gauss_legendre(n: int):
+    """Nodes and weights of the n-point Gauss-Legendre rule on [-1, 1]."""
+    x, w = np.zeros(n), np.zeros(n)
+    _load().oracle_gauss_legendre(int(n), _ptr(x), _ptr(w))
+    return x, w
 
 
 def inductance(loop_vtx_off, vx, vy, vz, wire_radius: float, L_self=None):

@@ -135,13 +135,127 @@ void oracle_basis(int32_t n_loops, const int32_t* loop_vtx_off, const double* vx
  * (0 ln 0 = 0).
  * A segment with itself: mu0 l/(2 pi) (ln(2 l / rw) - 1), the thin round wire without
  * internal inductance (skin depth far below the wire radius at these frequencies).
- * Status: 0 ok, 1 a pair that is neither parallel nor perpendicular, 2 overlapping
+ * Pairs that are neither parallel nor perpendicular (oblique) and do not touch use the
+ * Neumann integral by quadrature (oracle_segment_pair_quadrature).
+ * Status: 0 ok, 1 an oblique pair that touches (shares an end point), 2 overlapping
  * collinear segments.
  * ------------------------------------------------------------------------------------ */
 static double oracle_G(double u, double d) { return u * asinh(u / d) - sqrt(u * u + d * d); }
 static double oracle_G0(double u) {
   double a = fabs(u);
   return (a == 0.0) ? 0.0 : a * log(a) - a;
+}
+
+/* Gauss-Legendre rule of order n on [-1, 1]: the nodes are the roots of the Legendre
+ * polynomial P_n (Newton's method from the Chebyshev-like guesses cos(pi (i + 3/4)/(n + 1/2)),
+ * P_n and P_n' by the three-term recurrence), the weights 2 / ((1 - x^2) P_n'(x)^2). */
+void oracle_gauss_legendre(int n, double* x, double* w) {
+  for (int i = 0; i < n; ++i) {
+    double z = cos(ORACLE_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = pk;
+      }
+      if (n == 1) p0 = 1.0;
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+/* Integral of 1/|p - b(t)| along the straight segment b0 -> b1 (length l2, unit vector u2):
+ * with w = p - b0, t0 = w.u2, rho^2 = |w|^2 - t0^2, it is
+ *   asinh((l2 - t0)/rho) + asinh(t0/rho) = ln((R1 + l2 - t0) / (R0 - t0)),
+ * R0 = |p - b0|, R1 = |p - b1|; a factor that cancels is rewritten through
+ * (R - t)(R + t) = rho^2 (rho^2 itself cancels when the projection of p falls outside the
+ * span). */
+static double oracle_inv_distance_line(const double p[3], const double b0[3], const double u2[3],
+                                       double l2) {
+  double w0[3] = {p[0] - b0[0], p[1] - b0[1], p[2] - b0[2]};
+  double t0 = w0[0] * u2[0] + w0[1] * u2[1] + w0[2] * u2[2];
+  double R0 = sqrt(w0[0] * w0[0] + w0[1] * w0[1] + w0[2] * w0[2]);
+  double w1[3] = {w0[0] - l2 * u2[0], w0[1] - l2 * u2[1], w0[2] - l2 * u2[2]};
+  double R1 = sqrt(w1[0] * w1[0] + w1[1] * w1[1] + w1[2] * w1[2]);
+  double a = l2 - t0;
+  if (t0 <= 0.0) return log((R1 + a) / (R0 - t0)); /* projection before b0: no cancellation */
+  if (a < 0.0) return log((R0 + t0) / (R1 - a));   /* beyond b1: both factors rewritten */
+  double rho2 = R0 * R0 - t0 * t0;                   /* projection on the span */
+  return log((R1 + a) * (R0 + t0) / rho2);
+}
+
+/* Distance from point p to the segment a -> b. */
+static double oracle_point_segment_distance(const double p[3], const double a[3],
+                                            const double b[3]) {
+  double d[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+  double w[3] = {p[0] - a[0], p[1] - a[1], p[2] - a[2]};
+  double dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  double t = dd > 0.0 ? (w[0] * d[0] + w[1] * d[1] + w[2] * d[2]) / dd : 0.0;
+  t = t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t);
+  double e[3] = {w[0] - t * d[0], w[1] - t * d[1], w[2] - t * d[2]};
+  return sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+}
+
+/* Panels of the outer rule: the outer segment is split into m equal panels with
+ * m = min(8, ceil(l1 / d)), d the smallest distance from an end point of either segment to
+ * the other segment, so that each panel is no longer than the gap (for segments that cross
+ * without touching this d can overstate the gap). */
+int oracle_quadrature_panels(const double r1s[3], const double r1e[3], const double r2s[3],
+                             const double r2e[3]) {
+  double l1 = sqrt((r1e[0] - r1s[0]) * (r1e[0] - r1s[0]) + (r1e[1] - r1s[1]) * (r1e[1] - r1s[1]) +
+                   (r1e[2] - r1s[2]) * (r1e[2] - r1s[2]));
+  double d = oracle_point_segment_distance(r1s, r2s, r2e);
+  double t = oracle_point_segment_distance(r1e, r2s, r2e);
+  if (t < d) d = t;
+  t = oracle_point_segment_distance(r2s, r1s, r1e);
+  if (t < d) d = t;
+  t = oracle_point_segment_distance(r2e, r1s, r1e);
+  if (t < d) d = t;
+  if (!(d > 0.0)) return 8;
+  double m = ceil(l1 / d);
+  return m < 1.0 ? 1 : (m > 8.0 ? 8 : (int)m);
+}
+
+/* Mutual partial inductance of two straight filaments in any relative position that do not
+ * touch: M = mu0/(4 pi) (u1.u2) int_0^l1 int_0^l2 ds dt / |r1(s) - r2(t)| (Neumann), the
+ * inner integral in closed form and the outer one by the composite Gauss-Legendre rule of
+ * the given order on oracle_quadrature_panels equal panels. */
+double oracle_segment_pair_quadrature(const double r1s[3], const double r1e[3],
+                                      const double r2s[3], const double r2e[3], int order) {
+  double d1[3] = {r1e[0] - r1s[0], r1e[1] - r1s[1], r1e[2] - r1s[2]};
+  double d2[3] = {r2e[0] - r2s[0], r2e[1] - r2s[1], r2e[2] - r2s[2]};
+  double l1 = sqrt(d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2]);
+  double l2 = sqrt(d2[0] * d2[0] + d2[1] * d2[1] + d2[2] * d2[2]);
+  if (l1 == 0.0 || l2 == 0.0) return 0.0;
+  double u2[3] = {d2[0] / l2, d2[1] / l2, d2[2] / l2};
+  double cosang = (d1[0] * d2[0] + d1[1] * d2[1] + d1[2] * d2[2]) / (l1 * l2);
+  double x[64], w[64];
+  if (order > 64) order = 64;
+  oracle_gauss_legendre(order, x, w);
+  const int m = oracle_quadrature_panels(r1s, r1e, r2s, r2e);
+  double acc = 0.0;
+  for (int q = 0; q < m; ++q)
+    for (int i = 0; i < order; ++i) {
+      double s = (q + 0.5 * (x[i] + 1.0)) / m;
+      double p[3] = {r1s[0] + s * d1[0], r1s[1] + s * d1[1], r1s[2] + s * d1[2]};
+      acc += w[i] * oracle_inv_distance_line(p, r2s, u2, l2);
+    }
+  return ORACLE_MU0 / (4.0 * ORACLE_PI) * cosang * 0.5 * (l1 / m) * acc;
+}
+
+/* Order of the rule for oblique pairs (enough for segments farther apart than a tenth of
+ * their length; pairs that touch are reported instead). */
+#define ORACLE_OBLIQUE_ORDER 16
+
+static double oracle_dist2(const double a[3], const double b[3]) {
+  double d0 = a[0] - b[0], d1 = a[1] - b[1], d2 = a[2] - b[2];
+  return d0 * d0 + d1 * d1 + d2 * d2;
 }
 
 int oracle_segment_pair_inductance(const double r1s[3], const double r1e[3],
@@ -164,7 +278,14 @@ int oracle_segment_pair_inductance(const double r1s[3], const double r1e[3],
   double cross = sqrt(cx * cx + cy * cy + cz * cz);
   double tol = 1e-12 * l1 * l2;
   if (fabs(dot) <= tol) return 0; /* perpendicular */
-  if (cross > tol) return 1;      /* oblique: not supported */
+  if (cross > tol) {              /* oblique: quadrature unless the segments touch */
+    double e2 = 1e-24 * (l1 + l2) * (l1 + l2);
+    if (oracle_dist2(r1s, r2s) <= e2 || oracle_dist2(r1s, r2e) <= e2 ||
+        oracle_dist2(r1e, r2s) <= e2 || oracle_dist2(r1e, r2e) <= e2)
+      return 1; /* touching oblique pair (a polygon corner): not handled */
+    *out = oracle_segment_pair_quadrature(r1s, r1e, r2s, r2e, ORACLE_OBLIQUE_ORDER);
+    return 0;
+  }
   double u[3] = {d1[0] / l1, d1[1] / l1, d1[2] / l1};
   double w[3] = {r2s[0] - r1s[0], r2s[1] - r1s[1], r2s[2] - r1s[2]};
   double b_s = w[0] * u[0] + w[1] * u[1] + w[2] * u[2];

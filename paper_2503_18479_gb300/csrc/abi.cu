@@ -92,8 +92,8 @@ PlanLayout plan_layout(int n_struct) {
 
 // Elements of the tensor-core B operand, and the GEMM / SIMT work units of the superposition.
 static int64_t bop_elems(const mts_problem* pb, int64_t n_cfg, int npieces, int64_t* units,
-                         int64_t* simt_units = nullptr) {
-  int64_t a = 0, u = 0, v = 0;
+                         int64_t* simt_units = nullptr, int64_t* max_simt = nullptr) {
+  int64_t a = 0, u = 0, v = 0, vmax = 0;
   for (int s = 0; s < pb->n_struct; ++s) {
     int64_t N = pb->h_port_off[s + 1] - pb->h_port_off[s];
     int64_t P = pb->h_point_off[s + 1] - pb->h_point_off[s];
@@ -105,11 +105,14 @@ static int64_t bop_elems(const mts_problem* pb, int64_t n_cfg, int npieces, int6
       a += (int64_t)npieces * nn * nkc * kTileN * kChunkK;
       u += npt * nn;
     } else {
-      v += (P + kSimtPts - 1) / kSimtPts * ((n_cfg * F + kSimtSys - 1) / kSimtSys);
+      const int64_t vs = (P + kSimtPts - 1) / kSimtPts * ((n_cfg * F + kSimtSys - 1) / kSimtSys);
+      v += vs;
+      if (vs > vmax) vmax = vs;
     }
   }
   if (units) *units = u;
   if (simt_units) *simt_units = v;
+  if (max_simt) *max_simt = vmax;
   return a;
 }
 
@@ -130,6 +133,7 @@ TapeLayout tape_layout(const mts_problem* pb, int64_t n_cfg, mts_precision prec)
   t.err = o; o += 256;
   t.Bop = o; o += align256(2 * (size_t)bop_elems(pb, n_cfg, n_pieces(prec), nullptr));
   t.lu = o; o += align256((prec == MTS_FP64 ? 16 : 8) * nc * (size_t)ps.sumLU);
+  t.mu_loss = o; o += align256(16 * nc * ps.sumFN);
   t.total = o;
   return t;
 }
@@ -236,6 +240,7 @@ static SolveArgs solve_args(const mts_problem* pb, mts_precision prec, const voi
   a.bop_off = reinterpret_cast<const int64_t*>(T + tl.plan + pl.bop_off);
   a.lu_off = reinterpret_cast<const int64_t*>(T + tl.plan + pl.lu_off);
   a.lu = T + tl.lu;
+  a.mu_out = reinterpret_cast<double*>(T + tl.mu_loss);
   a.max_loss = max_loss_points(pb);
   a.rhs_in = nullptr;
   return a;
@@ -401,7 +406,7 @@ mts_status mts_superpose(const mts_problem* pb, mts_precision prec, const void* 
   a.n_cfg = ev->n_cfg;
   a.sumFN = ps.sumFN;
   a.sumFP = ps.sumFP;
-  bop_elems(pb, ev->n_cfg, n_pieces(prec), &a.total_units, &a.total_simt);
+  bop_elems(pb, ev->n_cfg, n_pieces(prec), &a.total_units, &a.total_simt, &a.max_simt);
   a.unit_off = reinterpret_cast<const int64_t*>(T + tl.plan + pl.unit_off);
   a.simt_off = reinterpret_cast<const int64_t*>(T + tl.plan + pl.simt_off);
   a.H = B + bl.H;
@@ -500,6 +505,24 @@ mts_status mts_tape_status(const mts_problem* pb, int64_t n_cfg, mts_precision p
   if (n_bad) *n_bad = h[1];
   if (h[0] != 0) return MTS_ECUDA;  // a kernel gave up on a bounded wait
   return h[1] ? MTS_ENOCONV : MTS_OK;
+}
+
+mts_status mts_param_grad(const mts_problem* pb, mts_precision prec, const void* basis,
+                          const mts_eval* ev, const void* tape, size_t tape_bytes,
+                          const double* grad_loss, double* grad_R, double* grad_L,
+                          mts_stream stream) {
+  mts_status v = check_solve_args(pb, prec, basis, ev, const_cast<void*>(tape), tape_bytes);
+  if (v != MTS_OK) return v;
+  if (!ev->target || (!grad_R && !grad_L)) return MTS_EINVAL;
+  BasisLayout bl = basis_layout(pb, prec);
+  TapeLayout tl = tape_layout(pb, ev->n_cfg, prec);
+  ProblemSums ps = problem_sums(pb, prec);
+  const char* T = static_cast<const char*>(tape);
+  return cuda_status(launch_param_grad(
+      ev->n_cfg, pb->n_struct, pb->n_ports, pb->port_off, pb->freq_off, pb->loss_off,
+      dev_tables(basis, bl, pb->n_struct, pb->n_freq), ps.sumFN, ev->omega,
+      reinterpret_cast<const double*>(T + tl.I), reinterpret_cast<const double*>(T + tl.mu_loss),
+      grad_loss, grad_R, grad_L, (cudaStream_t)stream));
 }
 
 mts_status mts_adam_step(int64_t n, const mts_adam* opt, double* C, double* u,

@@ -131,6 +131,52 @@ __global__ void count_bad_kernel(const int32_t* __restrict__ status, int64_t n, 
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
 }
 
+// dloss/dR_k = sum_f -Re(mu_k I_k), dloss/dL_k = sum_f w Im(mu_k I_k) (dA/dR_k = e_k e_k^T,
+// dA/dM_kk = j w e_k e_k^T in d(A^-1) = -A^-1 dA A^-1, Eq. 8-9), divided by F_s L_s like the
+// objective and weighted by the loss cotangent of the port's structure.
+__global__ void param_grad_kernel(int64_t n_cfg, int n_struct, int n_ports,
+                                  const int32_t* __restrict__ port_off,
+                                  const int32_t* __restrict__ freq_off,
+                                  const int32_t* __restrict__ loss_off, DevTables t, int64_t sumFN,
+                                  const double* __restrict__ omega, const double* __restrict__ I,
+                                  const double* __restrict__ mu, const double* __restrict__ grad_loss,
+                                  double* __restrict__ grad_R, double* __restrict__ grad_L) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_cfg * n_ports) return;
+  const int64_t b = i / n_ports;
+  const int port = (int)(i - b * n_ports);
+  const int s = find_struct_i32(port_off, n_struct, port);
+  const int N = port_off[s + 1] - port_off[s], k = port - port_off[s];
+  const int F = freq_off[s + 1] - freq_off[s];
+  const int L = loss_off[s + 1] - loss_off[s];
+  double gr = 0.0, gl = 0.0;
+  for (int f = 0; f < F; ++f) {
+    const int64_t o = 2 * (b * sumFN + t.fn_off[s] + (int64_t)f * N + k);
+    const double px = mu[o] * I[o] - mu[o + 1] * I[o + 1];  // Re(mu I)
+    const double py = mu[o] * I[o + 1] + mu[o + 1] * I[o];  // Im(mu I)
+    gr -= px;
+    gl += omega[freq_off[s] + f] * py;
+  }
+  double scale = (F * L > 0) ? 1.0 / ((double)F * L) : 0.0;
+  if (grad_loss) scale *= grad_loss[b * n_struct + s];
+  if (grad_R) grad_R[i] = gr * scale;
+  if (grad_L) grad_L[i] = gl * scale;
+}
+
+cudaError_t launch_param_grad(int64_t n_cfg, int n_struct, int n_ports, const int32_t* port_off,
+                              const int32_t* freq_off, const int32_t* loss_off, DevTables t,
+                              int64_t sumFN, const double* omega, const double* I,
+                              const double* mu, const double* grad_loss, double* grad_R,
+                              double* grad_L, cudaStream_t st) {
+  const int64_t n = n_cfg * n_ports;
+  if (n == 0) return cudaSuccess;
+  param_grad_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+      n_cfg, n_struct, n_ports, port_off, freq_off, loss_off, t, sumFN, omega, I, mu, grad_loss,
+      grad_R, grad_L);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_count_bad(const int32_t* status, int64_t n, int32_t* out, cudaStream_t st) {
   cudaMemsetAsync(out, 0, sizeof(int32_t), st);
   if (n > 0) {

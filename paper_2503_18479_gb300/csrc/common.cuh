@@ -30,6 +30,7 @@
 //   err        int32 [4]: [0] bounded-wait timeout code, [1] count of bad systems
 //   Bop        bf16 tensor-core operand of I, per structure
 //              [piece][n_tile][k_chunk][128 rows x 64 k], row = 2 (b F_s + f) + c
+//   mu_loss    FP64 complex [n_cfg][sum F N]    adjoint solution of the objective
 //   lu         complex FP32 (FP64 for MTS_FP64) [n_cfg][sum_{N_s > 64} F_s N_s^2]: LU
 //              factors of the systems too large for the register-resident solve
 #pragma once
@@ -107,7 +108,7 @@ struct TableLayout {
 
 struct TapeLayout {
   size_t I = 0, loss_part = 0, grad_part = 0, dldc = 0, lossv = 0, status = 0, mu = 0,
-         gfield = 0, plan = 0, err = 0, Bop = 0, lu = 0, total = 0;
+         gfield = 0, plan = 0, err = 0, Bop = 0, lu = 0, mu_loss = 0, total = 0;
 };
 
 // Per-call plan tables inside the tape (arrays of n_struct+1 int64).

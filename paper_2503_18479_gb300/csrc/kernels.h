@@ -40,6 +40,7 @@ struct SolveArgs {
   const int64_t* lu_off;   // per-structure element base of the factor scratch (plan table;
                            // [n_struct] = elements per configuration)
   void* lu;                // factor scratch of the large-system kernel
+  double* mu_out;          // adjoint solution mu of the objective (forward with a target)
   // systems of one launch: all (glist == nullptr: system = launch index), or the
   // configurations x the gcount frequencies glist[0 .. gcount-1] of one port class
   const int32_t* glist;
@@ -102,6 +103,7 @@ struct SuperposeArgs {
   int64_t total_units;      // GEMM work units (host-computed)
   const int64_t* unit_off;  // per-structure prefix of GEMM units (plan table)
   int64_t total_simt;       // SIMT work units (host-computed)
+  int64_t max_simt;         // most SIMT units of one structure (2-D grid: x unit, y structure)
   const int64_t* simt_off;  // per-structure prefix of SIMT units (plan table)
   const void* H;            // FP64 (MTS_FP64) basis
   const double* I;          // tape currents
@@ -137,6 +139,13 @@ cudaError_t launch_grad_combine(int64_t n_cfg, int n_struct, int n_ports,
                                 cudaStream_t st);
 
 cudaError_t launch_count_bad(const int32_t* status, int64_t n, int32_t* out, cudaStream_t st);
+
+// dloss/dR and dloss/dL (self inductances) from the stored adjoint solutions and currents
+cudaError_t launch_param_grad(int64_t n_cfg, int n_struct, int n_ports, const int32_t* port_off,
+                              const int32_t* freq_off, const int32_t* loss_off, DevTables t,
+                              int64_t sumFN, const double* omega, const double* I,
+                              const double* mu, const double* grad_loss, double* grad_R,
+                              double* grad_L, cudaStream_t st);
 
 cudaError_t launch_adam(int64_t n, const mts_adam& o, double* C, double* u, const double* g,
                         double* m, double* v, int64_t* step, const double* loss, int64_t n_loss,

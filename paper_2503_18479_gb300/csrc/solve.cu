@@ -216,6 +216,10 @@ __global__ void __launch_bounds__(NM >= 128 ? NM : 128) solve_fp64_kernel(SolveA
     if (valid && real_row) {
       double g = (mu.x * x.y + mu.y * x.x) / (w * Cr * Cr);  // Im(mu x)/(w C^2)
       a.grad_part[ioff + r] = g;
+      if (!bwd && a.mu_out) {
+        a.mu_out[2 * (ioff + r)] = mu.x;
+        a.mu_out[2 * (ioff + r) + 1] = mu.y;
+      }
     }
   }
   // status

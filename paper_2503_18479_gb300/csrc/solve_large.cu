@@ -528,6 +528,10 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
     for (int r = tid; r < N; r += T) {
       const cd mu = xk[r], x = xc[r];
       a.grad_part[ioff + r] = (mu.x * x.y + mu.y * x.x) / (w * Cb[r] * Cb[r]);
+      if (!bwd && a.mu_out) {
+        a.mu_out[2 * (ioff + r)] = mu.x;
+        a.mu_out[2 * (ioff + r) + 1] = mu.y;
+      }
     }
   }
   double bad = 0.0;

@@ -685,7 +685,13 @@ __global__ void __launch_bounds__(NM >= 64 ? NM : 128, NM >= 64 ? 5 : 1) solve_m
     } else {
       const cd mu = xk;
       // Im(mu x)/(w C^2) = Im(mu x) w (1/(w C))^2, without a second division
-      if (valid && real_row) a.grad_part[ioff + r] = (mu.x * x.y + mu.y * x.x) * w * (Dr.y * Dr.y);
+      if (valid && real_row) {
+        a.grad_part[ioff + r] = (mu.x * x.y + mu.y * x.x) * w * (Dr.y * Dr.y);
+        if (!bwd && a.mu_out) {
+          a.mu_out[2 * (ioff + r)] = mu.x;
+          a.mu_out[2 * (ioff + r) + 1] = mu.y;
+        }
+      }
     }
   }
   const float fb = gmax<NM>(bad ? 2.0f : (conv_all ? 0.0f : 1.0f), sm, r);

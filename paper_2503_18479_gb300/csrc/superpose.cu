@@ -107,8 +107,17 @@ __global__ void __launch_bounds__(kSimtPts) superpose_simt_kernel(SuperposeArgs 
   using V = typename SimtCfg<T>::V;
   extern __shared__ __align__(16) unsigned char sm_simt[];
   T* sI = reinterpret_cast<T*>(sm_simt);  // [KC][kSimtSys][re, im]
-  const int64_t unit = blockIdx.x;
-  const int s = find_struct_i64(a.simt_off, a.n_struct, unit);
+  // 2-D grid: y = structure, x = unit within it (no search); 1-D: search the unit prefix
+  int s;
+  int64_t unit;
+  if (gridDim.y > 1) {
+    s = blockIdx.y;
+    unit = a.simt_off[s] + blockIdx.x;
+    if (unit >= a.simt_off[s + 1]) return;  // CTA-uniform
+  } else {
+    unit = blockIdx.x;
+    s = find_struct_i64(a.simt_off, a.n_struct, unit);
+  }
   const int N = a.port_off[s + 1] - a.port_off[s];
   const int64_t P = a.point_off[s + 1] - a.point_off[s];
   const int F = a.freq_off[s + 1] - a.freq_off[s];
@@ -188,7 +197,12 @@ static cudaError_t launch_simt(const SuperposeArgs& a, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(superpose_simt_kernel<T>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  superpose_simt_kernel<T><<<(unsigned)a.total_simt, kSimtPts, sm, st>>>(a);
+  // one grid row per structure when the padding (units of the largest structure times the
+  // structures) stays within twice the work and the structures fit the y dimension
+  dim3 grid((unsigned)a.total_simt);
+  if (a.n_struct > 1 && a.n_struct <= 65535 && a.max_simt * a.n_struct <= 2 * a.total_simt)
+    grid = dim3((unsigned)a.max_simt, (unsigned)a.n_struct);
+  superpose_simt_kernel<T><<<grid, kSimtPts, sm, st>>>(a);
   note_launch();
   return cudaGetLastError();
 }

@@ -26,7 +26,7 @@ PRECISIONS = {"fp64": MTS_FP64, "mixed": MTS_MIXED, "bf16": MTS_BF16}
 EXPORTED = ["mts_status_string", "mts_version", "mts_launch_count", "mts_basis_bytes",
             "mts_build_basis", "mts_basis_export", "mts_basis_status", "mts_tape_bytes",
             "mts_solve", "mts_superpose", "mts_forward", "mts_backward", "mts_tape_status",
-            "mts_solve_static", "mts_adam_step"]
+            "mts_solve_static", "mts_adam_step", "mts_param_grad"]
 MTS_PROJ_NONE, MTS_PROJ_CLIP, MTS_PROJ_TANH = 0, 1, 2
 PROJECTIONS = {None: MTS_PROJ_NONE, "none": MTS_PROJ_NONE, "clip": MTS_PROJ_CLIP, "tanh": MTS_PROJ_TANH}
 
@@ -101,6 +101,8 @@ def lib():
             L.mts_backward.argtypes = [PP, ct.c_int, p, PE, p, sz, p, p, p, p]
             L.mts_solve_static.restype = ct.c_int
             L.mts_solve_static.argtypes = [PP, ct.c_int, p, PE, p, p, p, p]
+            L.mts_param_grad.restype = ct.c_int
+            L.mts_param_grad.argtypes = [PP, ct.c_int, p, PE, p, sz, p, p, p, p]
             L.mts_adam_step.restype = ct.c_int
             L.mts_adam_step.argtypes = [i64, ct.POINTER(MtsAdam), p, p, p, p, p, p, p, i64, p, i64, p]
             L.mts_tape_status.restype = ct.c_int
@@ -308,3 +310,11 @@ def mts_adam_step(n: int, opt: MtsAdam, C, u, grad_C, m, v, step, loss=None, los
     _check(lib().mts_adam_step(int(n), ct.byref(opt), _ptr(C), _ptr(u), _ptr(grad_C), _ptr(m),
                                _ptr(v), _ptr(step), _ptr(loss), int(n_loss), _ptr(loss_history),
                                int(hist_len), _stream(stream)), "mts_adam_step")
+
+
+def mts_param_grad(pb, prec, basis, ev: Eval, tape, grad_loss=None, grad_R=None, grad_L=None,
+                   stream=None):
+    """dloss/dR and dloss/dL (self inductances) after a forward with a target."""
+    _check(lib().mts_param_grad(pb.ref, _prec(prec), _ptr(basis), ev.ref, _ptr(tape),
+                                tape.numel() * tape.element_size(), _ptr(grad_loss),
+                                _ptr(grad_R), _ptr(grad_L), _stream(stream)), "mts_param_grad")

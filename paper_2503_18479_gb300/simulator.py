@@ -78,6 +78,15 @@ class Simulator:
         nv.mts_backward(self.pb, self.prec, self.basis, ev, tape, gB, gl, grad_C, stream)
         return grad_C
 
+    def param_grad(self, ev: nv.Eval, tape: torch.Tensor, grad_loss=None, stream=None):
+        """(dloss/dR, dloss/dL) per configuration and port, [n_cfg, n_ports] each, after a
+        forward with the objective (loss cotangent grad_loss [n_cfg, n_struct], default 1)."""
+        gR = torch.empty((ev.n_cfg, self.n_ports), dtype=torch.float64, device=self.device)
+        gL = torch.empty_like(gR)
+        gl = None if grad_loss is None else grad_loss.to(torch.float64).contiguous()
+        nv.mts_param_grad(self.pb, self.prec, self.basis, ev, tape, gl, gR, gL, stream)
+        return gR, gL
+
     def status(self, tape: torch.Tensor, n_cfg: int):
         return nv.mts_tape_status(self.pb, n_cfg, self.prec, tape)
 

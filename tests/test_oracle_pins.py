@@ -159,8 +159,8 @@ def test_parallel_filaments_textbook():
     assert st == 0 and abs(m2 + m) < 1e-24
     st, m3 = oracle.segment_pair_inductance((0, 0, 0), (l, 0, 0), (0, d, 0), (0, d + l, 0), 1e-3)
     assert st == 0 and m3 == 0.0
-    st, _ = oracle.segment_pair_inductance((0, 0, 0), (l, 0, 0), (0, d, 0), (l, d + l, 0), 1e-3)
-    assert st == 1  # oblique pairs are reported, not guessed
+    st, _ = oracle.segment_pair_inductance((0, 0, 0), (l, 0, 0), (l, 0, 0), (l + l, l, 0), 1e-3)
+    assert st == 1  # oblique pairs that touch (a polygon corner) are reported, not guessed
 
 
 def test_collinear_filaments_textbook():
@@ -590,3 +590,68 @@ def test_gradient_rl_single_loop_closed_form():
     gR, gL = oracle.gradient_rl(np.array([[h]]), np.array([[L]]), [R], [[C]], [w], V, [0], np.array([[t]]))
     assert abs(gR[0, 0] / wantR - 1) < 1e-12
     assert abs(gL[0, 0] / wantL - 1) < 1e-12
+
+
+
+# ---------------------------------------------------------------- oblique segment pairs
+def test_gauss_legendre_rule():
+    """The n-point rule integrates polynomials of degree 2n - 1 exactly and no higher."""
+    for n in (1, 2, 5, 16, 32):
+        x, w = oracle.gauss_legendre(n)
+        for deg in range(0, 2 * n, 1):
+            exact = 0.0 if deg % 2 else 2.0 / (deg + 1)
+            assert abs((w * x ** deg).sum() - exact) < 1e-13
+        if n <= 5:  # the error term for x^(2n) is visible at low orders
+            assert abs((w * x ** (2 * n)).sum() - 2.0 / (2 * n + 1)) > 1e-6
+
+
+@pytest.mark.parametrize("d", [0.01, 0.03, 0.2])
+@pytest.mark.parametrize("shift", [0.0, 0.02, -0.07])
+def test_quadrature_matches_parallel_closed_form(d, shift):
+    """For parallel filaments the quadrature reproduces the closed form (textbook G)."""
+    l1, l2 = 0.05, 0.03
+    a0, a1 = (0, 0, 0), (l1, 0, 0)
+    b0, b1 = (shift, d, 0.004), (shift + l2, d, 0.004)
+    st, exact = oracle.segment_pair_inductance(a0, a1, b0, b1, 1e-3)
+    assert st == 0
+    q = oracle.segment_pair_quadrature(a0, a1, b0, b1, 16)
+    assert abs(q / exact - 1) < 1e-10
+    # reversed second filament: sign flips
+    assert abs(oracle.segment_pair_quadrature(a0, a1, b1, b0, 16) + q) < 1e-12 * abs(q)
+
+
+def test_quadrature_symmetric_and_converged_for_skew_pairs():
+    """A skew pair: M(a, b) = M(b, a) (outer and inner integrals swap roles), order 16 agrees
+    with order 64, perpendicular directions give zero, and the pair the inductance routine
+    now accepts equals the quadrature."""
+    a0, a1 = np.array([0.0, 0.0, 0.0]), np.array([0.04, 0.01, 0.0])
+    b0, b1 = np.array([0.01, 0.03, 0.005]), np.array([0.05, 0.02, 0.02])
+    m_ab = oracle.segment_pair_quadrature(a0, a1, b0, b1, 16)
+    m_ba = oracle.segment_pair_quadrature(b0, b1, a0, a1, 16)
+    m64 = oracle.segment_pair_quadrature(a0, a1, b0, b1, 64)
+    assert abs(m_ab / m_ba - 1) < 1e-12 and abs(m_ab / m64 - 1) < 1e-12
+    st, m = oracle.segment_pair_inductance(a0, a1, b0, b1, 1e-3)
+    assert st == 0 and m == m_ab
+    assert oracle.segment_pair_quadrature(a0, a1, b0, b0 + np.array([0.0, 0.0, 0.03]), 16) == 0.0
+
+
+def test_coaxial_circles_maxwell():
+    """Mutual inductance of two coaxial circular loops (radii a, b, axial distance h) from
+    polygons of n and 2n segments, Richardson-extrapolated in 1/n^2, against Maxwell's
+    formula M = mu0 sqrt(ab) ((2/k - k) K(k) - (2/k) E(k)), k^2 = 4ab/((a+b)^2 + h^2)."""
+    sp = pytest.importorskip("scipy.special")
+    a, b, h = 0.05, 0.03, 0.02
+    k2 = 4 * a * b / ((a + b) ** 2 + h * h)
+    k = np.sqrt(k2)
+    exact = MU0 * np.sqrt(a * b) * ((2 / k - k) * sp.ellipk(k2) - (2 / k) * sp.ellipe(k2))
+
+    def polygon_pair(n):
+        loops = [W.circular_loop(a, n), W.circular_loop(b, n, z=h)]
+        off, vx, vy, vz = _loop_arrays(loops)
+        st, M = oracle.inductance(off, vx, vy, vz, 1e-3, L_self=np.array([1.0, 1.0]))
+        assert st == 0
+        return M[0, 1]
+
+    m1, m2 = polygon_pair(128), polygon_pair(256)
+    assert abs(m2 / exact - 1) < 1e-3
+    assert abs((4 * m2 - m1) / 3 / exact - 1) < 1e-6
