@@ -83,9 +83,11 @@ typedef enum {
  *                                                   indices inside structure s)
  * Loop k is the closed polyline of vertices loop_vtx_off[k] .. loop_vtx_off[k+1]-1, the
  * last joined back to the first; its orientation fixes the sign of its current. Each
- * structure is coupled only within itself. Off-diagonal inductances, and diagonal ones
- * when L_self is NULL, need every segment pair to be parallel or perpendicular
- * (rectilinear loops); other pairs give MTS_EUNSUPPORTED from mts_basis_status.
+ * structure is coupled only within itself. Inductances come from the Neumann integral over
+ * segment pairs: in closed form for parallel and perpendicular pairs, by quadrature
+ * (composite 16-point Gauss-Legendre, inner integral exact) for oblique pairs that do not
+ * touch. Oblique pairs that share an end point (the corners of a non-rectilinear polygon)
+ * give MTS_EUNSUPPORTED from mts_basis_status, so such loops need L_self.
  * Offset tables are given twice, identical: host copies (h_*) plan launches, device
  * copies are read by the kernels. Limits: 1 <= ports per structure <= 1024 (more give
  * MTS_EUNSUPPORTED from every entry point, before any launch). Systems of up to 64 ports

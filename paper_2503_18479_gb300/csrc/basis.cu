@@ -17,6 +17,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -292,8 +294,108 @@ __global__ void __launch_bounds__(128) basis_fp32_kernel(
 //     G(u) = u asinh(u/d) - sqrt(u^2 + d^2);
 //   collinear, non-overlapping: G replaced by its d -> 0 form |u| ln|u| - |u|;
 //   a segment with itself: mu0 l/(2 pi) (ln(2l/rw) - 1).
-// Returns 0, or 1 (oblique pair) / 2 (overlapping collinear pair) with value 0.
+//   oblique (neither parallel nor perpendicular) and not touching: the Neumann integral
+//     mu0/(4 pi) (u1.u2) int int ds dt / |r1(s) - r2(t)| with the inner integral in closed
+//     form (ln((R1 + l2 - t0)/(R0 - t0)), cancelling factors rewritten through rho^2) and the
+//     outer one by a composite 16-point Gauss-Legendre rule on m = min(8, ceil(l1/d))
+//     equal panels, d the smallest end-point-to-segment distance.
+// Returns 0, or 1 (oblique pair that touches) / 2 (overlapping collinear pair) with value 0.
 // ---------------------------------------------------------------------------------------
+struct GaussRule16 {
+  double x[16], w[16];
+};
+
+// 16-point Gauss-Legendre rule on [-1, 1] (host): roots of P_16 by Newton's method with
+// the three-term recurrence, weights 2 / ((1 - x^2) P_16'(x)^2).
+static GaussRule16 gauss_legendre16() {
+  GaussRule16 g;
+  const int n = 16;
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(3.14159265358979323846 * (i + 0.75) / (n + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = pk;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    g.x[i] = z;
+    g.w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+  return g;
+}
+
+__device__ inline double inv_distance_line(double px, double py, double pz, double b0x,
+                                           double b0y, double b0z, double ux, double uy,
+                                           double uz, double l2) {
+  const double w0x = px - b0x, w0y = py - b0y, w0z = pz - b0z;
+  const double t0 = w0x * ux + w0y * uy + w0z * uz;
+  const double R0 = sqrt(w0x * w0x + w0y * w0y + w0z * w0z);
+  const double w1x = w0x - l2 * ux, w1y = w0y - l2 * uy, w1z = w0z - l2 * uz;
+  const double R1 = sqrt(w1x * w1x + w1y * w1y + w1z * w1z);
+  const double a = l2 - t0;
+  if (t0 <= 0.0) return log((R1 + a) / (R0 - t0));
+  if (a < 0.0) return log((R0 + t0) / (R1 - a));
+  const double rho2 = R0 * R0 - t0 * t0;
+  return log((R1 + a) * (R0 + t0) / rho2);
+}
+
+__device__ inline double point_segment_distance(double px, double py, double pz, double ax,
+                                                double ay, double az, double bx, double by,
+                                                double bz) {
+  const double dx = bx - ax, dy = by - ay, dz = bz - az;
+  const double wx = px - ax, wy = py - ay, wz = pz - az;
+  const double dd = dx * dx + dy * dy + dz * dz;
+  double t = dd > 0.0 ? (wx * dx + wy * dy + wz * dz) / dd : 0.0;
+  t = t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t);
+  const double ex = wx - t * dx, ey = wy - t * dy, ez = wz - t * dz;
+  return sqrt(ex * ex + ey * ey + ez * ez);
+}
+
+__device__ double pair_quadrature(double s1x, double s1y, double s1z, double e1x, double e1y,
+                                  double e1z, double s2x, double s2y, double s2z, double e2x,
+                                  double e2y, double e2z, const GaussRule16& g) {
+  const double d1x = e1x - s1x, d1y = e1y - s1y, d1z = e1z - s1z;
+  const double d2x = e2x - s2x, d2y = e2y - s2y, d2z = e2z - s2z;
+  const double l1 = sqrt(d1x * d1x + d1y * d1y + d1z * d1z);
+  const double l2 = sqrt(d2x * d2x + d2y * d2y + d2z * d2z);
+  const double ux = d2x / l2, uy = d2y / l2, uz = d2z / l2;
+  const double cosang = (d1x * d2x + d1y * d2y + d1z * d2z) / (l1 * l2);
+  double d = point_segment_distance(s1x, s1y, s1z, s2x, s2y, s2z, e2x, e2y, e2z);
+  d = fmin(d, point_segment_distance(e1x, e1y, e1z, s2x, s2y, s2z, e2x, e2y, e2z));
+  d = fmin(d, point_segment_distance(s2x, s2y, s2z, s1x, s1y, s1z, e1x, e1y, e1z));
+  d = fmin(d, point_segment_distance(e2x, e2y, e2z, s1x, s1y, s1z, e1x, e1y, e1z));
+  int m = 8;
+  if (d > 0.0) {
+    const double mm = ceil(l1 / d);
+    m = mm < 1.0 ? 1 : (mm > 8.0 ? 8 : (int)mm);
+  }
+  double acc = 0.0;
+  for (int q = 0; q < m; ++q)
+#pragma unroll 4
+    for (int i = 0; i < 16; ++i) {
+      const double sp = (q + 0.5 * (g.x[i] + 1.0)) / m;
+      acc += g.w[i] * inv_distance_line(s1x + sp * d1x, s1y + sp * d1y, s1z + sp * d1z, s2x,
+                                        s2y, s2z, ux, uy, uz, l2);
+    }
+  return kMu0Over4Pi * cosang * 0.5 * (l1 / m) * acc;
+}
+
+__device__ inline bool touches(double s1x, double s1y, double s1z, double e1x, double e1y,
+                               double e1z, double s2x, double s2y, double s2z, double e2x,
+                               double e2y, double e2z, double e2) {
+  auto d2 = [](double ax, double ay, double az, double bx, double by, double bz) {
+    return (ax - bx) * (ax - bx) + (ay - by) * (ay - by) + (az - bz) * (az - bz);
+  };
+  return d2(s1x, s1y, s1z, s2x, s2y, s2z) <= e2 || d2(s1x, s1y, s1z, e2x, e2y, e2z) <= e2 ||
+         d2(e1x, e1y, e1z, s2x, s2y, s2z) <= e2 || d2(e1x, e1y, e1z, e2x, e2y, e2z) <= e2;
+}
+
 __device__ inline double Gpar(double u, double d) { return u * asinh(u / d) - sqrt(u * u + d * d); }
 __device__ inline double Gcol(double u) {
   double a = fabs(u);
@@ -302,7 +404,8 @@ __device__ inline double Gcol(double u) {
 
 __device__ int pair_inductance(double s1x, double s1y, double s1z, double e1x, double e1y,
                                double e1z, double s2x, double s2y, double s2z, double e2x,
-                               double e2y, double e2z, double rw, bool self, double* out) {
+                               double e2y, double e2z, double rw, bool self, double* out,
+                               const GaussRule16& g) {
   double d1x = e1x - s1x, d1y = e1y - s1y, d1z = e1z - s1z;
   double d2x = e2x - s2x, d2y = e2y - s2y, d2z = e2z - s2z;
   double l1 = sqrt(d1x * d1x + d1y * d1y + d1z * d1z);
@@ -318,7 +421,13 @@ __device__ int pair_inductance(double s1x, double s1y, double s1z, double e1x, d
   double cr = sqrt(cx * cx + cy * cy + cz * cz);
   double tol = 1e-12 * l1 * l2;
   if (fabs(dot) <= tol) return 0;
-  if (cr > tol) return 1;
+  if (cr > tol) {  // oblique
+    if (touches(s1x, s1y, s1z, e1x, e1y, e1z, s2x, s2y, s2z, e2x, e2y, e2z,
+                1e-24 * (l1 + l2) * (l1 + l2)))
+      return 1;
+    *out = pair_quadrature(s1x, s1y, s1z, e1x, e1y, e1z, s2x, s2y, s2z, e2x, e2y, e2z, g);
+    return 0;
+  }
   double ux = d1x / l1, uy = d1y / l1, uz = d1z / l1;
   double wx = s2x - s1x, wy = s2y - s1y, wz = s2z - s1z;
   double bs = wx * ux + wy * uy + wz * uz;
@@ -344,7 +453,8 @@ __global__ void __launch_bounds__(kIndThreads) inductance_kernel(
     int n_struct, const int32_t* __restrict__ port_off, const int32_t* __restrict__ loop_vtx_off,
     const double* __restrict__ vx, const double* __restrict__ vy, const double* __restrict__ vz,
     const double* __restrict__ L_self, double rw, const int64_t* __restrict__ pair_off,
-    const int64_t* __restrict__ nn_off, double* __restrict__ M, int32_t* status) {
+    const int64_t* __restrict__ nn_off, double* __restrict__ M, int32_t* status,
+    GaussRule16 gauss) {
   __shared__ double red[kIndThreads];
   int64_t q = blockIdx.x;
   int s = find_struct_i64(pair_off, n_struct, q);
@@ -370,7 +480,7 @@ __global__ void __launch_bounds__(kIndThreads) inductance_kernel(
       int je = (j + 1 < lb) ? j + 1 : la;
       double m;
       int r = pair_inductance(vx[i], vy[i], vz[i], vx[ie], vy[ie], vz[ie], vx[j], vy[j], vz[j],
-                              vx[je], vy[je], vz[je], rw, (k == l && i == j), &m);
+                              vx[je], vy[je], vz[je], rw, (k == l && i == j), &m, gauss);
       if (r && !st) st = r;
       acc += m;
     }
@@ -513,7 +623,8 @@ cudaError_t launch_build_basis(const mts_problem* pb, mts_precision prec, void* 
   note_launch();
   inductance_kernel<<<(unsigned)npairs, kIndThreads, 0, st>>>(
       pb->n_struct, pb->port_off, pb->loop_vtx_off, pb->vx, pb->vy, pb->vz, pb->L_self,
-      pb->wire_radius, t.pair_off, t.nn_off, (double*)(B + bl.M64), (int32_t*)(B + bl.status));
+      pb->wire_radius, t.pair_off, t.nn_off, (double*)(B + bl.M64), (int32_t*)(B + bl.status),
+      gauss_legendre16());
   note_launch();
   msplit_kernel<<<nblk(ps.sumNN, 256), 256, 0, st>>>(ps.sumNN, (const double*)(B + bl.M64),
                                                       (float*)(B + bl.M32hi),

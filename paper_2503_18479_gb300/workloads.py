@@ -293,6 +293,28 @@ def loop_sweep(n_init: int = 100, n_target: int = 100, grid: int = 32,
                     target_per_cfg=True, meta=dict(n_init=n_init, n_target=n_target))
 
 
+def circle_array(nx: int = 3, ny: int = 3, seed: int = 0, n_cfg: int = 64, n_freq: int = 3,
+                 radius: float = 0.025, pitch: float = 0.055, n_seg: int = 64,
+                 grid: int = 24) -> Workload:
+    """An nx x ny array of circular loops (regular n_seg-gons of the given radius); the
+    mutual inductances couple oblique segment pairs, the self inductances take the
+    closed-form loop value."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    rw = 0.001
+    loops = [circular_loop(radius, n_seg, (i - (nx - 1) / 2.0) * pitch, (j - (ny - 1) / 2.0) * pitch)
+             for j in range(ny) for i in range(nx)]
+    omega = 2 * np.pi * np.linspace(60 * MHZ, 68 * MHZ, n_freq)
+    hx, hy = (nx + 1) * pitch / 2.0, (ny + 1) * pitch / 2.0
+    pts = _concat_points(grid_plane(grid, hx, 0.020, half_span_y=hy),
+                         _cell_centre_points(nx, ny, pitch, 0.040))
+    loss_idx = np.arange(grid * grid, grid * grid + nx * ny)
+    Ls = np.full(nx * ny, circular_loop_inductance(radius, rw))
+    st = _structure_from(loops, pts, omega, 0.1, loss_idx, L_self=Ls, label=f"circles_{nx}x{ny}")
+    C = rng.uniform(20 * PF, 200 * PF, size=(n_cfg, nx * ny))
+    target = rng.standard_normal(n_freq * nx * ny) * 1e-6
+    return Workload(f"circles_{nx}x{ny}", [st], C, rw, target=target, meta=dict(seed=seed))
+
+
 def line_8x1(seed: int = 0, n_cfg: int = 1024, n_freq: int = 201, grid: int = 64) -> Workload:
     rng = np.random.Generator(np.random.PCG64(seed))
     loops = square_array(8, 1)

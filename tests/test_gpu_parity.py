@@ -45,8 +45,10 @@ _CASES = {
     # configurations take the tensor-core superposition, 3 the SIMT one
     "32x32": lambda: W.array_32x32(seed=2, n_cfg=20, grid=12, planes=(0.02,), seg_per_side=2),
     "32x32few": lambda: W.array_32x32(seed=3, n_cfg=3, grid=12, planes=(0.02,), seg_per_side=2),
-    # 80 ports: the large-system kernel with the matrix in shared memory in FP64 as well
+    # 80 ports: the large-system kernel at 128 threads in both precisions
     "10x8": lambda: small_rect(10, 8, n_cfg=20, n_freq=2, grid=10, seed=4),
+    # circular loops: mutual inductances from oblique segment pairs (quadrature)
+    "circles": lambda: W.circle_array(3, 3, seed=6, n_cfg=40, n_freq=3, grid=12),
 }
 _cache = {}
 
