@@ -136,6 +136,13 @@ typedef struct mts_problem {
  *   correction no longer halves (the residual precision, about cond(A) * 2^-45 relative,
  *   is reached); such a system is flagged if it missed refine_tol. max_refine: refinement
  *   steps per solve (0 selects 8).
+ * Schedule (results agree to rounding whatever the choice; an autotuner may time them):
+ *   simt_max_sys  superposition of a structure on the SIMT kernel when its configurations x
+ *                 frequencies are at most this, else on the tensor cores (MTS_MIXED,
+ *                 MTS_BF16); 0 selects 16, a negative value puts every structure on the
+ *                 tensor cores. Memory does not depend on it.
+ *   large_threads threads per system of the blocked solve for N > 64: 128 or 256; 0 selects
+ *                 128 for N <= 128 and 256 above. Other values give MTS_EINVAL.
  */
 typedef struct mts_eval {
   int64_t n_cfg;
@@ -147,6 +154,8 @@ typedef struct mts_eval {
   int32_t loss_mode; /* mts_loss_mode */
   double refine_tol;
   int32_t max_refine;
+  int32_t simt_max_sys;
+  int32_t large_threads;
 } mts_eval;
 
 /* Human-readable name of a status code (static string). */

@@ -73,6 +73,9 @@ def _load():
             lib.oracle_segment_pair_quadrature.argtypes = [p, p, p, p, ct.c_int]
             lib.oracle_gauss_legendre.restype = None
             lib.oracle_gauss_legendre.argtypes = [ct.c_int, p, p]
+            lib.oracle_gradient_omega_v.restype = ct.c_int
+            lib.oracle_gradient_omega_v.argtypes = [i32, p, p, p, i64, p, i32, p, p, i32, p, p,
+                                                    i32, i32, p, p]
             lib.oracle_gradient_rl.restype = ct.c_int
             lib.oracle_gradient_rl.argtypes = [i32, p, p, p, i64, p, i32, p, p, i32, p, p, i32,
                                                i32, p, p]
@@ -250,6 +253,23 @@ def gradient_rl(H, M, R, C, omega, V, loss_idx, target, mode: int = 0, target_pe
                                _ptr(V), len(li), _ptr(li), _ptr(t), int(target_per_cfg), int(mode),
                                _ptr(gR), _ptr(gL))
     return gR, gL
+
+
+def gradient_omega_v(H, M, R, C, omega, V, loss_idx, target, mode: int = 0,
+                     target_per_cfg: bool = False):
+    """(d loss / d omega with V fixed [n_cfg, F], d loss / d V cotangent [n_cfg, F, N])."""
+    H, M, R, C, omega = _f64(H), _f64(M), _f64(R), _f64(np.atleast_2d(C)), _f64(np.atleast_1d(omega))
+    V = _c128(np.atleast_2d(V))
+    P, N = H.shape
+    n_cfg, F = C.shape[0], len(omega)
+    li = _i64(loss_idx)
+    t = _target_arr(np.asarray(target), mode)
+    gw = np.zeros((n_cfg, F))
+    gV = np.zeros((n_cfg, F, N), np.complex128)
+    _load().oracle_gradient_omega_v(N, _ptr(H), _ptr(M), _ptr(R), n_cfg, _ptr(C), F, _ptr(omega),
+                                    _ptr(V), len(li), _ptr(li), _ptr(t), int(target_per_cfg),
+                                    int(mode), _ptr(gw), _ptr(gV))
+    return gw, gV
 
 
 def gradient_field(H, M, R, C, omega, V, gB):

@@ -614,6 +614,67 @@ int oracle_gradient_rl(int32_t N, const double* H, const double* M, const double
   return n_bad;
 }
 
+/* Gradients of the same objective with respect to the angular frequencies w_f (with the
+ * drive V held fixed) and to the drive V itself. With mu = A^-1 H_loss^T conj(G) as above:
+ *   dA/dw = j M + diag(j / (w^2 C))  (d(1/(j w C))/dw = -1/(j w^2 C)), so
+ *   dloss/dw_f = -Re(mu^T dA/dw I) = Im(mu^T M I) + sum_k Im(mu_k I_k) / (w^2 C_k);
+ *   dI = A^-1 dV gives dloss = Re(mu^T dV), i.e. the cotangent dL/dRe V + j dL/dIm V =
+ *   conj(mu). Both divided by F*L like the loss. Writes gw[b][F] and gV[b][F][N] (complex).
+ * Returns the number of singular systems. */
+int oracle_gradient_omega_v(int32_t N, const double* H, const double* M, const double* R,
+                            int64_t n_cfg, const double* C, int32_t F, const double* omega,
+                            const double complex* V, int32_t L, const int64_t* loss_idx,
+                            const double* target, int32_t target_per_cfg, int32_t mode,
+                            double* gw, double complex* gV) {
+  int n_bad = 0;
+  const int64_t tw = (mode == 0) ? 1 : 2;
+  const double nrm = (F * L > 0) ? 1.0 / ((double)F * L) : 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : n_bad)
+  for (int64_t b = 0; b < n_cfg; ++b) {
+    double complex* A = malloc(sizeof(double complex) * (size_t)N * N);
+    int32_t* piv = malloc(sizeof(int32_t) * (size_t)N);
+    double complex* x = malloc(sizeof(double complex) * (size_t)N);
+    double complex* mu = malloc(sizeof(double complex) * (size_t)N);
+    const double* Cb = C + b * N;
+    for (int32_t f = 0; f < F; ++f) {
+      gw[b * F + f] = 0.0;
+      for (int32_t k = 0; k < N; ++k) gV[(b * F + f) * N + k] = 0.0;
+      oracle_assemble(N, M, R, omega[f], Cb, A);
+      if (oracle_lu(N, A, piv) != 0) {
+        n_bad += 1;
+        continue;
+      }
+      memcpy(x, V + (int64_t)f * N, sizeof(double complex) * (size_t)N);
+      oracle_lu_solve(N, A, piv, x);
+      const double* t = target + (target_per_cfg ? b * (int64_t)F * L * tw : 0);
+      for (int32_t k = 0; k < N; ++k) mu[k] = 0.0;
+      for (int32_t l = 0; l < L; ++l) {
+        double complex s = 0.0, G;
+        for (int32_t k = 0; k < N; ++k) s += H[loss_idx[l] * N + k] * x[k];
+        oracle_point_loss(mode, s, t + ((int64_t)f * L + l) * tw, &G);
+        for (int32_t k = 0; k < N; ++k) mu[k] += H[loss_idx[l] * N + k] * conj(G);
+      }
+      oracle_lu_solve(N, A, piv, mu); /* A^T = A */
+      const double w = omega[f];
+      double complex muMI = 0.0;
+      double diag = 0.0;
+      for (int32_t k = 0; k < N; ++k) {
+        double complex MI = 0.0;
+        for (int32_t l = 0; l < N; ++l) MI += M[k * N + l] * x[l];
+        muMI += mu[k] * MI;
+        diag += cimag(mu[k] * x[k]) / (w * w * Cb[k]);
+        gV[(b * F + f) * N + k] = conj(mu[k]) * nrm;
+      }
+      gw[b * F + f] = (cimag(muMI) + diag) * nrm;
+    }
+    free(A);
+    free(piv);
+    free(x);
+    free(mu);
+  }
+  return n_bad;
+}
+
 /* Gradient with respect to C for an arbitrary field cotangent (the torch convention
  * gB = dL/dRe B + j dL/dIm B over the full field B[b][f][P]):
  * dL/dC_k = sum_f Im(mu_k I_k)/(w C_k^2) with mu = A^-1 H^T conj(gB[b][f]). */

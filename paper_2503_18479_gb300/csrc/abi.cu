@@ -92,18 +92,18 @@ PlanLayout plan_layout(int n_struct) {
 
 // Elements of the tensor-core B operand, and the GEMM / SIMT work units of the superposition.
 static int64_t bop_elems(const mts_problem* pb, int64_t n_cfg, int npieces, int64_t* units,
-                         int64_t* simt_units = nullptr, int64_t* max_simt = nullptr) {
+                         int64_t* simt_units = nullptr, int64_t* max_simt = nullptr,
+                         int64_t simt_max_sys = kSimtSys) {
   int64_t a = 0, u = 0, v = 0, vmax = 0;
   for (int s = 0; s < pb->n_struct; ++s) {
     int64_t N = pb->h_port_off[s + 1] - pb->h_port_off[s];
     int64_t P = pb->h_point_off[s + 1] - pb->h_point_off[s];
     int64_t F = pb->h_freq_off[s + 1] - pb->h_freq_off[s];
-    if (use_tensor_path(npieces, n_cfg, F)) {
-      int64_t nn = (2 * n_cfg * F + kTileN - 1) / kTileN;
-      int64_t npt = (P + kTileP - 1) / kTileP;
-      int64_t nkc = (N + kChunkK - 1) / kChunkK;
-      a += (int64_t)npieces * nn * nkc * kTileN * kChunkK;
-      u += npt * nn;
+    // the B operand exists for every structure (the schedule does not change memory)
+    const int64_t nn = (2 * n_cfg * F + kTileN - 1) / kTileN;
+    a += (int64_t)npieces * nn * ((N + kChunkK - 1) / kChunkK) * kTileN * kChunkK;
+    if (use_tensor_path(npieces, n_cfg, F, simt_max_sys)) {
+      u += (P + kTileP - 1) / kTileP * nn;
     } else {
       const int64_t vs = (P + kSimtPts - 1) / kSimtPts * ((n_cfg * F + kSimtSys - 1) / kSimtSys);
       v += vs;
@@ -173,8 +173,14 @@ static mts_status validate_prec(mts_precision prec) {
   return (prec == MTS_FP64 || prec == MTS_MIXED || prec == MTS_BF16) ? MTS_OK : MTS_EINVAL;
 }
 
+static int64_t simt_threshold(const mts_eval* ev) {
+  return ev->simt_max_sys == 0 ? kSimtSys : ev->simt_max_sys;
+}
+
 static mts_status validate_eval(const mts_problem* pb, const mts_eval* ev) {
   if (!ev) return MTS_EINVAL;
+  if (ev->large_threads != 0 && ev->large_threads != 128 && ev->large_threads != 256)
+    return MTS_EINVAL;
   if (ev->n_cfg < 0) return MTS_EINVAL;
   if (ev->n_cfg > 0 && !ev->C) return MTS_EINVAL;
   if (pb->n_freq > 0 && (!ev->omega || !ev->V)) return MTS_EINVAL;
@@ -242,6 +248,7 @@ static SolveArgs solve_args(const mts_problem* pb, mts_precision prec, const voi
   a.lu = T + tl.lu;
   a.mu_out = reinterpret_cast<double*>(T + tl.mu_loss);
   a.max_loss = max_loss_points(pb);
+  a.large_threads = ev->large_threads;
   a.rhs_in = nullptr;
   return a;
 }
@@ -362,7 +369,8 @@ mts_status mts_solve(const mts_problem* pb, mts_precision prec, const void* basi
   char* T = static_cast<char*>(tape);
   cudaError_t e = cudaMemsetAsync(T + tl.err, 0, 16, st);
   if (e == cudaSuccess)
-    e = launch_plan(pb, ev->n_cfg, n_pieces(prec), reinterpret_cast<int64_t*>(T + tl.plan + pl.bop_off),
+    e = launch_plan(pb, ev->n_cfg, n_pieces(prec), simt_threshold(ev),
+                    reinterpret_cast<int64_t*>(T + tl.plan + pl.bop_off),
                     reinterpret_cast<int64_t*>(T + tl.plan + pl.unit_off),
                     reinterpret_cast<int64_t*>(T + tl.plan + pl.lu_off),
                     reinterpret_cast<int64_t*>(T + tl.plan + pl.simt_off), st);
@@ -406,7 +414,8 @@ mts_status mts_superpose(const mts_problem* pb, mts_precision prec, const void* 
   a.n_cfg = ev->n_cfg;
   a.sumFN = ps.sumFN;
   a.sumFP = ps.sumFP;
-  bop_elems(pb, ev->n_cfg, n_pieces(prec), &a.total_units, &a.total_simt, &a.max_simt);
+  bop_elems(pb, ev->n_cfg, n_pieces(prec), &a.total_units, &a.total_simt, &a.max_simt,
+            simt_threshold(ev));
   a.unit_off = reinterpret_cast<const int64_t*>(T + tl.plan + pl.unit_off);
   a.simt_off = reinterpret_cast<const int64_t*>(T + tl.plan + pl.simt_off);
   a.H = B + bl.H;

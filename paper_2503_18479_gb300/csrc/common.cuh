@@ -57,15 +57,16 @@ __host__ __device__
 inline int port_class(int64_t N) { return N <= 8 ? 0 : N <= 16 ? 1 : N <= 32 ? 2 : N <= 64 ? 3 : 4; }
 
 // Superposition schedule of a structure: the tensor-core GEMM when its configurations x
-// frequencies fill column tiles, else the SIMT kernel (H read once, no padded columns).
-// MTS_FP64 (npieces == 0) always takes the SIMT kernel.
+// frequencies exceed the threshold (column tiles fill), else the SIMT kernel (H read once,
+// no padded columns). MTS_FP64 (npieces == 0) always takes the SIMT kernel; a negative
+// threshold puts every structure of the other precisions on the tensor cores.
 constexpr int kSimtPts = 128;  // points per SIMT unit (one per thread)
-constexpr int kSimtSys = 16;   // systems per SIMT unit
+constexpr int kSimtSys = 16;   // systems per SIMT unit, and the default threshold
 #ifdef __CUDACC__
 __host__ __device__
 #endif
-inline bool use_tensor_path(int npieces, int64_t n_cfg, int64_t F) {
-  return npieces > 0 && n_cfg * F > kSimtSys;
+inline bool use_tensor_path(int npieces, int64_t n_cfg, int64_t F, int64_t simt_max_sys) {
+  return npieces > 0 && (simt_max_sys < 0 || n_cfg * F > simt_max_sys);
 }
 
 // Each structure's H block starts at a multiple of 32 elements (128 bytes), so that its rows

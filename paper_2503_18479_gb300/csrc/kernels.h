@@ -45,6 +45,7 @@ struct SolveArgs {
   // configurations x the gcount frequencies glist[0 .. gcount-1] of one port class
   const int32_t* glist;
   int64_t gcount;
+  int large_threads;  // 0: 128 for N <= 128, else 256
   int npieces;
   int max_loss;  // max loss points of one structure (uniform trip count for group loops)
   // backward (field cotangent) mode: solve A mu = rhs_in and write grad terms only
@@ -73,8 +74,9 @@ cudaError_t launch_export_basis(const mts_problem* pb, mts_precision prec, const
                                 double* M_out, cudaStream_t st);
 
 // Per-call plan tables in the tape (bases of the B operand, GEMM unit prefixes).
-cudaError_t launch_plan(const mts_problem* pb, int64_t n_cfg, int npieces, int64_t* bop_off,
-                        int64_t* unit_off, int64_t* lu_off, int64_t* simt_off, cudaStream_t st);
+cudaError_t launch_plan(const mts_problem* pb, int64_t n_cfg, int npieces, int64_t simt_max_sys,
+                        int64_t* bop_off, int64_t* unit_off, int64_t* lu_off, int64_t* simt_off,
+                        cudaStream_t st);
 
 // Solve of every system: the register-resident kernels for N <= kRegMaxPorts, the blocked
 // large-system kernel (solve_large.cu) for the others.

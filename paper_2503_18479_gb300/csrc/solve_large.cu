@@ -565,7 +565,7 @@ static cudaError_t launch_large(const SolveArgs& a, int64_t n_sys, int min_ports
 cudaError_t launch_solve_large(const SolveArgs& a, mts_precision prec, int64_t n_sys, int min_ports,
                                int max_ports, void* scratch, cudaStream_t st) {
   if (n_sys == 0) return cudaSuccess;
-  const bool small = large_threads(max_ports) == 128;
+  const bool small = (a.large_threads ? a.large_threads : large_threads(max_ports)) == 128;
   if (prec == MTS_FP64)
     return small ? launch_large<double, 128>(a, n_sys, min_ports, max_ports, scratch, st)
                  : launch_large<double, 256>(a, n_sys, min_ports, max_ports, scratch, st);

@@ -16,8 +16,8 @@ namespace mts {
 __global__ void plan_kernel(int n_struct, int64_t n_cfg, const int32_t* __restrict__ port_off,
                             const int64_t* __restrict__ point_off,
                             const int32_t* __restrict__ freq_off, int npieces,
-                            int64_t* bop_off, int64_t* unit_off, int64_t* lu_off,
-                            int64_t* simt_off) {
+                            int64_t simt_max_sys, int64_t* bop_off, int64_t* unit_off,
+                            int64_t* lu_off, int64_t* simt_off) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   int64_t a = 0, u = 0, f = 0, v = 0;
   for (int s = 0; s < n_struct; ++s) {
@@ -28,12 +28,11 @@ __global__ void plan_kernel(int n_struct, int64_t n_cfg, const int32_t* __restri
     int64_t N = port_off[s + 1] - port_off[s];
     int64_t P = point_off[s + 1] - point_off[s];
     int64_t F = freq_off[s + 1] - freq_off[s];
-    if (use_tensor_path(npieces, n_cfg, F)) {
-      int64_t nn = (2 * n_cfg * F + kTileN - 1) / kTileN;
-      int64_t np = (P + kTileP - 1) / kTileP;
-      int64_t nkc = (N + kChunkK - 1) / kChunkK;
-      a += (int64_t)npieces * nn * nkc * kTileN * kChunkK;
-      u += np * nn;
+    // the B operand exists for every structure (the schedule does not change memory)
+    const int64_t nn = (2 * n_cfg * F + kTileN - 1) / kTileN;
+    a += (int64_t)npieces * nn * ((N + kChunkK - 1) / kChunkK) * kTileN * kChunkK;
+    if (use_tensor_path(npieces, n_cfg, F, simt_max_sys)) {
+      u += (P + kTileP - 1) / kTileP * nn;
     } else {
       v += (P + kSimtPts - 1) / kSimtPts * ((n_cfg * F + kSimtSys - 1) / kSimtSys);
     }
@@ -45,10 +44,11 @@ __global__ void plan_kernel(int n_struct, int64_t n_cfg, const int32_t* __restri
   simt_off[n_struct] = v;
 }
 
-cudaError_t launch_plan(const mts_problem* pb, int64_t n_cfg, int npieces, int64_t* bop_off,
-                        int64_t* unit_off, int64_t* lu_off, int64_t* simt_off, cudaStream_t st) {
+cudaError_t launch_plan(const mts_problem* pb, int64_t n_cfg, int npieces, int64_t simt_max_sys,
+                        int64_t* bop_off, int64_t* unit_off, int64_t* lu_off, int64_t* simt_off,
+                        cudaStream_t st) {
   plan_kernel<<<1, 32, 0, st>>>(pb->n_struct, n_cfg, pb->port_off, pb->point_off, pb->freq_off,
-                                npieces, bop_off, unit_off, lu_off, simt_off);
+                                npieces, simt_max_sys, bop_off, unit_off, lu_off, simt_off);
   note_launch();
   return cudaGetLastError();
 }

@@ -51,6 +51,7 @@ class MtsEval(ct.Structure):
         ("n_cfg", ct.c_int64), ("C", ct.c_void_p), ("omega", ct.c_void_p), ("V", ct.c_void_p),
         ("target", ct.c_void_p), ("target_per_cfg", ct.c_int32), ("loss_mode", ct.c_int32),
         ("refine_tol", ct.c_double), ("max_refine", ct.c_int32),
+        ("simt_max_sys", ct.c_int32), ("large_threads", ct.c_int32),
     ]
 
 
@@ -190,7 +191,8 @@ class Eval:
 
     def __init__(self, C: torch.Tensor, omega: torch.Tensor, V: torch.Tensor,
                  target: Optional[torch.Tensor] = None, target_per_cfg: bool = False,
-                 loss_mode: int = MTS_LOSS_ABS, refine_tol: float = 0.0, max_refine: int = 0):
+                 loss_mode: int = MTS_LOSS_ABS, refine_tol: float = 0.0, max_refine: int = 0,
+                 simt_max_sys: int = 0, large_threads: int = 0):
         self.C = C.contiguous()
         self.omega = omega.contiguous()
         self.V = V.contiguous()
@@ -205,6 +207,8 @@ class Eval:
         e.loss_mode = int(loss_mode)
         e.refine_tol = float(refine_tol)
         e.max_refine = int(max_refine)
+        e.simt_max_sys = int(simt_max_sys)
+        e.large_threads = int(large_threads)
         self.c = e
 
     @property

@@ -44,11 +44,15 @@ class Simulator:
         self.sumFN = int(sum(s.n_freq * s.n_ports for s in wl.structures))
         self.n_ports = wl.n_ports
         self.b_dtype = torch.complex128 if self.prec == nv.MTS_FP64 else torch.complex64
+        # launch schedule (mts_eval.simt_max_sys, large_threads); 0 = the library's rules,
+        # set by tune.autotune
+        self.tuning = {"simt_max_sys": 0, "large_threads": 0}
 
     # ------------------------------------------------------------------
     def make_eval(self, C: torch.Tensor, with_target: bool = True) -> nv.Eval:
         return nv.Eval(C, self.omega, self.V, self.target if with_target else None,
-                       self.target_per_cfg, self.loss_mode, self.refine_tol, self.max_refine)
+                       self.target_per_cfg, self.loss_mode, self.refine_tol, self.max_refine,
+                       **self.tuning)
 
     def alloc_tape(self, n_cfg: int) -> torch.Tensor:
         return nv.alloc_bytes(nv.mts_tape_bytes(self.pb, n_cfg, self.prec), self.device)

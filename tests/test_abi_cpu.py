@@ -212,3 +212,18 @@ def test_adam_step_validation(nv):
     assert call(good, step=None) == nv.MTS_EINVAL
     tanh = nv.MtsAdam(1e-13, 0.9, 0.999, 1e-8, nv.MTS_PROJ_TANH, 1e-11, 2e-10)
     assert call(tanh, u=None) == nv.MTS_EINVAL
+
+
+def test_schedule_fields_are_validated(nv):
+    """large_threads must be 0, 128 or 256; the schedule does not change the tape size."""
+    L = nv.lib()
+    wl = W.array_8x8(n_cfg=2, grid=4, planes=(0.02,))
+    c, keep = fake_problem(nv, wl)
+    ev = nv.MtsEval()
+    ev.n_cfg = 2
+    ev.C = ev.omega = ev.V = FAKE
+    tneed = L.mts_tape_bytes(ct.byref(c), 2, nv.MTS_MIXED)
+    ev.large_threads = 64
+    code = L.mts_solve(ct.byref(c), nv.MTS_MIXED, ct.c_void_p(FAKE), ct.byref(ev), None, None,
+                       ct.c_void_p(FAKE), tneed, None)
+    assert code == nv.MTS_EINVAL

@@ -655,3 +655,39 @@ def test_coaxial_circles_maxwell():
     m1, m2 = polygon_pair(128), polygon_pair(256)
     assert abs(m2 / exact - 1) < 1e-3
     assert abs((4 * m2 - m1) / 3 / exact - 1) < 1e-6
+
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_gradient_omega_and_drive_central_differences(mode):
+    """dloss/dw_f (V held fixed) and the cotangent of V (dL/dRe V + j dL/dIm V) from the
+    adjoint versus Richardson-extrapolated central differences of the oracle loss."""
+    H, M, R, C, omega, V, li, t = _grad_case(mode)
+    gw, gV = oracle.gradient_omega_v(H, M, R, C, omega, V, li, t, mode=mode)
+    F, N = len(omega), C.shape[1]
+
+    def loss(om, VV):
+        return oracle.forward(H, M, R, C, om, VV, li, t, mode=mode, want_B=False)["loss"]
+
+    def cd_w(h):
+        fd = np.zeros_like(gw)
+        for f in range(F):
+            op, om = np.array(omega, float), np.array(omega, float)
+            op[f] += h
+            om[f] -= h
+            fd[:, f] = (loss(op, V) - loss(om, V)) / (2 * h)
+        return fd
+
+    w1, w2 = cd_w(1e2), cd_w(0.5e2)  # w ~ 4e8 rad/s
+    assert _rel(gw, (4 * w2 - w1) / 3) < 1e-6
+    V = np.asarray(V)
+    scale = np.abs(V).max()
+    for f, k in ((0, 0), (F - 1, N - 1), (1, 3)):
+        for part in (1.0, 1j):
+            h = 1e-6 * scale
+            Vp, Vm = V.copy(), V.copy()
+            Vp[f, k] += part * h
+            Vm[f, k] -= part * h
+            fd = (loss(omega, Vp) - loss(omega, Vm)) / (2 * h)
+            want = gV[:, f, k].real if part == 1.0 else gV[:, f, k].imag
+            assert _rel(want, fd) < 1e-6
