@@ -236,20 +236,24 @@ mts_status mts_backward(const mts_problem* pb, mts_precision prec, const void* b
                         const void* grad_B, const double* grad_loss, double* grad_C,
                         mts_stream stream);
 
-/* mts_param_grad: gradients of the objective with respect to the loop resistances R_k and
- * the self inductances L_k = M_kk (Fig. 2 of the paper names R, L, C and w as optimisation
- * variables), from the adjoint solution mu the forward kept in the tape:
- *   grad_R[b][port] = grad_loss[b][s] * sum_f -Re(mu_k I_k) / (F_s L_s)
- *   grad_L[b][port] = grad_loss[b][s] * sum_f  w Im(mu_k I_k) / (F_s L_s)
- * (dA/dR_k = e_k e_k^T and dA/dM_kk = j w e_k e_k^T in d(A^-1) = -A^-1 dA A^-1, Eq. 8-9).
- * Needs a preceding mts_solve / mts_forward on this tape with ev->target (the objective's
- * adjoint); covers the loss cotangent only (not a field cotangent grad_B). grad_loss device
- * [n_cfg][n_struct] or NULL (all ones); grad_R, grad_L device [n_cfg][n_ports] or NULL (at
- * least one given). MTS_EINVAL if ev has no target or both outputs are NULL. */
+/* mts_param_grad: gradients of the objective with respect to the other parameters Fig. 2
+ * of the paper names as optimisation variables (R, L, w) and to the drive, from the adjoint
+ * solution mu the forward kept in the tape (d(A^-1) = -A^-1 dA A^-1, Eq. 8-9):
+ *   grad_R[b][port]  = g sum_f -Re(mu_k I_k)            (dA/dR_k = e_k e_k^T)
+ *   grad_L[b][port]  = g sum_f  w Im(mu_k I_k)          (L_k = M_kk, dA/dM_kk = j w e_k e_k^T)
+ *   grad_omega[b][g] = g (Im(mu^T M I) + sum_k Im(mu_k I_k)/(w^2 C_k))  (V held fixed;
+ *                      dA/dw = j M + diag(j/(w^2 C)))
+ *   grad_V[b][FN]    = g conj(mu)                       (dL/dRe V + j dL/dIm V; complex)
+ * with g = grad_loss[b][s] / (F_s L_s). Needs a preceding mts_solve / mts_forward on this
+ * tape with ev->target (the objective's adjoint); covers the loss cotangent only (not a field
+ * cotangent grad_B). grad_loss device [n_cfg][n_struct] or NULL (all ones); grad_R, grad_L
+ * device [n_cfg][n_ports], grad_omega device [n_cfg][n_freq], grad_V device complex
+ * [n_cfg][FN], each may be NULL (at least one given). grad_omega costs an N^2 FP64 product
+ * per system. MTS_EINVAL if ev has no target or every output is NULL. */
 mts_status mts_param_grad(const mts_problem* pb, mts_precision prec, const void* basis,
                           const mts_eval* ev, const void* tape, size_t tape_bytes,
                           const double* grad_loss, double* grad_R, double* grad_L,
-                          mts_stream stream);
+                          double* grad_omega, double* grad_V, mts_stream stream);
 
 /* Synchronises `stream` and summarises the per-system status of the last forward on
  * this tape: MTS_OK, or MTS_ENOCONV if any system missed the refinement tolerance or

@@ -519,19 +519,29 @@ mts_status mts_tape_status(const mts_problem* pb, int64_t n_cfg, mts_precision p
 mts_status mts_param_grad(const mts_problem* pb, mts_precision prec, const void* basis,
                           const mts_eval* ev, const void* tape, size_t tape_bytes,
                           const double* grad_loss, double* grad_R, double* grad_L,
-                          mts_stream stream) {
+                          double* grad_omega, double* grad_V, mts_stream stream) {
   mts_status v = check_solve_args(pb, prec, basis, ev, const_cast<void*>(tape), tape_bytes);
   if (v != MTS_OK) return v;
-  if (!ev->target || (!grad_R && !grad_L)) return MTS_EINVAL;
+  if (!ev->target || (!grad_R && !grad_L && !grad_omega && !grad_V)) return MTS_EINVAL;
   BasisLayout bl = basis_layout(pb, prec);
   TapeLayout tl = tape_layout(pb, ev->n_cfg, prec);
   ProblemSums ps = problem_sums(pb, prec);
   const char* T = static_cast<const char*>(tape);
-  return cuda_status(launch_param_grad(
-      ev->n_cfg, pb->n_struct, pb->n_ports, pb->port_off, pb->freq_off, pb->loss_off,
-      dev_tables(basis, bl, pb->n_struct, pb->n_freq), ps.sumFN, ev->omega,
-      reinterpret_cast<const double*>(T + tl.I), reinterpret_cast<const double*>(T + tl.mu_loss),
-      grad_loss, grad_R, grad_L, (cudaStream_t)stream));
+  const char* Bz = static_cast<const char*>(basis);
+  const DevTables t = dev_tables(basis, bl, pb->n_struct, pb->n_freq);
+  const double* I = reinterpret_cast<const double*>(T + tl.I);
+  const double* mu = reinterpret_cast<const double*>(T + tl.mu_loss);
+  cudaError_t e = cudaSuccess;
+  if (grad_R || grad_L)
+    e = launch_param_grad(ev->n_cfg, pb->n_struct, pb->n_ports, pb->port_off, pb->freq_off,
+                          pb->loss_off, t, ps.sumFN, ev->omega, I, mu, grad_loss, grad_R, grad_L,
+                          (cudaStream_t)stream);
+  if (e == cudaSuccess && (grad_omega || grad_V))
+    e = launch_omega_v_grad(ev->n_cfg, pb->n_freq, pb->n_struct, pb->n_ports, pb->port_off,
+                            pb->freq_off, pb->loss_off, t, ps.sumFN, ev->omega, ev->C,
+                            reinterpret_cast<const double*>(Bz + bl.M64), I, mu, grad_loss,
+                            grad_omega, grad_V, (cudaStream_t)stream);
+  return cuda_status(e);
 }
 
 mts_status mts_adam_step(int64_t n, const mts_adam* opt, double* C, double* u,

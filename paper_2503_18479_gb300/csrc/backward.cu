@@ -177,6 +177,91 @@ cudaError_t launch_param_grad(int64_t n_cfg, int n_struct, int n_ports, const in
   return cudaGetLastError();
 }
 
+// dloss/dw_g with the drive held fixed (dA/dw = j M + diag(j/(w^2 C))):
+//   Im(mu^T M I) + sum_k Im(mu_k I_k)/(w^2 C_k), divided by F_s L_s, times the loss cotangent.
+// One warp per system (b, g); FP64 (an N^2 product per system).
+__global__ void omega_grad_kernel(int64_t n_cfg, int n_freq, int n_struct, int n_ports,
+                                  const int32_t* __restrict__ port_off,
+                                  const int32_t* __restrict__ freq_off,
+                                  const int32_t* __restrict__ loss_off, DevTables t,
+                                  int64_t sumFN, const double* __restrict__ omega,
+                                  const double* __restrict__ C, const double* __restrict__ M64,
+                                  const double* __restrict__ I, const double* __restrict__ mu,
+                                  const double* __restrict__ grad_loss,
+                                  double* __restrict__ grad_w) {
+  const int64_t sys = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (sys >= n_cfg * n_freq) return;  // warp-uniform
+  const int64_t b = sys / n_freq;
+  const int g = (int)(sys - b * n_freq);
+  const int s = t.freq_struct[g];
+  const int k0 = port_off[s], N = port_off[s + 1] - k0;
+  const int F = freq_off[s + 1] - freq_off[s], f = g - freq_off[s];
+  const int L = loss_off[s + 1] - loss_off[s];
+  const double w = omega[g];
+  const double* Ms = M64 + t.nn_off[s];
+  const int64_t o = 2 * (b * sumFN + t.fn_off[s] + (int64_t)f * N);
+  double im_muMI = 0.0, diag = 0.0;
+  for (int k = lane; k < N; k += 32) {
+    double tx = 0.0, ty = 0.0;  // (M I)_k
+    for (int l = 0; l < N; ++l) {
+      const double m = Ms[(int64_t)k * N + l];
+      tx = fma(m, I[o + 2 * l], tx);
+      ty = fma(m, I[o + 2 * l + 1], ty);
+    }
+    const double ux = mu[o + 2 * k], uy = mu[o + 2 * k + 1];
+    im_muMI += ux * ty + uy * tx;
+    const double ck = C[b * n_ports + k0 + k];
+    diag += (ux * I[o + 2 * k + 1] + uy * I[o + 2 * k]) / (w * w * ck);
+  }
+  double v = im_muMI + diag;
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  if (lane == 0) {
+    double scale = (F * L > 0) ? 1.0 / ((double)F * L) : 0.0;
+    if (grad_loss) scale *= grad_loss[b * n_struct + s];
+    grad_w[b * n_freq + g] = v * scale;
+  }
+}
+
+// cotangent of the drive (dL/dRe V + j dL/dIm V) = conj(mu) / (F_s L_s) times the loss cotangent
+__global__ void drive_grad_kernel(int64_t n_cfg, int n_struct, const int32_t* __restrict__ freq_off,
+                                  const int32_t* __restrict__ loss_off, DevTables t, int64_t sumFN,
+                                  const double* __restrict__ mu, const double* __restrict__ grad_loss,
+                                  double* __restrict__ grad_V) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_cfg * sumFN) return;
+  const int64_t b = i / sumFN, e = i - b * sumFN;
+  const int s = find_struct_i64(t.fn_off, n_struct, e);
+  const int F = freq_off[s + 1] - freq_off[s], L = loss_off[s + 1] - loss_off[s];
+  double scale = (F * L > 0) ? 1.0 / ((double)F * L) : 0.0;
+  if (grad_loss) scale *= grad_loss[b * n_struct + s];
+  grad_V[2 * i] = mu[2 * i] * scale;
+  grad_V[2 * i + 1] = -mu[2 * i + 1] * scale;
+}
+
+cudaError_t launch_omega_v_grad(int64_t n_cfg, int n_freq, int n_struct, int n_ports,
+                                const int32_t* port_off, const int32_t* freq_off,
+                                const int32_t* loss_off, DevTables t, int64_t sumFN,
+                                const double* omega, const double* C, const double* M64,
+                                const double* I, const double* mu, const double* grad_loss,
+                                double* grad_w, double* grad_V, cudaStream_t st) {
+  if (grad_w && n_cfg * n_freq > 0) {
+    const int64_t threads = n_cfg * n_freq * 32;
+    omega_grad_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
+        n_cfg, n_freq, n_struct, n_ports, port_off, freq_off, loss_off, t, sumFN, omega, C, M64,
+        I, mu, grad_loss, grad_w);
+    note_launch();
+  }
+  if (grad_V && n_cfg * sumFN > 0) {
+    const int64_t n = n_cfg * sumFN;
+    drive_grad_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n_cfg, n_struct, freq_off,
+                                                                  loss_off, t, sumFN, mu,
+                                                                  grad_loss, grad_V);
+    note_launch();
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_count_bad(const int32_t* status, int64_t n, int32_t* out, cudaStream_t st) {
   cudaMemsetAsync(out, 0, sizeof(int32_t), st);
   if (n > 0) {

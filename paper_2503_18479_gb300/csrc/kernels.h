@@ -142,6 +142,14 @@ cudaError_t launch_grad_combine(int64_t n_cfg, int n_struct, int n_ports,
 
 cudaError_t launch_count_bad(const int32_t* status, int64_t n, int32_t* out, cudaStream_t st);
 
+// dloss/dw (drive fixed) and the drive cotangent from the stored adjoint solutions
+cudaError_t launch_omega_v_grad(int64_t n_cfg, int n_freq, int n_struct, int n_ports,
+                                const int32_t* port_off, const int32_t* freq_off,
+                                const int32_t* loss_off, DevTables t, int64_t sumFN,
+                                const double* omega, const double* C, const double* M64,
+                                const double* I, const double* mu, const double* grad_loss,
+                                double* grad_w, double* grad_V, cudaStream_t st);
+
 // dloss/dR and dloss/dL (self inductances) from the stored adjoint solutions and currents
 cudaError_t launch_param_grad(int64_t n_cfg, int n_struct, int n_ports, const int32_t* port_off,
                               const int32_t* freq_off, const int32_t* loss_off, DevTables t,

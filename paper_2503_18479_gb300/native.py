@@ -103,7 +103,7 @@ def lib():
             L.mts_solve_static.restype = ct.c_int
             L.mts_solve_static.argtypes = [PP, ct.c_int, p, PE, p, p, p, p]
             L.mts_param_grad.restype = ct.c_int
-            L.mts_param_grad.argtypes = [PP, ct.c_int, p, PE, p, sz, p, p, p, p]
+            L.mts_param_grad.argtypes = [PP, ct.c_int, p, PE, p, sz, p, p, p, p, p, p]
             L.mts_adam_step.restype = ct.c_int
             L.mts_adam_step.argtypes = [i64, ct.POINTER(MtsAdam), p, p, p, p, p, p, p, i64, p, i64, p]
             L.mts_tape_status.restype = ct.c_int
@@ -317,8 +317,10 @@ def mts_adam_step(n: int, opt: MtsAdam, C, u, grad_C, m, v, step, loss=None, los
 
 
 def mts_param_grad(pb, prec, basis, ev: Eval, tape, grad_loss=None, grad_R=None, grad_L=None,
-                   stream=None):
-    """dloss/dR and dloss/dL (self inductances) after a forward with a target."""
+                   grad_omega=None, grad_V=None, stream=None):
+    """dloss/dR, dloss/dL (self inductances), dloss/domega (drive fixed) and the drive
+    cotangent after a forward with a target."""
     _check(lib().mts_param_grad(pb.ref, _prec(prec), _ptr(basis), ev.ref, _ptr(tape),
                                 tape.numel() * tape.element_size(), _ptr(grad_loss),
-                                _ptr(grad_R), _ptr(grad_L), _stream(stream)), "mts_param_grad")
+                                _ptr(grad_R), _ptr(grad_L), _ptr(grad_omega), _ptr(grad_V),
+                                _stream(stream)), "mts_param_grad")

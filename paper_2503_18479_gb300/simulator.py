@@ -82,14 +82,21 @@ class Simulator:
         nv.mts_backward(self.pb, self.prec, self.basis, ev, tape, gB, gl, grad_C, stream)
         return grad_C
 
-    def param_grad(self, ev: nv.Eval, tape: torch.Tensor, grad_loss=None, stream=None):
+    def param_grad(self, ev: nv.Eval, tape: torch.Tensor, grad_loss=None, stream=None,
+                   with_omega: bool = False):
         """(dloss/dR, dloss/dL) per configuration and port, [n_cfg, n_ports] each, after a
-        forward with the objective (loss cotangent grad_loss [n_cfg, n_struct], default 1)."""
+        forward with the objective (loss cotangent grad_loss [n_cfg, n_struct], default 1);
+        with_omega adds dloss/domega [n_cfg, n_freq] (drive fixed) and the drive cotangent
+        [n_cfg, sum F N] (complex128)."""
         gR = torch.empty((ev.n_cfg, self.n_ports), dtype=torch.float64, device=self.device)
         gL = torch.empty_like(gR)
+        gw = gV = None
+        if with_omega:
+            gw = torch.empty((ev.n_cfg, int(self.omega.numel())), dtype=torch.float64, device=self.device)
+            gV = torch.empty((ev.n_cfg, self.sumFN), dtype=torch.complex128, device=self.device)
         gl = None if grad_loss is None else grad_loss.to(torch.float64).contiguous()
-        nv.mts_param_grad(self.pb, self.prec, self.basis, ev, tape, gl, gR, gL, stream)
-        return gR, gL
+        nv.mts_param_grad(self.pb, self.prec, self.basis, ev, tape, gl, gR, gL, gw, gV, stream)
+        return (gR, gL, gw, gV) if with_omega else (gR, gL)
 
     def status(self, tape: torch.Tensor, n_cfg: int):
         return nv.mts_tape_status(self.pb, n_cfg, self.prec, tape)

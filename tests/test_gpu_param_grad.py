@@ -76,3 +76,33 @@ def test_param_grad_matches_oracle(name, prec):
             else:
                 assert err <= max(TOL[prec] * np.linalg.norm(want), TOL_ALL[prec] * nrm), \
                     (s, rel(got, want))
+
+
+@pytest.mark.parametrize("name", ["8x8", "ragged128"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_omega_and_drive_gradients_match_oracle(name, prec):
+    """dloss/domega (drive fixed) and the drive cotangent conj(mu) per structure against the
+    oracle's adjoint forms (pinned by central differences)."""
+    from paper_2503_18479_gb300.simulator import Simulator
+    wl, _ = _case(name)
+    sim = Simulator(wl, prec)
+    out = sim.forward(torch.from_numpy(wl.C).cuda(), want_B=False)
+    gR, gL, gw, gV = sim.param_grad(out["ev"], out["tape"], with_omega=True)
+    gw, gV = gw.cpu().numpy(), gV.cpu().numpy()
+    fo = np.concatenate([[0], np.cumsum([st.n_freq for st in wl.structures])])
+    vo = np.concatenate([[0], np.cumsum([st.n_freq * st.n_ports for st in wl.structures])])
+    want_w, want_V = [], []
+    for s, st in enumerate(wl.structures):
+        H, M = structure_basis(wl, s)
+        w_s, V_s = oracle.gradient_omega_v(H, M, st.R, wl.structure_C(s), st.omega, st.V,
+                                           st.loss_idx, wl.structure_target(s))
+        want_w.append(w_s)
+        want_V.append(V_s.reshape(wl.n_cfg, -1))
+        got_w, got_V = gw[:, fo[s]:fo[s + 1]], gV[:, vo[s]:vo[s + 1]]
+        if prec == "fp64":
+            assert rel(got_w, w_s) < 1e-10, (s, rel(got_w, w_s))
+            assert rel(got_V, V_s.reshape(wl.n_cfg, -1)) < 1e-10
+    if prec == "mixed":  # whole-tensor bounds (per-structure sums can cancel, as for dR/dL)
+        assert rel(gw, np.concatenate(want_w, axis=1)) < 1e-6
+        assert rel(gV, np.concatenate(want_V, axis=1)) < 1e-6
+        assert cosine(gw, np.concatenate(want_w, axis=1)) >= 0.9999
