@@ -70,7 +70,7 @@ def parse():
     ap.add_argument("--no-fp64-path", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--n-cfg", type=int, default=N_CFG, help="configurations per GPU (profiling runs)")
-    ap.add_argument("--other-workloads", default="loop,line,fit",
+    ap.add_argument("--other-workloads", default="loop,line,fit,fit8x8",
                     help="comma list of extra workloads timed after the headline (loop, line, "
                          "ragged, 32x32; empty for none); reported under other_workloads")
     return ap.parse_args()
@@ -389,6 +389,9 @@ def other_workloads(args, dev, prec):
         "32x32": ("array_32x32: 1024 ports, 256 configs, 4x512x512 grid", lambda: W.array_32x32(seed=0)),
         "fit": ("loop_sweep: Adam fits (lr 1e-13) of 100 initial C x 100 target fields on the "
                 "single loop at 63.6 MHz, 200 epochs replayed from one CUDA graph", None),
+        "fit8x8": ("array_8x8: 4096 independent Adam fits (lr 1e-13) of the 64 capacitances to "
+                   "the 64-point target, 200 epochs (solve + objective + adjoint + Adam, no field) "
+                   "replayed from one CUDA graph", None),
     }
     res = {}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -397,6 +400,9 @@ def other_workloads(args, dev, prec):
         desc, make = makers[name]
         if name == "fit":
             res[name] = fit_sweep(desc, dev, prec)
+            continue
+        if name == "fit8x8":
+            res[name] = fit_array(desc, dev, prec)
             continue
         wl = make()
         if wl.target is None:  # timing only: a zero target costs the same work
@@ -473,6 +479,32 @@ def fit_sweep(desc, dev, prec, epochs=200):
     return {"workload": desc, "precision": prec, "fits": wl.n_cfg, "epochs": epochs,
             "ms": ms, "fit_epochs_per_s": wl.n_cfg * epochs / (ms / 1e3),
             "share_of_fits_loss_down_100x": improved}
+
+
+def fit_array(desc, dev, prec, epochs=200):
+    """The optimisation loop on the 8x8 array: 4096 fits, fit-epochs per second."""
+    import torch
+
+    from paper_2503_18479_gb300 import workloads as W
+    from paper_2503_18479_gb300.optimize import AdamFit
+    from paper_2503_18479_gb300.simulator import Simulator
+    wl = W.array_8x8(seed=0, n_cfg=N_CFG, grid=8, planes=(0.02,))  # the field grid is unused
+    sim = Simulator(wl, prec, device=dev)
+    fit = AdamFit(sim, torch.from_numpy(wl.C), lr=1e-13, max_epochs=epochs + 2)
+    fit.run(2)
+    torch.cuda.synchronize()
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record()
+    fit.run(epochs)
+    a1.record()
+    a1.synchronize()
+    ms = a0.elapsed_time(a1)
+    h = fit.history[: epochs + 2].cpu().numpy()[:, :, 0]
+    return {"workload": desc, "precision": prec, "fits": wl.n_cfg, "epochs": epochs, "ms": ms,
+            "fit_epochs_per_s": wl.n_cfg * epochs / (ms / 1e3),
+            "ms_per_epoch_all_fits": ms / epochs,
+            "median_loss_ratio_last_over_first": float(np.median(h[-1] / h[0]))}
 
 
 def cpu_baseline_and_accuracy(wl, sim, C, B, loss, grad_C, gl, tape, ev):

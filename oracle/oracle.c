@@ -311,12 +311,14 @@ int oracle_segment_pair_inductance(const double r1s[3], const double r1e[3],
 
 /* Inductance matrix M[k][l] = sum over segment pairs of loops k and l (Eq. 12: L on the
  * diagonal, mutual M off it). If L_self is not NULL, its entries replace the diagonal
- * (the closed-form loop inductance of a circular loop, for instance). Returns the first
- * nonzero pair status, else 0. */
+ * (the closed-form loop inductance of a circular loop, for instance). Rows are independent
+ * (threads over k; every entry is summed in the same order whatever the thread count).
+ * Returns the largest pair status met (0 when every pair was handled). */
 int oracle_inductance(int32_t n_loops, const int32_t* loop_vtx_off, const double* vx,
                       const double* vy, const double* vz, double rw, const double* L_self,
                       double* M) {
   int status = 0;
+#pragma omp parallel for schedule(dynamic) reduction(max : status)
   for (int32_t k = 0; k < n_loops; ++k) {
     for (int32_t l = 0; l < n_loops; ++l) {
       if (k == l && L_self != NULL) {
@@ -332,7 +334,7 @@ int oracle_inductance(int32_t n_loops, const int32_t* loop_vtx_off, const double
           double b0[3] = {vx[j], vy[j], vz[j]}, b1[3] = {vx[je], vy[je], vz[je]};
           double m;
           int st = oracle_segment_pair_inductance(a0, a1, b0, b1, rw, (k == l && i == j), &m);
-          if (st != 0 && status == 0) status = st;
+          if (st > status) status = st;
           s += m;
         }
       }
