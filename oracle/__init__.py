@@ -49,6 +49,8 @@ def _load():
             lib.oracle_segment_bz.argtypes = [d] * 10
             lib.oracle_basis.restype = None
             lib.oracle_basis.argtypes = [i32, p, p, p, p, i64, p, p, p, d, p]
+            lib.oracle_basis_comp.restype = None
+            lib.oracle_basis_comp.argtypes = [i32, p, p, p, p, i64, p, p, p, p, d, p]
             lib.oracle_segment_pair_inductance.restype = ct.c_int
             lib.oracle_segment_pair_inductance.argtypes = [p, p, p, p, d, ct.c_int, p]
             lib.oracle_inductance.restype = ct.c_int
@@ -119,14 +121,16 @@ def segment_bz(r1, r2, p, wire_radius: float) -> float:
                                            float(wire_radius)))
 
 
-def basis(loop_vtx_off, vx, vy, vz, px, py, pz, wire_radius: float) -> np.ndarray:
-    """H[p, k] = Bz at point p per ampere in loop k."""
+def basis(loop_vtx_off, vx, vy, vz, px, py, pz, wire_radius: float, comp=None) -> np.ndarray:
+    """H[p, k] = B component comp[p] (0: z, 1: x, 2: y; None: z) at point p per ampere in
+    loop k."""
     off = _i32(loop_vtx_off)
     vx, vy, vz, px, py, pz = map(_f64, (vx, vy, vz, px, py, pz))
     n, P = len(off) - 1, len(px)
     H = np.zeros((P, n), dtype=np.float64)
-    _load().oracle_basis(n, _ptr(off), _ptr(vx), _ptr(vy), _ptr(vz), P, _ptr(px), _ptr(py),
-                         _ptr(pz), float(wire_radius), _ptr(H))
+    c = None if comp is None else np.ascontiguousarray(comp, dtype=np.int8)
+    _load().oracle_basis_comp(n, _ptr(off), _ptr(vx), _ptr(vy), _ptr(vz), P, _ptr(px), _ptr(py),
+                              _ptr(pz), _ptr(c), float(wire_radius), _ptr(H))
     return H
 
 

@@ -63,10 +63,11 @@ int oracle_num_threads(void) {
  * on the span) the field of a uniform current density grows linearly with rho, so the
  * term is scaled by rho^2 / rw^2 relative to the thin-wire expression (which is
  * proportional to 1/rho there). The paper does not treat this case; it is our reading.
- * Returns the z component.
+ * Returns component `comp` (0: z, 1: x, 2: y) of the field; the direction of every
+ * component is that of R1 x R2.
  * ------------------------------------------------------------------------------------ */
-double oracle_segment_bz(double x1, double y1, double z1, double x2, double y2, double z2,
-                         double px, double py, double pz, double rw) {
+double oracle_segment_b(double x1, double y1, double z1, double x2, double y2, double z2,
+                        double px, double py, double pz, double rw, int comp) {
   double R1[3] = {x1 - px, y1 - py, z1 - pz};
   double R2[3] = {x2 - px, y2 - py, z2 - pz};
   double d[3] = {x2 - x1, y2 - y1, z2 - z1};
@@ -96,15 +97,24 @@ double oracle_segment_bz(double x1, double y1, double z1, double x2, double y2, 
     if (c2 == 0.0) return 0.0;
     f = (n1 + n2) * (n1 * n2 - dot) / (n1 * n2 * c2);
   }
-  return ORACLE_MU0 / (4.0 * ORACLE_PI) * c[2] * f * scale;
+  const double cc = comp == 1 ? c[0] : (comp == 2 ? c[1] : c[2]);
+  return ORACLE_MU0 / (4.0 * ORACLE_PI) * cc * f * scale;
+}
+
+/* The z component (the normal field Bz the configurations optimise). */
+double oracle_segment_bz(double x1, double y1, double z1, double x2, double y2, double z2,
+                         double px, double py, double pz, double rw) {
+  return oracle_segment_b(x1, y1, z1, x2, y2, z2, px, py, pz, rw, 0);
 }
 
 /* Field basis H[p][k] (Sec. I-A; the per-port field of Eq. 7 at unit current): the sum
  * over the closed polyline of loop k (vertices loop_vtx_off[k] .. loop_vtx_off[k+1]-1,
- * last vertex joined back to the first) of oracle_segment_bz. */
-void oracle_basis(int32_t n_loops, const int32_t* loop_vtx_off, const double* vx,
-                  const double* vy, const double* vz, int64_t n_points, const double* px,
-                  const double* py, const double* pz, double rw, double* H) {
+ * last vertex joined back to the first) of oracle_segment_b, for the component comp[p]
+ * of point p (0: z, 1: x, 2: y; comp NULL: z everywhere; Eq. 7 superposes all three). */
+void oracle_basis_comp(int32_t n_loops, const int32_t* loop_vtx_off, const double* vx,
+                       const double* vy, const double* vz, int64_t n_points, const double* px,
+                       const double* py, const double* pz, const int8_t* comp, double rw,
+                       double* H) {
 #pragma omp parallel for schedule(static)
   for (int64_t p = 0; p < n_points; ++p) {
     for (int32_t k = 0; k < n_loops; ++k) {
@@ -112,12 +122,18 @@ void oracle_basis(int32_t n_loops, const int32_t* loop_vtx_off, const double* vx
       double s = 0.0;
       for (int32_t v = a; v < b; ++v) {
         int32_t w = (v + 1 < b) ? v + 1 : a;
-        s += oracle_segment_bz(vx[v], vy[v], vz[v], vx[w], vy[w], vz[w], px[p], py[p], pz[p],
-                               rw);
+        s += oracle_segment_b(vx[v], vy[v], vz[v], vx[w], vy[w], vz[w], px[p], py[p], pz[p],
+                              rw, comp ? comp[p] : 0);
       }
       H[p * n_loops + k] = s;
     }
   }
+}
+
+void oracle_basis(int32_t n_loops, const int32_t* loop_vtx_off, const double* vx,
+                  const double* vy, const double* vz, int64_t n_points, const double* px,
+                  const double* py, const double* pz, double rw, double* H) {
+  oracle_basis_comp(n_loops, loop_vtx_off, vx, vy, vz, n_points, px, py, pz, NULL, rw, H);
 }
 
 /* ------------------------------------------------------------------------------------

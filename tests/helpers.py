@@ -15,6 +15,21 @@ def rel(a, b) -> float:
     return float(np.linalg.norm((a - b).ravel()) / (den if den > 0 else 1.0))
 
 
+def loss_err(loss, ref, loss_idx) -> float:
+    """Error of the objective mean_{f,l} (|B| - t)^2 per configuration, scaled by its
+    sensitivity to the field. A field error dB moves the objective by at most
+    2 sqrt(loss) rms|dB| + rms|dB|^2, so near a good fit (loss -> 0) the plain relative error
+    of the objective is the field's relative error times rms|B| / sqrt(loss); dividing by
+    loss + 2 sqrt(loss) rms|B| gives the quantity a relative field tolerance bounds.
+    `ref` is the oracle's forward dict (B [n_cfg, F, P], loss [n_cfg])."""
+    loss = np.asarray(loss, float).ravel()
+    lr = np.asarray(ref["loss"], float).ravel()
+    bl = np.abs(ref["B"][:, :, np.asarray(loss_idx)])
+    rms = np.sqrt(np.mean(bl.reshape(len(lr), -1) ** 2, axis=1))
+    den = lr + 2.0 * np.sqrt(lr) * rms
+    return float(np.max(np.abs(loss - lr) / np.where(den > 0, den, 1.0)))
+
+
 def cosine(a, b) -> float:
     a = np.asarray(a, float).ravel()
     b = np.asarray(b, float).ravel()

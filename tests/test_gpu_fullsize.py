@@ -2,13 +2,16 @@
 batch, the library's default schedule): the CUDA path runs every configuration; the FP64
 oracle recomputes a sample of configurations (all their points, or a sample of points for
 the largest array) and their objective and dloss/dC. Tolerances as in test_gpu_parity
-(MTS_MIXED: 1e-6 on B, the loss and the gradient; 5e-6 on B of the K = 1024 tensor path)."""
+(MTS_MIXED: 1e-6 on B, the loss and the gradient; 5e-6 on B of the K = 1024 tensor path). A
+sampled configuration can sit close to its target, where the objective is a small difference
+of nearly equal fields: its error is then measured against the objective's sensitivity to the
+field (helpers.loss_err), not against the objective alone."""
 import numpy as np
 import pytest
 import torch
 
 import oracle
-from helpers import apply_target_rule, rel, structure_basis
+from helpers import apply_target_rule, loss_err, rel, structure_basis
 from paper_2503_18479_gb300 import build_lib
 from paper_2503_18479_gb300 import workloads as W
 
@@ -54,7 +57,8 @@ def _check_single(wl, n_sample, seed, tol_b=1e-6):
     idx = torch.from_numpy(cfg).cuda()
     Bg = B[idx].cpu().numpy().reshape(ref["B"].shape)
     assert rel(Bg, ref["B"]) < tol_b, rel(Bg, ref["B"])
-    assert rel(loss[idx, 0].cpu().numpy(), ref["loss"]) < 1e-6
+    err = loss_err(loss[idx, 0].cpu().numpy(), ref, st.loss_idx)
+    assert err < 1e-6, err
     assert rel(g[idx].cpu().numpy(), gref) < 1e-6
 
 

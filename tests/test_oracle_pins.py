@@ -691,3 +691,53 @@ def test_gradient_omega_and_drive_central_differences(mode):
             fd = (loss(omega, Vp) - loss(omega, Vm)) / (2 * h)
             want = gV[:, f, k].real if part == 1.0 else gV[:, f, k].imag
             assert _rel(want, fd) < 1e-6
+
+
+# ---------------------------------------------------------------- in-plane field components
+@pytest.mark.parametrize("rho,zp", [(0.02, 0.01), (0.049, 0.003), (0.08, -0.02)])
+def test_circle_radial_field_elliptic(rho, zp):
+    """Radial field of a circular loop (complete elliptic integrals, scipy's K, E):
+    B_rho = mu0 z / (2 pi rho sqrt((a+rho)^2+z^2)) [-K + (a^2+rho^2+z^2)/((a-rho)^2+z^2) E];
+    at azimuth phi, Bx = B_rho cos(phi), By = B_rho sin(phi)."""
+    from scipy.special import ellipe, ellipk
+    a = 0.05
+    m = 4 * a * rho / ((a + rho) ** 2 + zp ** 2)
+    brho = MU0 * zp / (2 * np.pi * rho * np.sqrt((a + rho) ** 2 + zp ** 2)) * (
+        -ellipk(m) + (a * a + rho * rho + zp * zp) / ((a - rho) ** 2 + zp ** 2) * ellipe(m))
+    off, vx, vy, vz = _loop_arrays([W.circular_loop(a, 8192)])
+    for phi in (0.0, 0.7):
+        px, py = [rho * np.cos(phi)] * 2, [rho * np.sin(phi)] * 2
+        H = oracle.basis(off, vx, vy, vz, px, py, [zp] * 2, 1e-4, comp=[1, 2])
+        assert abs(H[0, 0] - brho * np.cos(phi)) < 2e-5 * abs(brho) + 1e-15
+        assert abs(H[1, 0] - brho * np.sin(phi)) < 2e-5 * abs(brho) + 1e-15
+
+
+def test_components_of_a_wire_and_on_axis():
+    """A long straight side (current along +x) of a huge rectangle: at (0, 0, d) the field
+    is -mu0 I/(2 pi d) along y (right-hand rule), with no x or z component; on the axis of
+    a square loop the in-plane components vanish."""
+    L, D, d = 1e3, 1e3, 0.01
+    vx = np.array([-L, L, L, -L])
+    vy = np.array([0.0, 0.0, D, D])
+    vz = np.zeros(4)
+    H = oracle.basis(np.array([0, 4], np.int32), vx, vy, vz, [0.0] * 3, [0.0] * 3, [d] * 3, 1e-3,
+                     comp=[1, 2, 0])[:, 0]
+    want = -MU0 / (2 * np.pi * d)
+    assert abs(H[1] / want - 1) < 1e-4          # far sides contribute ~d/L
+    assert abs(H[0]) < 1e-12 * abs(want) and abs(H[2]) < 1e-4 * abs(want)
+    off, vx, vy, vz = _loop_arrays([W.square_loop(0.05, 16)])
+    H = oracle.basis(off, vx, vy, vz, [0.0] * 2, [0.0] * 2, [0.02] * 2, 1e-3, comp=[1, 2])
+    assert np.all(np.abs(H) < 1e-20)
+
+
+def test_square_loop_quarter_turn_maps_components():
+    """A square loop centred at the origin is invariant under a quarter turn about z, so
+    B(R p) = R B(p): Bx(Rp) = -By(p), By(Rp) = Bx(p), Bz(Rp) = Bz(p)."""
+    off, vx, vy, vz = _loop_arrays([W.square_loop(0.05, 16)])
+    p = np.array([0.013, -0.021, 0.017])
+    q = np.array([-p[1], p[0], p[2]])  # R p
+    Hp = oracle.basis(off, vx, vy, vz, [p[0]] * 3, [p[1]] * 3, [p[2]] * 3, 1e-3, comp=[1, 2, 0])[:, 0]
+    Hq = oracle.basis(off, vx, vy, vz, [q[0]] * 3, [q[1]] * 3, [q[2]] * 3, 1e-3, comp=[1, 2, 0])[:, 0]
+    assert abs(Hq[0] + Hp[1]) < 1e-12 * np.abs(Hp).max()
+    assert abs(Hq[1] - Hp[0]) < 1e-12 * np.abs(Hp).max()
+    assert abs(Hq[2] - Hp[2]) < 1e-12 * np.abs(Hp).max()
