@@ -5,8 +5,8 @@
  *
  * Method (paper: "Differentiable Cosimulator for Electrically Reconfigurable Structures",
  * Mueller, Philipp, Guenther):
- *   (a) field basis  H[p][k] = Bz at point p per ampere in loop k, from the Biot-Savart
- *       law over straight wire segments (Sec. I-A: circuit model plus Biot-Savart for
+ *   (a) field basis  H[p][k] = Bz (or Bx, By: pcomp) at point p per ampere in loop k,
+ *       from the Biot-Savart law over straight wire segments (Sec. I-A: circuit model plus Biot-Savart for
  *       structures small against the wavelength); coupling M[k][l] = self and mutual
  *       inductances (Eq. 12-13, here from Neumann partial inductances).
  *   (b) port solve   (diag(R) + j w M + diag(1/(j w C))) I = V per configuration and
@@ -119,6 +119,10 @@ typedef struct mts_problem {
   const int64_t* loss_idx;     /* device [n_loss] */
   const double* R;             /* device [n_ports], ohm, > 0 */
   const double* L_self;        /* device [n_ports] henry, or NULL (partial inductances) */
+  const int8_t* pcomp;         /* device [n_points] field component per point: 0 = Bz (the
+                                  paper's normal field), 1 = Bx, 2 = By; NULL = Bz everywhere.
+                                  Another code makes that point's basis rows NaN and
+                                  mts_basis_status report MTS_EINVAL. */
 } mts_problem;
 
 /*
@@ -183,8 +187,9 @@ mts_status mts_build_basis(const mts_problem* pb, mts_precision prec, void* basi
 mts_status mts_basis_export(const mts_problem* pb, mts_precision prec, const void* basis,
                             double* H_out, double* M_out, mts_stream stream);
 
-/* Synchronises `stream`, then reports MTS_EUNSUPPORTED if a segment pair needed for M
- * was neither parallel nor perpendicular (or two collinear segments overlapped). */
+/* Synchronises `stream`, then reports MTS_EINVAL if a component code in pcomp was not 0, 1
+ * or 2, else MTS_EUNSUPPORTED if a segment pair needed for M could not be integrated (two
+ * collinear segments overlapped, or oblique segments touched without L_self). */
 mts_status mts_basis_status(const mts_problem* pb, mts_precision prec, const void* basis,
                             mts_stream stream);
 

@@ -337,6 +337,7 @@ mts_status mts_basis_status(const mts_problem* pb, mts_precision prec, const voi
   if (cudaMemcpy(&w, static_cast<const char*>(basis) + bl.status, sizeof(w),
                  cudaMemcpyDeviceToHost) != cudaSuccess)
     return MTS_ECUDA;
+  if (w & (1 << 30)) return MTS_EINVAL;  // a component code outside {0, 1, 2}
   return w ? MTS_EUNSUPPORTED : MTS_OK;
 }
 

@@ -112,17 +112,20 @@ __global__ void tables_kernel(int n_struct, int n_freq, const int32_t* __restric
 }
 
 // ---------------------------------------------------------------------------------------
-// Biot-Savart: z field of a straight segment r1 -> r2 carrying 1 A at the origin-shifted
+// Biot-Savart: field of a straight segment r1 -> r2 carrying 1 A at the origin-shifted
 // point (R1 = r1 - p, R2 = r2 - p):
-//   Bz = mu0/(4 pi) (R1 x R2)_z (|R1| + |R2|) / (|R1||R2| (|R1||R2| + R1.R2)),
+//   B = mu0/(4 pi) (R1 x R2) (|R1| + |R2|) / (|R1||R2| (|R1||R2| + R1.R2)),
+// of which one component is taken per field point (comp 0 = z, the paper's Bz; 1 = x; 2 = y),
 // with |R1||R2| + R1.R2 = |R1 x R2|^2 / (|R1||R2| - R1.R2) when R1.R2 < 0 (no cancellation
 // beside the span). Inside the wire (rho < rw, foot on the span) a uniform current gives a
 // field linear in rho: the thin-wire value is scaled by rho^2/rw^2.
 // ---------------------------------------------------------------------------------------
 constexpr double kMu0Over4Pi = 1e-7;  // mu0/(4 pi) with mu0 = 4 pi 1e-7 H/m
+// status bit of a component code outside {0, 1, 2} (its basis rows are NaN)
+constexpr int32_t kBadComponent = 1 << 30;
 
-__device__ inline double seg_bz_f64(double ax, double ay, double az, double bx, double by,
-                                    double bz, double rw) {
+__device__ inline double seg_b_f64(double ax, double ay, double az, double bx, double by,
+                                   double bz, double rw, int comp) {
   // (ax,ay,az) = R1, (bx,by,bz) = R2
   double cx = ay * bz - az * by, cy = az * bx - ax * bz, cz = ax * by - ay * bx;
   double n1 = sqrt(ax * ax + ay * ay + az * az);
@@ -148,11 +151,12 @@ __device__ inline double seg_bz_f64(double ax, double ay, double az, double bx, 
     if (c2 == 0.0) return 0.0;
     f = (n1 + n2) * (n1 * n2 - dot) / (n1 * n2 * c2);
   }
-  return kMu0Over4Pi * cz * f * scale;
+  const double cc = comp == 1 ? cx : (comp == 2 ? cy : cz);
+  return kMu0Over4Pi * cc * f * scale;
 }
 
-__device__ inline float seg_bz_f32(float ax, float ay, float az, float dx, float dy, float dz,
-                                   float rw2) {
+__device__ inline float seg_b_f32(float ax, float ay, float az, float dx, float dy, float dz,
+                                  float rw2, int comp) {
   float bx = ax + dx, by = ay + dy, bz = az + dz;
   float cx = ay * bz - az * by, cy = az * bx - ax * bz, cz = ax * by - ay * bx;
   float q1 = ax * ax + ay * ay + az * az;
@@ -178,7 +182,8 @@ __device__ inline float seg_bz_f32(float ax, float ay, float az, float dx, float
     if (c2 == 0.0f) return 0.0f;
     f = (n1 + n2) * (n12 - dot) / (n12 * c2);
   }
-  return cz * f * scale;  // times mu0/(4 pi) by the caller
+  const float cc = comp == 1 ? cx : (comp == 2 ? cy : cz);
+  return cc * f * scale;  // times mu0/(4 pi) by the caller
 }
 
 __global__ void basis_fp64_kernel(int n_struct, const int64_t* __restrict__ point_off,
@@ -187,8 +192,9 @@ __global__ void basis_fp64_kernel(int n_struct, const int64_t* __restrict__ poin
                                   const double* __restrict__ vx, const double* __restrict__ vy,
                                   const double* __restrict__ vz, const double* __restrict__ px,
                                   const double* __restrict__ py, const double* __restrict__ pz,
-                                  double rw, int64_t n_points, const int64_t* __restrict__ pn_off,
-                                  double* __restrict__ H) {
+                                  const int8_t* __restrict__ pcomp, double rw, int64_t n_points,
+                                  const int64_t* __restrict__ pn_off, double* __restrict__ H,
+                                  int32_t* __restrict__ status) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int k = blockIdx.y;
   if (p >= n_points) return;
@@ -198,10 +204,15 @@ __global__ void basis_fp64_kernel(int n_struct, const int64_t* __restrict__ poin
   int loop = port_off[s] + k;
   int a = loop_vtx_off[loop], b = loop_vtx_off[loop + 1];
   double x = px[p], y = py[p], z = pz[p];
+  const int comp = pcomp != nullptr ? pcomp[p] : 0;
   double acc = 0.0;
   for (int v = a; v < b; ++v) {
     int w = (v + 1 < b) ? v + 1 : a;
-    acc += seg_bz_f64(vx[v] - x, vy[v] - y, vz[v] - z, vx[w] - x, vy[w] - y, vz[w] - z, rw);
+    acc += seg_b_f64(vx[v] - x, vy[v] - y, vz[v] - z, vx[w] - x, vy[w] - y, vz[w] - z, rw, comp);
+  }
+  if (comp < 0 || comp > 2) {
+    atomicOr(status, kBadComponent);
+    acc = __longlong_as_double(0x7ff8000000000000LL);
   }
   H[pn_off[s] + (p - point_off[s]) * N + k] = acc;
 }
@@ -215,9 +226,9 @@ __global__ void __launch_bounds__(128) basis_fp32_kernel(
     int n_struct, const int64_t* __restrict__ point_off, const int32_t* __restrict__ port_off,
     const int32_t* __restrict__ loop_vtx_off, const double* __restrict__ vx,
     const double* __restrict__ vy, const double* __restrict__ vz, const double* __restrict__ px,
-    const double* __restrict__ py, const double* __restrict__ pz, double rw,
-    const int64_t* __restrict__ ptile_off, const int64_t* __restrict__ pn_off,
-    float* __restrict__ H) {
+    const double* __restrict__ py, const double* __restrict__ pz,
+    const int8_t* __restrict__ pcomp, double rw, const int64_t* __restrict__ ptile_off,
+    const int64_t* __restrict__ pn_off, float* __restrict__ H, int32_t* __restrict__ status) {
   __shared__ float s_seg[6][kSegChunk];  // ax, ay, az (start), dx, dy, dz
   __shared__ float s_len2[kSegChunk];
   int64_t tile = blockIdx.x;
@@ -233,6 +244,7 @@ __global__ void __launch_bounds__(128) basis_fp32_kernel(
   int a = loop_vtx_off[loop], b = loop_vtx_off[loop + 1];
   double ox = vx[a], oy = vy[a], oz = vz[a];
   double xd = px[p], yd = py[p], zd = pz[p];
+  const int fc = pcomp != nullptr ? pcomp[p] : 0;  // field component
   float x = (float)(xd - ox), y = (float)(yd - oy), z = (float)(zd - oz);
   float rw2 = (float)(rw * rw);
   float acc = 0.0f, comp = 0.0f;
@@ -269,10 +281,10 @@ __global__ void __launch_bounds__(128) basis_fp32_kernel(
       if (dist2 < len2) {
         int v = a + c0 + i;
         int w = (v + 1 < b) ? v + 1 : a;
-        acc64 += seg_bz_f64(vx[v] - xd, vy[v] - yd, vz[v] - zd, vx[w] - xd, vy[w] - yd,
-                            vz[w] - zd, rw);
+        acc64 += seg_b_f64(vx[v] - xd, vy[v] - yd, vz[v] - zd, vx[w] - xd, vy[w] - yd,
+                           vz[w] - zd, rw, fc);
       } else {
-        float term = seg_bz_f32(ax, ay, az, dx, dy, dz, rw2);
+        float term = seg_b_f32(ax, ay, az, dx, dy, dz, rw2, fc);
         float yk = term - comp;
         float tk = acc + yk;
         comp = (tk - acc) - yk;
@@ -282,6 +294,10 @@ __global__ void __launch_bounds__(128) basis_fp32_kernel(
   }
   if (valid) {
     double v = (double)acc * kMu0Over4Pi + acc64;
+    if (fc < 0 || fc > 2) {
+      atomicOr(status, kBadComponent);
+      v = __longlong_as_double(0x7ff8000000000000LL);
+    }
     H[pn_off[s] + lp * N + k] = (float)v;
   }
 }
@@ -611,14 +627,16 @@ cudaError_t launch_build_basis(const mts_problem* pb, mts_precision prec, void* 
     dim3 grid(nblk(pb->n_points, 128), ps.max_ports);
     basis_fp64_kernel<<<grid, 128, 0, st>>>(pb->n_struct, pb->point_off, pb->port_off,
                                             pb->loop_vtx_off, pb->vx, pb->vy, pb->vz, pb->px,
-                                            pb->py, pb->pz, pb->wire_radius, pb->n_points,
-                                            t.pn_off, (double*)(B + bl.H));
+                                            pb->py, pb->pz, pb->pcomp, pb->wire_radius,
+                                            pb->n_points, t.pn_off, (double*)(B + bl.H),
+                                            (int32_t*)(B + bl.status));
   } else {
     dim3 grid((unsigned)ntiles, ps.max_ports);
     basis_fp32_kernel<<<grid, 128, 0, st>>>(pb->n_struct, pb->point_off, pb->port_off,
                                             pb->loop_vtx_off, pb->vx, pb->vy, pb->vz, pb->px,
-                                            pb->py, pb->pz, pb->wire_radius, t.ptile_off,
-                                            t.pn_off, (float*)(B + bl.H));
+                                            pb->py, pb->pz, pb->pcomp, pb->wire_radius,
+                                            t.ptile_off, t.pn_off, (float*)(B + bl.H),
+                                            (int32_t*)(B + bl.status));
   }
   note_launch();
   inductance_kernel<<<(unsigned)npairs, kIndThreads, 0, st>>>(

@@ -43,6 +43,7 @@ class MtsProblem(ct.Structure):
         ("loop_vtx_off", ct.c_void_p), ("vx", ct.c_void_p), ("vy", ct.c_void_p),
         ("vz", ct.c_void_p), ("px", ct.c_void_p), ("py", ct.c_void_p), ("pz", ct.c_void_p),
         ("loss_idx", ct.c_void_p), ("R", ct.c_void_p), ("L_self", ct.c_void_p),
+        ("pcomp", ct.c_void_p),
     ]
 
 
@@ -161,6 +162,8 @@ class Problem:
         }
         if flat.get("L_self") is not None:
             self.d["L_self"] = dev(flat["L_self"], np.float64)
+        if flat.get("pcomp") is not None:
+            self.d["pcomp"] = dev(flat["pcomp"], np.int8)
         n_struct = len(self.h_port_off) - 1
         c = MtsProblem()
         c.n_struct = n_struct
@@ -178,6 +181,7 @@ class Problem:
                   "vz", "px", "py", "pz", "loss_idx", "R"):
             setattr(c, k, self.d[k].data_ptr() if self.d[k].numel() else None)
         c.L_self = self.d["L_self"].data_ptr() if "L_self" in self.d else None
+        c.pcomp = self.d["pcomp"].data_ptr() if "pcomp" in self.d else None
         self.c = c
         self.n_struct = n_struct
 

@@ -52,6 +52,7 @@ class Structure:
     V: np.ndarray  # complex [F, N] volt
     loss_idx: np.ndarray  # int64 [L], local point indices
     L_self: Optional[np.ndarray] = None  # [N] henry or None (partial-inductance sum)
+    pcomp: Optional[np.ndarray] = None  # int8 [P] field component per point (0 z, 1 x, 2 y)
     label: str = ""
 
     @property
@@ -146,6 +147,7 @@ class Workload:
         has_L = any(s.L_self is not None for s in ss)
         if has_L and not all(s.L_self is not None for s in ss):
             raise ValueError("L_self must be given for every structure or none")
+        has_comp = any(s.pcomp is not None for s in ss)
         return dict(
             port_off=self.port_off(), point_off=self.point_off(), freq_off=self.freq_off(),
             loss_off=self.loss_off(),
@@ -157,6 +159,8 @@ class Workload:
             loss_idx=np.concatenate([s.loss_idx + pt_base[i] for i, s in enumerate(ss)]).astype(np.int64),
             R=np.concatenate([s.R for s in ss]),
             L_self=np.concatenate([s.L_self for s in ss]) if has_L else None,
+            pcomp=np.concatenate([s.pcomp if s.pcomp is not None else np.zeros(s.n_points, np.int8)
+                                  for s in ss]).astype(np.int8) if has_comp else None,
             omega=np.concatenate([s.omega for s in ss]),
             V=np.concatenate([s.V.reshape(-1) for s in ss]).astype(np.complex128),
         )

@@ -38,7 +38,8 @@ def cosine(a, b) -> float:
 
 def structure_basis(wl: W.Workload, s: int):
     st = wl.structures[s]
-    H = oracle.basis(st.loop_vtx_off, st.vx, st.vy, st.vz, st.px, st.py, st.pz, wl.wire_radius)
+    H = oracle.basis(st.loop_vtx_off, st.vx, st.vy, st.vz, st.px, st.py, st.pz, wl.wire_radius,
+                     comp=st.pcomp)
     status, M = oracle.inductance(st.loop_vtx_off, st.vx, st.vy, st.vz, wl.wire_radius, st.L_self)
     assert status == 0
     return H, M
@@ -129,6 +130,15 @@ def small_loop(n_cfg=16, n_freq=11, grid=16, seed=0):
 
 def small_ragged(n_struct=12, seed=3, grid=12, max_freq=4, ports=(1, 8, 16, 32, 64)):
     return W.ragged(seed=seed, n_struct=n_struct, grid=grid, max_freq=max_freq, port_choices=ports)
+
+
+def with_components(wl: W.Workload, seed: int) -> W.Workload:
+    """The same structures with a seeded field component (0 z, 1 x, 2 y) at every point."""
+    import dataclasses
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ss = [dataclasses.replace(st, pcomp=rng.integers(0, 3, size=st.n_points).astype(np.int8))
+          for st in wl.structures]
+    return dataclasses.replace(wl, structures=ss)
 
 
 def small_rect(nx, ny, n_cfg=20, n_freq=2, grid=10, seed=0):

@@ -2,7 +2,7 @@
 and one without frequencies inside a batch, a one-port structure on the tensor-core path
 (K = 1 padded to 64), per-configuration complex targets on a 128-port structure (the
 large-system kernel in the complex-objective mode), and a problem whose only structure
-takes the SIMT superposition."""
+takes the SIMT superposition; an invalid field-component code."""
 import numpy as np
 import pytest
 import torch
@@ -93,3 +93,19 @@ def test_complex_targets_per_config_on_a_large_structure():
         loss.sum().backward()
         assert rel(loss.detach().cpu().numpy()[:, 0], ref[0]["loss"]) < tol
         assert rel(Cg.grad.cpu().numpy(), ref[0]["grad"]) < tol
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_invalid_component_code_is_reported(prec):
+    """A field-component code other than 0, 1, 2 makes the basis build report MTS_EINVAL."""
+    import dataclasses
+    from paper_2503_18479_gb300 import native as nv
+    from paper_2503_18479_gb300.simulator import Simulator
+    st = _struct(2, 2, 2, 6)
+    pc = np.zeros(st.n_points, np.int8)
+    pc[5] = 3
+    wl = W.Workload("bad_component", [dataclasses.replace(st, pcomp=pc)], np.full((2, 4), 50e-12),
+                    0.001, target=np.zeros(2 * st.n_loss))
+    with pytest.raises(nv.MtsError) as e:
+        Simulator(wl, prec)
+    assert e.value.code == nv.MTS_EINVAL

@@ -9,7 +9,7 @@ import torch
 
 from helpers import (apply_target_rule, cosine, oracle_reference, rel, small_8x8, small_line,
                      small_loop, small_ragged, small_rect, split_B, split_I, split_ports,
-                     structure_basis)
+                     structure_basis, with_components)
 from paper_2503_18479_gb300 import build_lib
 from paper_2503_18479_gb300 import workloads as W
 
@@ -49,6 +49,8 @@ _CASES = {
     "10x8": lambda: small_rect(10, 8, n_cfg=20, n_freq=2, grid=10, seed=4),
     # circular loops: mutual inductances from oblique segment pairs (quadrature)
     "circles": lambda: W.circle_array(3, 3, seed=6, n_cfg=40, n_freq=3, grid=12),
+    # Bx, By or Bz chosen per field point (objective points included), ragged structures
+    "components": lambda: apply_target_rule(with_components(small_ragged(n_struct=6, seed=9), 10)),
 }
 _cache = {}
 
