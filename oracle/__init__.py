@@ -85,6 +85,11 @@ def _load():
             lib.oracle_dcurrents_dC.argtypes = [i32, p, p, d, p, p, p]
             lib.oracle_sroute.restype = ct.c_int
             lib.oracle_sroute.argtypes = [i32, p, p, i32, d, d, d, p, p, p]
+            sr = [i32, i32, i32, i64, i32, p, p, p, p, p, i64, p, i32, p, p, i32]
+            lib.oracle_sroute_forward.restype = ct.c_int
+            lib.oracle_sroute_forward.argtypes = sr + [p, p, p]
+            lib.oracle_sroute_gradient.restype = ct.c_int
+            lib.oracle_sroute_gradient.argtypes = sr + [p]
             lib.oracle_num_threads.restype = ct.c_int
             lib.oracle_num_threads.argtypes = []
             _lib = lib
@@ -307,3 +312,46 @@ def sroute(Z, Zload, drive: int, Z0: float, P_in: float, omega: float, C=None, w
     st = _load().oracle_sroute(n, _ptr(Z), _ptr(Zload), int(drive), float(Z0), float(P_in),
                                float(omega), _ptr(Cv), _ptr(Iout), _ptr(dI))
     return int(st), Iout, dI
+
+
+def sroute_pipeline(S0, field, Sconst, rows, cols, svar, loss_idx=None, target=None,
+                    mode: int = 0, want_B: bool = True, want_loss: bool = True):
+    """The S-parameter pipeline (Sec. III-A, Eq. 3-7) for a batch of variable S-parameters.
+    S0 [F, n0, n0], field [F, P, n0], Sconst [F, n, n] (n = n0 + n1), svar [n_batch, F, nS],
+    rows/cols [nS], target [F, n1, L] (real, or complex for mode 1).
+    Returns dict W [n_batch, F, n0, n1], B [n_batch, n1, F, P], loss [n_batch], n_singular."""
+    S0, field, Sconst, svar = _c128(S0), _c128(field), _c128(Sconst), _c128(svar)
+    F, n0 = S0.shape[0], S0.shape[1]
+    n1 = Sconst.shape[1] - n0
+    P = field.shape[1]
+    n_batch, nS = svar.shape[0], svar.shape[2]
+    li = _i64(loss_idx if loss_idx is not None else np.zeros(0, np.int64))
+    L = len(li)
+    do_loss = want_loss and L > 0
+    t = _target_arr(np.asarray(target), mode) if do_loss else np.zeros(1)
+    W = np.zeros((n_batch, F, n0, n1), dtype=np.complex128)
+    B = np.zeros((n_batch, n1, F, P), dtype=np.complex128) if want_B else None
+    loss = np.zeros(n_batch) if do_loss else None
+    bad = _load().oracle_sroute_forward(n0, n1, F, P, nS, _ptr(_i32(rows)), _ptr(_i32(cols)),
+                                        _ptr(S0), _ptr(field), _ptr(Sconst), n_batch, _ptr(svar),
+                                        L, _ptr(li), _ptr(t), int(mode), _ptr(W), _ptr(B),
+                                        _ptr(loss))
+    return {"W": W, "B": B, "loss": loss, "n_singular": int(bad)}
+
+
+def sroute_gradient(S0, field, Sconst, rows, cols, svar, loss_idx, target, mode: int = 0):
+    """d objective / d svar (Eq. 10, forward mode), torch's convention, [n_batch, F, nS]."""
+    S0, field, Sconst, svar = _c128(S0), _c128(field), _c128(Sconst), _c128(svar)
+    F, n0 = S0.shape[0], S0.shape[1]
+    n1 = Sconst.shape[1] - n0
+    P = field.shape[1]
+    n_batch, nS = svar.shape[0], svar.shape[2]
+    li = _i64(loss_idx)
+    t = _target_arr(np.asarray(target), mode)
+    g = np.zeros((n_batch, F, nS), dtype=np.complex128)
+    bad = _load().oracle_sroute_gradient(n0, n1, F, P, nS, _ptr(_i32(rows)), _ptr(_i32(cols)),
+                                         _ptr(S0), _ptr(field), _ptr(Sconst), n_batch,
+                                         _ptr(svar), len(li), _ptr(li), _ptr(t), int(mode),
+                                         _ptr(g))
+    assert bad == 0, bad
+    return g

@@ -843,3 +843,184 @@ done:
   free(piv);
   return st;
 }
+
+/* ------------------------------------------------------------------------------------
+ * The scattering-parameter pipeline as a first-class path (Sec. III and III-A, Eq. 3-7,
+ * Eq. 10), on a structure described by its own S-matrix S0 and per-port fields, both from
+ * any solver.
+ *
+ *   n0 structure ports, n1 external ports, n = n0 + n1; F frequencies; P field points.
+ *   S0[f]      complex [n0][n0]   structure scattering matrix (Eq. 5: V-res = S0 V+res)
+ *   field[f]   complex [P][n0]    field at point p when port k receives a unit incident
+ *                                 wave (Eq. 7's B, one component per point)
+ *   Sconst[f]  complex [n][n]     constant part of the network tensor S_C (Sec. III-A 2)
+ *   svar[b][f] complex [nS]       user-preprocessed variable S-parameters; entry i goes to
+ *                                 row rows[i], column cols[i] of S_C,var (Sec. III-A 1)
+ * Per configuration b and frequency f (Sec. III-A 3, Eq. 6, Eq. 7):
+ *   S_C = S_C,var + S_C,const;  S11 = S_C[0:n0, 0:n0],  S12 = S_C[0:n0, n0:n]
+ *   A = 1 - S11 S0;  W = A^-1 S12  (the wave ratio V+res / V-exc, n0 x n1)
+ *   Bcomb[b][c][f][p] = sum_k field[f][p][k] W[k][c]
+ * Objective: the point loss of oracle_point_loss on Bcomb at the loss points, target
+ * [f][c][l] (mode 0 real, mode 1 complex), mean over (f, c, l).
+ * ------------------------------------------------------------------------------------ */
+static void oracle_sroute_assemble(int32_t n0, int32_t n1, int32_t nS, const int32_t* rows,
+                                   const int32_t* cols, const double complex* S0,
+                                   const double complex* Sconst, const double complex* svar,
+                                   double complex* SC, double complex* A) {
+  const int32_t n = n0 + n1;
+  memcpy(SC, Sconst, sizeof(double complex) * (size_t)n * n);
+  for (int32_t i = 0; i < nS; ++i) SC[rows[i] * n + cols[i]] += svar[i];
+  for (int32_t i = 0; i < n0; ++i)
+    for (int32_t j = 0; j < n0; ++j) {
+      double complex s = 0.0;
+      for (int32_t k = 0; k < n0; ++k) s += SC[i * n + k] * S0[k * n0 + j];
+      A[i * n0 + j] = (i == j ? 1.0 : 0.0) - s;
+    }
+}
+
+/* W = A^-1 S12 column by column with the factors of A; W is [n0][n1]. */
+static void oracle_sroute_wave_ratio(int32_t n0, int32_t n1, const double complex* LU,
+                                     const int32_t* piv, const double complex* SC,
+                                     double complex* col, double complex* W) {
+  const int32_t n = n0 + n1;
+  for (int32_t c = 0; c < n1; ++c) {
+    for (int32_t k = 0; k < n0; ++k) col[k] = SC[k * n + n0 + c];
+    oracle_lu_solve(n0, LU, piv, col);
+    for (int32_t k = 0; k < n0; ++k) W[k * n1 + c] = col[k];
+  }
+}
+
+int oracle_sroute_forward(int32_t n0, int32_t n1, int32_t F, int64_t P, int32_t nS,
+                          const int32_t* rows, const int32_t* cols, const double complex* S0,
+                          const double complex* field, const double complex* Sconst,
+                          int64_t n_batch, const double complex* svar, int32_t L,
+                          const int64_t* loss_idx, const double* target, int32_t mode,
+                          double complex* W_out, double complex* B_out, double* loss_out) {
+  const int32_t n = n0 + n1;
+  const int64_t tw = (mode == 0) ? 1 : 2;
+  int n_bad = 0;
+#pragma omp parallel for schedule(static) reduction(+ : n_bad)
+  for (int64_t b = 0; b < n_batch; ++b) {
+    double complex* SC = malloc(sizeof(double complex) * (size_t)n * n);
+    double complex* A = malloc(sizeof(double complex) * (size_t)n0 * n0);
+    double complex* W = malloc(sizeof(double complex) * (size_t)n0 * n1);
+    double complex* col = malloc(sizeof(double complex) * (size_t)n0);
+    int32_t* piv = malloc(sizeof(int32_t) * (size_t)n0);
+    double acc = 0.0;
+    for (int32_t f = 0; f < F; ++f) {
+      oracle_sroute_assemble(n0, n1, nS, rows, cols, S0 + (int64_t)f * n0 * n0,
+                             Sconst + (int64_t)f * n * n, svar + (b * F + f) * nS, SC, A);
+      if (oracle_lu(n0, A, piv) != 0) {
+        n_bad += 1;
+        continue;
+      }
+      oracle_sroute_wave_ratio(n0, n1, A, piv, SC, col, W);
+      if (W_out) memcpy(W_out + (b * F + f) * n0 * n1, W, sizeof(double complex) * (size_t)n0 * n1);
+      const double complex* fd = field + (int64_t)f * P * n0;
+      for (int32_t c = 0; c < n1; ++c) {
+        if (B_out)
+          for (int64_t p = 0; p < P; ++p) {
+            double complex s = 0.0;
+            for (int32_t k = 0; k < n0; ++k) s += fd[p * n0 + k] * W[k * n1 + c];
+            B_out[((b * n1 + c) * F + f) * P + p] = s;
+          }
+        if (loss_out)
+          for (int32_t l = 0; l < L; ++l) {
+            double complex s = 0.0, G;
+            for (int32_t k = 0; k < n0; ++k) s += fd[loss_idx[l] * n0 + k] * W[k * n1 + c];
+            acc += oracle_point_loss(mode, s, target + (((int64_t)f * n1 + c) * L + l) * tw, &G);
+          }
+      }
+    }
+    if (loss_out) loss_out[b] = (F * n1 * L > 0) ? acc / ((double)F * n1 * L) : 0.0;
+    free(SC);
+    free(A);
+    free(W);
+    free(col);
+    free(piv);
+  }
+  return n_bad;
+}
+
+/* Gradient of the objective with respect to the variable S-parameters, from Eq. 10 in
+ * forward mode: entry i enters S_C at (r, c) = (rows[i], cols[i]), so d S_C / d svar_i is
+ * the unit matrix E_rc (S_C is holomorphic in svar). Eq. 10 gives
+ *   dW = A^-1 (dS11 S0 W + dS12):   r < n0, c < n0:  row r of the bracket is row c of S0 W;
+ *                                    r < n0, c >= n0: the bracket is E_{r, c-n0};
+ *                                    r >= n0:         S21 and S22 do not reach the field.
+ * With dBcomb = field dW and G the objective's field derivative (oracle_point_loss), the
+ * gradient in torch's convention dL/dRe + j dL/dIm of a holomorphic dependence is
+ *   grad_i = sum over (f, c, l) of conj(dBcomb_l,c) G_l,c / (F n1 L).
+ * One extra solve per variable and frequency. Writes grad_out[b][f][nS]. */
+int oracle_sroute_gradient(int32_t n0, int32_t n1, int32_t F, int64_t P, int32_t nS,
+                           const int32_t* rows, const int32_t* cols, const double complex* S0,
+                           const double complex* field, const double complex* Sconst,
+                           int64_t n_batch, const double complex* svar, int32_t L,
+                           const int64_t* loss_idx, const double* target, int32_t mode,
+                           double complex* grad_out) {
+  const int32_t n = n0 + n1;
+  const int64_t tw = (mode == 0) ? 1 : 2;
+  const double norm = (double)F * n1 * L;
+  int n_bad = 0;
+  (void)P;
+#pragma omp parallel for schedule(static) reduction(+ : n_bad)
+  for (int64_t b = 0; b < n_batch; ++b) {
+    double complex* SC = malloc(sizeof(double complex) * (size_t)n * n);
+    double complex* A = malloc(sizeof(double complex) * (size_t)n0 * n0);
+    double complex* W = malloc(sizeof(double complex) * (size_t)n0 * n1);
+    double complex* SW = malloc(sizeof(double complex) * (size_t)n0 * n1);
+    double complex* G = malloc(sizeof(double complex) * (size_t)(n1 * L > 0 ? n1 * L : 1));
+    double complex* col = malloc(sizeof(double complex) * (size_t)n0);
+    int32_t* piv = malloc(sizeof(int32_t) * (size_t)n0);
+    for (int32_t f = 0; f < F; ++f) {
+      double complex* g = grad_out + (b * F + f) * nS;
+      for (int32_t i = 0; i < nS; ++i) g[i] = 0.0;
+      const double complex* S0f = S0 + (int64_t)f * n0 * n0;
+      oracle_sroute_assemble(n0, n1, nS, rows, cols, S0f, Sconst + (int64_t)f * n * n,
+                             svar + (b * F + f) * nS, SC, A);
+      if (oracle_lu(n0, A, piv) != 0) {
+        n_bad += 1;
+        continue;
+      }
+      oracle_sroute_wave_ratio(n0, n1, A, piv, SC, col, W);
+      const double complex* fd = field + (int64_t)f * P * n0;
+      for (int32_t c = 0; c < n1; ++c)
+        for (int32_t l = 0; l < L; ++l) {
+          double complex s = 0.0;
+          for (int32_t k = 0; k < n0; ++k) s += fd[loss_idx[l] * n0 + k] * W[k * n1 + c];
+          oracle_point_loss(mode, s, target + (((int64_t)f * n1 + c) * L + l) * tw, &G[c * L + l]);
+        }
+      for (int32_t k = 0; k < n0; ++k) /* S0 W */
+        for (int32_t c = 0; c < n1; ++c) {
+          double complex s = 0.0;
+          for (int32_t j = 0; j < n0; ++j) s += S0f[k * n0 + j] * W[j * n1 + c];
+          SW[k * n1 + c] = s;
+        }
+      for (int32_t i = 0; i < nS; ++i) {
+        const int32_t r = rows[i], cc = cols[i];
+        if (r >= n0) continue;
+        for (int32_t c = 0; c < n1; ++c) {
+          /* column c of the Eq. 10 bracket, then one solve */
+          for (int32_t k = 0; k < n0; ++k) col[k] = 0.0;
+          if (cc < n0) col[r] = SW[cc * n1 + c];
+          else if (cc - n0 == c) col[r] = 1.0;
+          else continue;
+          oracle_lu_solve(n0, A, piv, col);
+          for (int32_t l = 0; l < L; ++l) {
+            double complex db = 0.0;
+            for (int32_t k = 0; k < n0; ++k) db += fd[loss_idx[l] * n0 + k] * col[k];
+            g[i] += conj(db) * G[c * L + l] / norm;
+          }
+        }
+      }
+    }
+    free(SC);
+    free(A);
+    free(W);
+    free(SW);
+    free(G);
+    free(col);
+    free(piv);
+  }
+  return n_bad;
+}

@@ -426,6 +426,162 @@ def test_eq10_derivative_equals_direct():
         assert _rel(dI_s[k], dI_z[k]) < 1e-9
 
 
+def _sroute_from_zroute(n_cells=3, seed=5, F=2, n_batch=3, Z0=50.0, P_in=1.0):
+    """A loop structure written in the pipeline's terms (Sec. III, Eq. 3-7): ports at the
+    cell capacitors and at the drive loop, S0 = (Z - Z0)(Z + Z0)^-1 per frequency, fields
+    per unit incident wave at port k with the other ports matched, i.e. the Biot-Savart
+    field of the currents (1 - S0) e_k / Z0, times sqrt(Z0 P) (Eq. 4's V-exc) so that the
+    combined field is the physical one. The drive port sees a matched source through S_C12;
+    each cell port is loaded by its capacitor, scattered into S_C11 as Gamma (Eq. 3)."""
+    rng = np.random.default_rng(seed)
+    loops = W.square_array(n_cells, 1, seg_per_side=4)
+    loops.append(W.square_loop(0.2, 4, 0.0, 0.0, 0.03))
+    off, vx, vy, vz = _loop_arrays(loops)
+    _, M = oracle.inductance(off, vx, vy, vz, 1e-3)
+    px, py, pz = W.grid_plane(5, 0.1, 0.02)
+    H = oracle.basis(off, vx, vy, vz, px, py, pz, 1e-3)
+    n0 = len(loops)
+    omega = 2 * np.pi * np.linspace(62e6, 65e6, F)
+    R = np.full(n0, 0.1)
+    C = rng.uniform(20e-12, 200e-12, (n_batch, n0 - 1))
+    S0 = np.zeros((F, n0, n0), complex)
+    field = np.zeros((F, len(px), n0), complex)
+    for f, w in enumerate(omega):
+        Z = np.diag(R).astype(complex) + 1j * w * M
+        S0[f] = np.linalg.solve((Z + Z0 * np.eye(n0)).T, (Z - Z0 * np.eye(n0)).T).T
+        field[f] = H @ (np.eye(n0) - S0[f]) / Z0 * np.sqrt(Z0 * P_in)
+    Sconst = np.zeros((F, n0 + 1, n0 + 1), complex)
+    Sconst[:, n0 - 1, n0] = 1.0  # S_C12: the source's wave enters the drive port
+    rows = np.arange(n0 - 1)
+    Zl = 1 / (1j * omega[None, :, None] * C[:, None, :])  # [b, f, k]
+    svar = (Zl - Z0) / (Zl + Z0)  # Eq. 3
+    return dict(H=H, M=M, R=R, C=C, omega=omega, S0=S0, field=field, Sconst=Sconst,
+                rows=rows, cols=rows, svar=svar, Z0=Z0, P_in=P_in, n0=n0)
+
+
+def test_sroute_pipeline_equals_impedance_route():
+    """The pipeline's combined field equals H I of the impedance route with the drive loop
+    fed by a Thevenin source E = 2 sqrt(Z0 P) behind Z0 and the cells closed by their
+    capacitors (the Z <-> S identity of Eq. 3-6 carried through Eq. 7)."""
+    c = _sroute_from_zroute()
+    out = oracle.sroute_pipeline(c["S0"], c["field"], c["Sconst"], c["rows"], c["cols"], c["svar"])
+    assert out["n_singular"] == 0
+    n0, Z0 = c["n0"], c["Z0"]
+    for b in range(c["C"].shape[0]):
+        for f, w in enumerate(c["omega"]):
+            Z = np.diag(c["R"]).astype(complex) + 1j * w * c["M"]
+            Zl = np.append(1 / (1j * w * c["C"][b]), Z0)
+            E = np.zeros(n0, complex)
+            E[-1] = 2 * np.sqrt(Z0 * c["P_in"])
+            _, I = oracle.solve_loaded(Z, Zl, E)
+            assert _rel(out["B"][b, 0, f], c["H"] @ I) < 1e-11
+
+
+def test_sroute_one_port_closed_form():
+    """n0 = n1 = 1: A = 1 - s11 s0 and W = s12 / (1 - s11 s0) (Eq. 6), B = field W (Eq. 7)."""
+    rng = np.random.default_rng(3)
+    F, P = 3, 4
+    S0 = (rng.uniform(-0.6, 0.6, (F, 1, 1)) + 1j * rng.uniform(-0.6, 0.6, (F, 1, 1)))
+    field = rng.standard_normal((F, P, 1)) + 1j * rng.standard_normal((F, P, 1))
+    Sconst = np.zeros((F, 2, 2), complex)
+    Sconst[:, 0, 1] = 0.7 - 0.2j
+    svar = rng.uniform(-0.9, 0.9, (2, F, 1)) + 1j * rng.uniform(-0.9, 0.9, (2, F, 1))
+    out = oracle.sroute_pipeline(S0, field, Sconst, [0], [0], svar)
+    Wc = (0.7 - 0.2j) / (1 - svar[:, :, 0] * S0[None, :, 0, 0])
+    assert _rel(out["W"][:, :, 0, 0], Wc) < 1e-14
+    assert _rel(out["B"][:, 0], Wc[:, :, None] * field[None, :, :, 0]) < 1e-14
+
+
+def test_sroute_two_ports_by_cramer():
+    """A general 2 x 2 network (every S11 entry variable, two external ports): W from
+    Cramer's rule on A = 1 - S11 S0."""
+    rng = np.random.default_rng(4)
+    F, P, n0, n1 = 1, 3, 2, 2
+    S0 = (rng.standard_normal((F, n0, n0)) + 1j * rng.standard_normal((F, n0, n0))) * 0.4
+    field = rng.standard_normal((F, P, n0)) + 1j * rng.standard_normal((F, P, n0))
+    Sconst = (rng.standard_normal((F, 4, 4)) + 1j * rng.standard_normal((F, 4, 4))) * 0.3
+    rows, cols = [0, 0, 1, 1, 2], [0, 1, 0, 1, 3]
+    svar = (rng.standard_normal((1, F, 5)) + 1j * rng.standard_normal((1, F, 5))) * 0.3
+    out = oracle.sroute_pipeline(S0, field, Sconst, rows, cols, svar)
+    SC = Sconst[0].copy()
+    for i, (r, q) in enumerate(zip(rows, cols)):
+        SC[r, q] += svar[0, 0, i]
+    A = np.eye(2) - SC[:2, :2] @ S0[0]
+    det = A[0, 0] * A[1, 1] - A[0, 1] * A[1, 0]
+    for c in range(n1):
+        b0, b1 = SC[0, 2 + c], SC[1, 2 + c]
+        w0 = (b0 * A[1, 1] - A[0, 1] * b1) / det
+        w1 = (A[0, 0] * b1 - b0 * A[1, 0]) / det
+        assert _rel(out["W"][0, 0, :, c], [w0, w1]) < 1e-13
+        assert _rel(out["B"][0, c, 0], field[0] @ np.array([w0, w1])) < 1e-13
+
+
+def _sroute_random(mode, seed=7, F=2, n0=4, n1=2, P=9, n_batch=2):
+    rng = np.random.default_rng(seed)
+    S0 = (rng.standard_normal((F, n0, n0)) + 1j * rng.standard_normal((F, n0, n0))) * 0.25
+    field = rng.standard_normal((F, P, n0)) + 1j * rng.standard_normal((F, P, n0))
+    n = n0 + n1
+    Sconst = (rng.standard_normal((F, n, n)) + 1j * rng.standard_normal((F, n, n))) * 0.2
+    # S11 diagonal and off-diagonal, S12, S21 and S22 entries
+    rows = np.array([0, 1, 2, 3, 1, 0, 2, 5, 4])
+    cols = np.array([0, 1, 2, 3, 3, 4, 5, 1, 4])
+    svar = (rng.standard_normal((n_batch, F, len(rows))) + 1j * rng.standard_normal((n_batch, F, len(rows)))) * 0.3
+    li = np.array([0, 4, 7])
+    if mode == 0:
+        t = np.abs(rng.standard_normal((F, n1, len(li))))
+    else:
+        t = rng.standard_normal((F, n1, len(li), 2))
+    return S0, field, Sconst, rows, cols, svar, li, t
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_sroute_gradient_central_differences(mode):
+    """Eq. 10's gradient against central differences of the objective along the real and
+    imaginary part of every variable S-parameter (torch's dL/dRe + j dL/dIm); S21 and S22
+    entries do not reach the field and get exactly 0."""
+    S0, field, Sconst, rows, cols, svar, li, t = _sroute_random(mode)
+    g = oracle.sroute_gradient(S0, field, Sconst, rows, cols, svar, li, t, mode=mode)
+    h = 1e-6
+    fd = np.zeros_like(g)
+    for idx in np.ndindex(*svar.shape):
+        for unit in (1.0, 1j):
+            sp, sm = svar.copy(), svar.copy()
+            sp[idx] += h * unit
+            sm[idx] -= h * unit
+            lp = oracle.sroute_pipeline(S0, field, Sconst, rows, cols, sp, li, t, mode=mode, want_B=False)["loss"]
+            lm = oracle.sroute_pipeline(S0, field, Sconst, rows, cols, sm, li, t, mode=mode, want_B=False)["loss"]
+            d = (lp[idx[0]] - lm[idx[0]]) / (2 * h)
+            fd[idx] += d * (1.0 if unit == 1.0 else 1j)
+    assert _rel(g, fd) < 1e-7
+    assert np.all(g[:, :, rows >= 4] == 0)
+
+
+def test_sroute_gradient_through_eq3_equals_impedance_adjoint():
+    """Chaining Eq. 10 through Eq. 3 (dGamma/dC = 2 Z0 / (Zl + Z0)^2 * j/(w C^2)) gives the
+    impedance route's adjoint dloss/dC on the same structure and objective."""
+    c = _sroute_from_zroute(n_batch=2)
+    F, n0, Z0 = len(c["omega"]), c["n0"], c["Z0"]
+    li = np.array([2, 7, 12, 20])
+    t = np.full((F, 1, len(li)), 2e-7)
+    g = oracle.sroute_gradient(c["S0"], c["field"], c["Sconst"], c["rows"], c["cols"], c["svar"], li, t)
+    w = c["omega"][None, :, None]
+    Zl = 1 / (1j * w * c["C"][:, None, :])
+    dgam = 2 * Z0 / (Zl + Z0) ** 2 * (1j / (w * c["C"][:, None, :] ** 2))
+    gC = np.real(np.conj(g) * dgam).sum(axis=1)  # [b, n0 - 1]
+    # impedance route: the drive loop's Z0 in R, an "infinite" capacitor, EMF 2 sqrt(Z0 P)
+    R = c["R"].copy()
+    R[-1] += Z0
+    Cz = np.concatenate([c["C"], np.full((c["C"].shape[0], 1), 1e30)], axis=1)
+    V = np.zeros((F, n0), complex)
+    V[:, -1] = 2 * np.sqrt(Z0 * c["P_in"])
+    gz = oracle.gradient(c["H"], c["M"], R, Cz, c["omega"], V, li, t[:, 0, :])
+    out = oracle.sroute_pipeline(c["S0"], c["field"], c["Sconst"], c["rows"], c["cols"], c["svar"],
+                                 li, t, want_B=False)
+    lz = oracle.forward(c["H"], c["M"], R, Cz, c["omega"], V, li, t[:, 0, :], want_B=False)["loss"]
+    assert _rel(out["loss"], lz) < 1e-10
+    assert _rel(gC, gz[:, :-1]) < 1e-9
+
+
 # ---------------------------------------------------------------- objective and gradient
 def _grad_case(mode=0, n=6, F=3, n_cfg=2, seed=11):
     rng = np.random.default_rng(seed)
