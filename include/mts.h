@@ -332,6 +332,118 @@ mts_status mts_adam_step(int64_t n, const mts_adam* opt, double* C, double* u,
                          const double* loss, int64_t n_loss, double* loss_history,
                          int64_t history_len, mts_stream stream);
 
+/* =====================================================================================
+ * Scattering-parameter route (paper Sec. III and III-A, Eq. 3-7, Eq. 10): the paper's own
+ * pipeline, on a structure described by its S-matrix S0 and per-port fields exported from
+ * any solver, with a network tensor S_C whose variable entries the caller computes (the
+ * "user-defined preprocessing" of Sec. III-A, e.g. mts_rc_reflection below).
+ *
+ * With n = n0 + n1, per configuration b and frequency f:
+ *   S_C   = S_C,const[f] + scatter(svar[b][f]) (entry i at row svar_row[i], column
+ *           svar_col[i]; Sec. III-A steps 1-3)
+ *   S11   = S_C[0:n0, 0:n0],  S12 = S_C[0:n0, n0:n]       (Fig. 1: S21, S22 do not reach
+ *                                                           the structure's field)
+ *   A     = 1 - S11 S0[f],    W = A^-1 S12                (Eq. 6: the wave ratio
+ *                                                           V+res / V-exc, n0 x n1)
+ *   Bcomb[b][c][f][p] = sum_k field[f][p][k] W[k][c]      (Eq. 7)
+ * objective: mean over (f, c, loss point l) of (|Bcomb| - t)^2 or |Bcomb - t|^2, and its
+ * gradient with respect to every svar entry (Eq. 10, evaluated in adjoint form: one solve
+ * with A^H per system), in torch's convention dL/dRe + j dL/dIm.
+ *
+ * Solve: LU with partial pivoting of A in shared memory (FP32 for MTS_MIXED / MTS_BF16,
+ * FP64 for MTS_FP64) with iterative refinement on FP64 residuals, stopping as for mts_eval's
+ * refine_tol / max_refine. Superposition: the kernels of mts_superpose, with field[f] as the
+ * real basis [Re field | Im field] of 2 n0 columns (complex field times complex W).
+ * ===================================================================================== */
+typedef struct mts_sparams {
+  int32_t n0;        /* structure ports, 1 <= n0 <= 96 (more: MTS_EUNSUPPORTED) */
+  int32_t n1;        /* external (excitation) ports, 1 <= n1 <= 8 (more: MTS_EUNSUPPORTED) */
+  int32_t n_freq;    /* >= 1 */
+  int64_t n_points;  /* >= 0 */
+  int32_t n_svar;    /* variable S-parameters per (configuration, frequency), 1 .. 1024 */
+  int32_t n_loss;    /* loss points, >= 0 */
+  const int32_t* h_svar_row; /* host [n_svar]: row of S_C, 0 .. n-1 */
+  const int32_t* h_svar_col; /* host [n_svar]: column of S_C, 0 .. n-1; (row, col) distinct */
+  const double* S0;          /* device complex [n_freq][n0][n0] (Eq. 5: V-res = S0 V+res) */
+  const double* field;       /* device complex [n_freq][n_points][n0]: one field component
+                                at point p when port k receives a unit incident wave and the
+                                other ports are matched (Eq. 7's B); NULL if n_points == 0 */
+  const double* sc_const;    /* device complex [n_freq][n][n] S_C,const, or NULL (zero) */
+  const int64_t* loss_idx;   /* device [n_loss] point indices (0 .. n_points-1, trusted) */
+} mts_sparams;
+
+/* Per-call inputs of the route.
+ *   svar    device complex [n_cfg][n_freq][n_svar]
+ *   target  device [n_freq][n1][n_loss], real (MTS_LOSS_ABS) or complex (MTS_LOSS_COMPLEX);
+ *           NULL = no objective
+ *   refine_tol, max_refine as in mts_eval (0 selects 1e-8 and 8). */
+typedef struct mts_sroute_eval {
+  int64_t n_cfg;
+  const double* svar;
+  const double* target;
+  int32_t loss_mode; /* mts_loss_mode */
+  double refine_tol;
+  int32_t max_refine;
+} mts_sroute_eval;
+
+/* Basis of the route: the field as superposition operands, T[f] = S_C,const11 S0[f] (the
+ * constant part of S11 S0), and the scatter tables of svar. Device buffer of
+ * mts_sroute_basis_bytes(...) bytes, 256-byte aligned, written by mts_sroute_build (once per
+ * S0, field and S_C,const; rebuild when any of them changes). */
+size_t mts_sroute_basis_bytes(const mts_sparams* sp, mts_precision prec);
+mts_status mts_sroute_build(const mts_sparams* sp, mts_precision prec, void* sbasis,
+                            size_t sbasis_bytes, mts_stream stream);
+
+/* Tape of the route (wave ratios, currents of the superposition, LU factors and pivots of
+ * every system, objective partials, status): device buffer of mts_sroute_tape_bytes(...)
+ * bytes, 256-byte aligned. */
+size_t mts_sroute_tape_bytes(const mts_sparams* sp, int64_t n_cfg, mts_precision prec);
+
+/* Eq. 3-7 for every configuration and frequency. Outputs (each may be NULL):
+ *   B_out    device [n_cfg][n1][n_freq][n_points] complex (complex128 for MTS_FP64, else
+ *            complex64): Bcomb
+ *   W_out    device complex [n_cfg][n_freq][n0][n1]: the wave ratios
+ *   loss_out device [n_cfg]: the objective (needs ev->target) */
+mts_status mts_sroute_forward(const mts_sparams* sp, mts_precision prec, const void* sbasis,
+                              const mts_sroute_eval* ev, void* B_out, double* W_out,
+                              double* loss_out, void* tape, size_t tape_bytes,
+                              mts_stream stream);
+
+/* Eq. 10 in adjoint form: grad_svar (device complex [n_cfg][n_freq][n_svar], overwritten) =
+ *     grad_loss[b] * dloss_b/dsvar          (grad_loss device [n_cfg], or NULL: no term;
+ *                                             needs ev->target)
+ *   + dL/dsvar of a field cotangent grad_B   (device, layout and type of B_out, or NULL)
+ * `ev` must be the forward's (same svar). Entries in rows n0 .. n-1 (S21, S22) get 0. */
+mts_status mts_sroute_backward(const mts_sparams* sp, mts_precision prec, const void* sbasis,
+                               const mts_sroute_eval* ev, void* tape, size_t tape_bytes,
+                               const void* grad_B, const double* grad_loss, double* grad_svar,
+                               mts_stream stream);
+
+/* Synchronises `stream` and summarises the per-system status of the last forward on this
+ * tape: MTS_OK, or MTS_ENOCONV if a system missed the refinement tolerance, had a zero
+ * pivot or met a non-finite value (n_bad, if not NULL, receives their number). */
+mts_status mts_sroute_status(const mts_sparams* sp, int64_t n_cfg, mts_precision prec,
+                             const void* tape, int64_t* n_bad, mts_stream stream);
+
+/* Preprocessing for loads that are series RC circuits (Eq. 2: Z = R - j/(w C); Eq. 3:
+ * Gamma = (Z - Z0)/(Z + Z0)): svar[b][f][svar_offset + k] = Gamma(R[b][k], C[b][k], w_f) for
+ * k < n_loads, other entries untouched. R, C device [n_cfg][n_loads] (R may be NULL: 0 ohm),
+ * omega device [n_freq], Z0 > 0 ohm, svar device complex [n_cfg][n_freq][svar_stride] with
+ * svar_offset + n_loads <= svar_stride. */
+mts_status mts_rc_reflection(int64_t n_cfg, int32_t n_freq, int32_t n_loads, const double* omega,
+                             const double* R, const double* C, double Z0, int32_t svar_stride,
+                             int32_t svar_offset, double* svar, mts_stream stream);
+
+/* Its vector-Jacobian product: from grad_svar (device complex, the layout of svar above),
+ *   grad_C[b][k] = sum_f Re(conj(g) dGamma/dC),  dGamma/dC = 2 Z0/(Z + Z0)^2 * j/(w C^2)
+ *   grad_R[b][k] = sum_f Re(conj(g) dGamma/dR),  dGamma/dR = 2 Z0/(Z + Z0)^2
+ * (overwritten; either may be NULL). */
+mts_status mts_rc_reflection_vjp(int64_t n_cfg, int32_t n_freq, int32_t n_loads,
+                                 const double* omega, const double* R, const double* C, double Z0,
+                                 int32_t svar_stride, int32_t svar_offset,
+                                 const double* grad_svar, double* grad_R, double* grad_C,
+                                 mts_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -91,9 +91,8 @@ PlanLayout plan_layout(int n_struct) {
 }
 
 // Elements of the tensor-core B operand, and the GEMM / SIMT work units of the superposition.
-static int64_t bop_elems(const mts_problem* pb, int64_t n_cfg, int npieces, int64_t* units,
-                         int64_t* simt_units = nullptr, int64_t* max_simt = nullptr,
-                         int64_t simt_max_sys = kSimtSys) {
+int64_t bop_elems(const mts_problem* pb, int64_t n_cfg, int npieces, int64_t* units,
+                  int64_t* simt_units, int64_t* max_simt, int64_t simt_max_sys) {
   int64_t a = 0, u = 0, v = 0, vmax = 0;
   for (int s = 0; s < pb->n_struct; ++s) {
     int64_t N = pb->h_port_off[s + 1] - pb->h_port_off[s];
@@ -277,6 +276,50 @@ static ReduceArgs reduce_args(const mts_problem* pb, mts_precision prec, const v
   return r;
 }
 
+cudaError_t superpose_core(const mts_problem* pb, mts_precision prec, const void* basis,
+                           int64_t n_cfg, int64_t simt_thr, const double* I,
+                           const __nv_bfloat16* Bop, const void* plan, int32_t* err, void* B_out,
+                           cudaStream_t st) {
+  BasisLayout bl = basis_layout(pb, prec);
+  PlanLayout pl = plan_layout(pb->n_struct);
+  ProblemSums ps = problem_sums(pb, prec);
+  const char* B = static_cast<const char*>(basis);
+  const char* Pl = static_cast<const char*>(plan);
+  SuperposeArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n_struct = pb->n_struct;
+  a.n_freq = pb->n_freq;
+  a.n_ports = pb->n_ports;
+  a.port_off = pb->port_off;
+  a.freq_off = pb->freq_off;
+  a.point_off = pb->point_off;
+  a.t = dev_tables(basis, bl, pb->n_struct, pb->n_freq);
+  a.n_cfg = n_cfg;
+  a.sumFN = ps.sumFN;
+  a.sumFP = ps.sumFP;
+  bop_elems(pb, n_cfg, n_pieces(prec), &a.total_units, &a.total_simt, &a.max_simt, simt_thr);
+  a.unit_off = reinterpret_cast<const int64_t*>(Pl + pl.unit_off);
+  a.simt_off = reinterpret_cast<const int64_t*>(Pl + pl.simt_off);
+  a.H = B + bl.H;
+  a.I = I;
+  a.Aop = reinterpret_cast<const __nv_bfloat16*>(B + bl.Aop);
+  a.Bop = Bop;
+  a.bop_off = reinterpret_cast<const int64_t*>(Pl + pl.bop_off);
+  a.npieces = n_pieces(prec);
+  a.B_out = B_out;
+  a.err = err;
+  if (pb->n_struct == 1 && a.total_units > 0) {
+    a.uni.on = 1;
+    a.uni.N = pb->h_port_off[1];
+    a.uni.F = pb->h_freq_off[1];
+    a.uni.P = pb->h_point_off[1];
+    a.uni.nkc = (a.uni.N + kChunkK - 1) / kChunkK;
+    a.uni.nptile = (a.uni.P + kTileP - 1) / kTileP;
+    a.uni.nntile = (2 * n_cfg * a.uni.F + kTileN - 1) / kTileN;
+  }
+  return launch_superpose(a, prec, st);
+}
+
 }  // namespace mts
 
 using namespace mts;
@@ -397,46 +440,12 @@ mts_status mts_superpose(const mts_problem* pb, mts_precision prec, const void* 
   if (validate_prec(prec) != MTS_OK || !basis || !tape || !B_out) return MTS_EINVAL;
   v = validate_eval(pb, ev);
   if (v != MTS_OK) return v;
-  BasisLayout bl = basis_layout(pb, prec);
   TapeLayout tl = tape_layout(pb, ev->n_cfg, prec);
-  PlanLayout pl = plan_layout(pb->n_struct);
-  ProblemSums ps = problem_sums(pb, prec);
-  const char* B = static_cast<const char*>(basis);
   const char* T = static_cast<const char*>(tape);
-  SuperposeArgs a;
-  std::memset(&a, 0, sizeof(a));
-  a.n_struct = pb->n_struct;
-  a.n_freq = pb->n_freq;
-  a.n_ports = pb->n_ports;
-  a.port_off = pb->port_off;
-  a.freq_off = pb->freq_off;
-  a.point_off = pb->point_off;
-  a.t = dev_tables(basis, bl, pb->n_struct, pb->n_freq);
-  a.n_cfg = ev->n_cfg;
-  a.sumFN = ps.sumFN;
-  a.sumFP = ps.sumFP;
-  bop_elems(pb, ev->n_cfg, n_pieces(prec), &a.total_units, &a.total_simt, &a.max_simt,
-            simt_threshold(ev));
-  a.unit_off = reinterpret_cast<const int64_t*>(T + tl.plan + pl.unit_off);
-  a.simt_off = reinterpret_cast<const int64_t*>(T + tl.plan + pl.simt_off);
-  a.H = B + bl.H;
-  a.I = reinterpret_cast<const double*>(T + tl.I);
-  a.Aop = reinterpret_cast<const __nv_bfloat16*>(B + bl.Aop);
-  a.Bop = reinterpret_cast<const __nv_bfloat16*>(T + tl.Bop);
-  a.bop_off = reinterpret_cast<const int64_t*>(T + tl.plan + pl.bop_off);
-  a.npieces = n_pieces(prec);
-  a.B_out = B_out;
-  a.err = reinterpret_cast<int32_t*>(const_cast<char*>(T) + tl.err);
-  if (pb->n_struct == 1 && a.total_units > 0) {
-    a.uni.on = 1;
-    a.uni.N = pb->h_port_off[1];
-    a.uni.F = pb->h_freq_off[1];
-    a.uni.P = pb->h_point_off[1];
-    a.uni.nkc = (a.uni.N + kChunkK - 1) / kChunkK;
-    a.uni.nptile = (a.uni.P + kTileP - 1) / kTileP;
-    a.uni.nntile = (2 * ev->n_cfg * a.uni.F + kTileN - 1) / kTileN;
-  }
-  return cuda_status(launch_superpose(a, prec, (cudaStream_t)stream));
+  return cuda_status(superpose_core(
+      pb, prec, basis, ev->n_cfg, simt_threshold(ev), reinterpret_cast<const double*>(T + tl.I),
+      reinterpret_cast<const __nv_bfloat16*>(T + tl.Bop), T + tl.plan,
+      reinterpret_cast<int32_t*>(const_cast<char*>(T) + tl.err), B_out, (cudaStream_t)stream));
 }
 
 mts_status mts_forward(const mts_problem* pb, mts_precision prec, const void* basis,

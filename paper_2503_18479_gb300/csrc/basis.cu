@@ -599,8 +599,8 @@ __global__ void export_h_kernel(int64_t n, int n_struct, const int64_t* __restri
 // ---------------------------------------------------------------------------------------
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-cudaError_t launch_build_basis(const mts_problem* pb, mts_precision prec, void* basis,
-                               const BasisLayout& bl, const ProblemSums& ps, cudaStream_t st) {
+cudaError_t launch_basis_tables(const mts_problem* pb, mts_precision prec, void* basis,
+                                const BasisLayout& bl, cudaStream_t st) {
   char* B = static_cast<char*>(basis);
   TableLayout tl = table_layout(pb->n_struct, pb->n_freq);
   char* T = B + bl.tables;
@@ -614,6 +614,36 @@ cudaError_t launch_build_basis(const mts_problem* pb, mts_precision prec, void* 
       (int64_t*)(T + tl.aop_off), (int64_t*)(T + tl.ptile_off), (int64_t*)(T + tl.pair_off),
       (int32_t*)(T + tl.freq_struct), (int32_t*)(T + tl.cls_freq));
   note_launch();
+  return cudaGetLastError();
+}
+
+static int64_t point_tiles(const mts_problem* pb) {
+  int64_t ntiles = 0;
+  for (int s = 0; s < pb->n_struct; ++s)
+    ntiles += (pb->h_point_off[s + 1] - pb->h_point_off[s] + kTileP - 1) / kTileP;
+  return ntiles;
+}
+
+cudaError_t launch_pack_a(const mts_problem* pb, mts_precision prec, void* basis,
+                          const BasisLayout& bl, cudaStream_t st) {
+  const int npieces = n_pieces(prec);
+  const int64_t ntiles = point_tiles(pb);
+  if (npieces == 0 || ntiles == 0) return cudaSuccess;
+  char* B = static_cast<char*>(basis);
+  DevTables t = dev_tables(basis, bl, pb->n_struct, pb->n_freq);
+  pack_a_kernel<<<(unsigned)ntiles, 256, 0, st>>>(pb->n_struct, t.ptile_off, pb->port_off,
+                                                  pb->point_off, t.pn_off, t.aop_off,
+                                                  (const float*)(B + bl.H), npieces,
+                                                  (__nv_bfloat16*)(B + bl.Aop));
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_basis(const mts_problem* pb, mts_precision prec, void* basis,
+                               const BasisLayout& bl, const ProblemSums& ps, cudaStream_t st) {
+  char* B = static_cast<char*>(basis);
+  cudaError_t e = launch_basis_tables(pb, prec, basis, bl, st);
+  if (e != cudaSuccess) return e;
   DevTables t = dev_tables(basis, bl, pb->n_struct, pb->n_freq);
   // host copies of the tile and pair counts
   int64_t ntiles = 0, npairs = 0;
@@ -661,14 +691,9 @@ cudaError_t launch_build_basis(const mts_problem* pb, mts_precision prec, void* 
           (float*)(B + bl.Hloss32));
     note_launch();
   }
-  if (npieces > 0) {
-    pack_a_kernel<<<(unsigned)ntiles, 256, 0, st>>>(pb->n_struct, t.ptile_off, pb->port_off,
-                                                    pb->point_off, t.pn_off, t.aop_off,
-                                                    (const float*)(B + bl.H), npieces,
-                                                    (__nv_bfloat16*)(B + bl.Aop));
-    note_launch();
-  }
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_pack_a(pb, prec, basis, bl, st);
 }
 
 cudaError_t launch_export_basis(const mts_problem* pb, mts_precision prec, const void* basis,

@@ -69,6 +69,11 @@ struct ReduceArgs {
 
 cudaError_t launch_build_basis(const mts_problem* pb, mts_precision prec, void* basis,
                                const BasisLayout& bl, const ProblemSums& ps, cudaStream_t st);
+// The two table/operand steps of launch_build_basis, reused for bases built from given fields.
+cudaError_t launch_basis_tables(const mts_problem* pb, mts_precision prec, void* basis,
+                                const BasisLayout& bl, cudaStream_t st);
+cudaError_t launch_pack_a(const mts_problem* pb, mts_precision prec, void* basis,
+                          const BasisLayout& bl, cudaStream_t st);
 cudaError_t launch_export_basis(const mts_problem* pb, mts_precision prec, const void* basis,
                                 const BasisLayout& bl, const ProblemSums& ps, double* H_out,
                                 double* M_out, cudaStream_t st);
@@ -119,6 +124,18 @@ struct SuperposeArgs {
 };
 
 cudaError_t launch_superpose(const SuperposeArgs& a, mts_precision prec, cudaStream_t st);
+
+// Elements of the tensor-core B operand of a problem, and its GEMM / SIMT work units.
+int64_t bop_elems(const mts_problem* pb, int64_t n_cfg, int npieces, int64_t* units,
+                  int64_t* simt_units = nullptr, int64_t* max_simt = nullptr,
+                  int64_t simt_max_sys = kSimtSys);
+
+// B = H I of a problem for currents I (device complex [n_cfg][sum F N]) whose B operand and
+// plan tables (launch_plan) are in place: the superposition step of mts_superpose.
+cudaError_t superpose_core(const mts_problem* pb, mts_precision prec, const void* basis,
+                           int64_t n_cfg, int64_t simt_thr, const double* I,
+                           const __nv_bfloat16* Bop, const void* plan, int32_t* err, void* B_out,
+                           cudaStream_t st);
 
 struct FieldAdjArgs {
   int n_struct, n_freq, n_ports;

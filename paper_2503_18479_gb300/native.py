@@ -26,7 +26,10 @@ PRECISIONS = {"fp64": MTS_FP64, "mixed": MTS_MIXED, "bf16": MTS_BF16}
 EXPORTED = ["mts_status_string", "mts_version", "mts_launch_count", "mts_basis_bytes",
             "mts_build_basis", "mts_basis_export", "mts_basis_status", "mts_tape_bytes",
             "mts_solve", "mts_superpose", "mts_forward", "mts_backward", "mts_tape_status",
-            "mts_solve_static", "mts_adam_step", "mts_param_grad"]
+            "mts_solve_static", "mts_adam_step", "mts_param_grad", "mts_sroute_basis_bytes",
+            "mts_sroute_build", "mts_sroute_tape_bytes", "mts_sroute_forward",
+            "mts_sroute_backward", "mts_sroute_status", "mts_rc_reflection",
+            "mts_rc_reflection_vjp"]
 MTS_PROJ_NONE, MTS_PROJ_CLIP, MTS_PROJ_TANH = 0, 1, 2
 PROJECTIONS = {None: MTS_PROJ_NONE, "none": MTS_PROJ_NONE, "clip": MTS_PROJ_CLIP, "tanh": MTS_PROJ_TANH}
 
@@ -60,6 +63,20 @@ class MtsAdam(ct.Structure):
     _fields_ = [("lr", ct.c_double), ("beta1", ct.c_double), ("beta2", ct.c_double),
                 ("eps", ct.c_double), ("projection", ct.c_int32), ("c_min", ct.c_double),
                 ("c_max", ct.c_double)]
+
+
+class MtsSparams(ct.Structure):
+    _fields_ = [
+        ("n0", ct.c_int32), ("n1", ct.c_int32), ("n_freq", ct.c_int32), ("n_points", ct.c_int64),
+        ("n_svar", ct.c_int32), ("n_loss", ct.c_int32), ("h_svar_row", ct.c_void_p),
+        ("h_svar_col", ct.c_void_p), ("S0", ct.c_void_p), ("field", ct.c_void_p),
+        ("sc_const", ct.c_void_p), ("loss_idx", ct.c_void_p),
+    ]
+
+
+class MtsSrouteEval(ct.Structure):
+    _fields_ = [("n_cfg", ct.c_int64), ("svar", ct.c_void_p), ("target", ct.c_void_p),
+                ("loss_mode", ct.c_int32), ("refine_tol", ct.c_double), ("max_refine", ct.c_int32)]
 
 
 _lock = threading.Lock()
@@ -107,6 +124,24 @@ def lib():
             L.mts_param_grad.argtypes = [PP, ct.c_int, p, PE, p, sz, p, p, p, p, p, p]
             L.mts_adam_step.restype = ct.c_int
             L.mts_adam_step.argtypes = [i64, ct.POINTER(MtsAdam), p, p, p, p, p, p, p, i64, p, i64, p]
+            PS, PSE = ct.POINTER(MtsSparams), ct.POINTER(MtsSrouteEval)
+            d = ct.c_double
+            L.mts_sroute_basis_bytes.restype = sz
+            L.mts_sroute_basis_bytes.argtypes = [PS, ct.c_int]
+            L.mts_sroute_build.restype = ct.c_int
+            L.mts_sroute_build.argtypes = [PS, ct.c_int, p, sz, p]
+            L.mts_sroute_tape_bytes.restype = sz
+            L.mts_sroute_tape_bytes.argtypes = [PS, i64, ct.c_int]
+            L.mts_sroute_forward.restype = ct.c_int
+            L.mts_sroute_forward.argtypes = [PS, ct.c_int, p, PSE, p, p, p, p, sz, p]
+            L.mts_sroute_backward.restype = ct.c_int
+            L.mts_sroute_backward.argtypes = [PS, ct.c_int, p, PSE, p, sz, p, p, p, p]
+            L.mts_sroute_status.restype = ct.c_int
+            L.mts_sroute_status.argtypes = [PS, i64, ct.c_int, p, ct.POINTER(ct.c_int64), p]
+            L.mts_rc_reflection.restype = ct.c_int
+            L.mts_rc_reflection.argtypes = [i64, i32, i32, p, p, p, d, i32, i32, p, p]
+            L.mts_rc_reflection_vjp.restype = ct.c_int
+            L.mts_rc_reflection_vjp.argtypes = [i64, i32, i32, p, p, p, d, i32, i32, p, p, p, p]
             L.mts_tape_status.restype = ct.c_int
             L.mts_tape_status.argtypes = [PP, i64, ct.c_int, p, ct.POINTER(ct.c_int64), p]
             _lib = L
@@ -328,3 +363,127 @@ def mts_param_grad(pb, prec, basis, ev: Eval, tape, grad_loss=None, grad_R=None,
                                 tape.numel() * tape.element_size(), _ptr(grad_loss),
                                 _ptr(grad_R), _ptr(grad_L), _ptr(grad_omega), _ptr(grad_V),
                                 _stream(stream)), "mts_param_grad")
+
+
+# ---------------------------------------------------------------------------------------
+# scattering-parameter route
+# ---------------------------------------------------------------------------------------
+class Sparams:
+    """A structure in S-parameter form (mts_sparams): S0 [F, n0, n0], field [F, P, n0],
+    S_C,const [F, n, n] (or None), the (row, col) of each variable entry, loss points."""
+
+    def __init__(self, S0, field, rows, cols, n1: int, sc_const=None, loss_idx=None,
+                 device="cuda"):
+        def dev(a, dt):
+            return torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).to(device)
+
+        def cdev(a):
+            return torch.view_as_real(torch.from_numpy(np.ascontiguousarray(a, np.complex128))).contiguous().to(device)
+        S0 = np.asarray(S0)
+        field = np.asarray(field)
+        self.F, self.n0 = S0.shape[0], S0.shape[1]
+        self.P = field.shape[1]
+        self.h_rows = np.ascontiguousarray(rows, np.int32)
+        self.h_cols = np.ascontiguousarray(cols, np.int32)
+        self.d = {"S0": cdev(S0), "field": cdev(field)}
+        self.n1 = int(n1)
+        if sc_const is not None:
+            self.d["sc_const"] = cdev(sc_const)
+        li = np.zeros(0, np.int64) if loss_idx is None else np.asarray(loss_idx, np.int64)
+        self.d["loss_idx"] = dev(li, np.int64)
+        self.L = len(li)
+        self.nS = len(self.h_rows)
+        c = MtsSparams()
+        c.n0, c.n1, c.n_freq, c.n_points = self.n0, self.n1, self.F, self.P
+        c.n_svar, c.n_loss = self.nS, self.L
+        c.h_svar_row = self.h_rows.ctypes.data
+        c.h_svar_col = self.h_cols.ctypes.data
+        c.S0 = self.d["S0"].data_ptr()
+        c.field = self.d["field"].data_ptr() if self.d["field"].numel() else None
+        c.sc_const = self.d["sc_const"].data_ptr() if "sc_const" in self.d else None
+        c.loss_idx = self.d["loss_idx"].data_ptr() if self.L else None
+        self.c = c
+
+    @property
+    def ref(self):
+        return ct.byref(self.c)
+
+
+class SrouteEval:
+    """Per-call inputs of the route (mts_sroute_eval): svar complex [n_cfg, F, nS] (as a
+    float64 view [..., 2]), target [F, n1, L] (real, or [..., 2] complex) or None."""
+
+    def __init__(self, svar: torch.Tensor, target: Optional[torch.Tensor] = None,
+                 loss_mode: int = MTS_LOSS_ABS, refine_tol: float = 0.0, max_refine: int = 0):
+        self.svar = svar.contiguous()
+        self.target = None if target is None else target.contiguous()
+        e = MtsSrouteEval()
+        e.n_cfg = self.svar.shape[0]
+        e.svar = self.svar.data_ptr() if self.svar.numel() else None
+        e.target = None if self.target is None else self.target.data_ptr()
+        e.loss_mode = int(loss_mode)
+        e.refine_tol = float(refine_tol)
+        e.max_refine = int(max_refine)
+        self.c = e
+
+    @property
+    def n_cfg(self) -> int:
+        return int(self.c.n_cfg)
+
+    @property
+    def ref(self):
+        return ct.byref(self.c)
+
+
+def _nbytes(t):
+    return 0 if t is None else t.numel() * t.element_size()
+
+
+def mts_sroute_basis_bytes(sp: Sparams, prec) -> int:
+    return int(lib().mts_sroute_basis_bytes(sp.ref, _prec(prec)))
+
+
+def mts_sroute_build(sp: Sparams, prec, sbasis: torch.Tensor, stream=None):
+    _check(lib().mts_sroute_build(sp.ref, _prec(prec), _ptr(sbasis), _nbytes(sbasis),
+                                  _stream(stream)), "mts_sroute_build")
+
+
+def mts_sroute_tape_bytes(sp: Sparams, n_cfg: int, prec) -> int:
+    return int(lib().mts_sroute_tape_bytes(sp.ref, int(n_cfg), _prec(prec)))
+
+
+def mts_sroute_forward(sp: Sparams, prec, sbasis, ev: SrouteEval, B_out=None, W_out=None,
+                       loss_out=None, tape=None, stream=None):
+    _check(lib().mts_sroute_forward(sp.ref, _prec(prec), _ptr(sbasis), ev.ref, _ptr(B_out),
+                                    _ptr(W_out), _ptr(loss_out), _ptr(tape), _nbytes(tape),
+                                    _stream(stream)), "mts_sroute_forward")
+
+
+def mts_sroute_backward(sp: Sparams, prec, sbasis, ev: SrouteEval, tape, grad_B=None,
+                        grad_loss=None, grad_svar=None, stream=None):
+    _check(lib().mts_sroute_backward(sp.ref, _prec(prec), _ptr(sbasis), ev.ref, _ptr(tape),
+                                     _nbytes(tape), _ptr(grad_B), _ptr(grad_loss),
+                                     _ptr(grad_svar), _stream(stream)), "mts_sroute_backward")
+
+
+def mts_sroute_status(sp: Sparams, n_cfg: int, prec, tape, stream=None):
+    n_bad = ct.c_int64(0)
+    code = lib().mts_sroute_status(sp.ref, int(n_cfg), _prec(prec), _ptr(tape), ct.byref(n_bad),
+                                   _stream(stream))
+    return int(code), int(n_bad.value)
+
+
+def mts_rc_reflection(n_cfg: int, n_freq: int, n_loads: int, omega, R, C, Z0: float,
+                      svar_stride: int, svar_offset: int, svar, stream=None):
+    _check(lib().mts_rc_reflection(int(n_cfg), int(n_freq), int(n_loads), _ptr(omega), _ptr(R),
+                                   _ptr(C), float(Z0), int(svar_stride), int(svar_offset),
+                                   _ptr(svar), _stream(stream)), "mts_rc_reflection")
+
+
+def mts_rc_reflection_vjp(n_cfg: int, n_freq: int, n_loads: int, omega, R, C, Z0: float,
+                          svar_stride: int, svar_offset: int, grad_svar, grad_R=None, grad_C=None,
+                          stream=None):
+    _check(lib().mts_rc_reflection_vjp(int(n_cfg), int(n_freq), int(n_loads), _ptr(omega),
+                                       _ptr(R), _ptr(C), float(Z0), int(svar_stride),
+                                       int(svar_offset), _ptr(grad_svar), _ptr(grad_R),
+                                       _ptr(grad_C), _stream(stream)), "mts_rc_reflection_vjp")

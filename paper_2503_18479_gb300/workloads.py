@@ -24,6 +24,13 @@ Workloads (all seeded with numpy PCG64):
                   N(0,1) x 1e-6 T; the paper's 2D MTS (Sec. IV-C).
   ragged       -- many independent rectangular arrays with 1..128 ports and 1..16 frequencies.
   array_32x32  -- 32x32 cells (1024 ports), 4 planes of 512x512 points over +-900 mm.
+  sroute_array -- inputs of the scattering-parameter route shaped like the 8x8 array driven
+                  by one excitation loop (n0 = 65 structure ports, one external port): a
+                  reciprocal passive S0 per frequency, per-port fields of z-directed
+                  magnetic-dipole form at the array's points, the drive port fed through
+                  S_C12, and series RC loads (R, C) on the 64 cell ports. These stand in for
+                  a full-wave export; the S-parameters of the loads are computed by the route
+                  itself (Eq. 2-3), not here.
 """
 from __future__ import annotations
 
@@ -391,3 +398,73 @@ def random_cotangent(shape, seed: int = 1) -> np.ndarray:
     """Seeded complex field cotangent dL/dRe B + j dL/dIm B for backward tests."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+@dataclass
+class SrouteWorkload:
+    """Inputs of the scattering-parameter route (one structure)."""
+    name: str
+    S0: np.ndarray        # complex [F, n0, n0]
+    field: np.ndarray     # complex [F, P, n0]
+    sc_const: np.ndarray  # complex [F, n, n], n = n0 + n1
+    rows: np.ndarray      # int32 [nS]: the loads' positions in S_C (diagonal of S11)
+    cols: np.ndarray
+    n1: int
+    omega: np.ndarray     # [F] rad/s
+    R: np.ndarray         # [n_cfg, nS] ohm (series RC loads)
+    C: np.ndarray         # [n_cfg, nS] farad
+    Z0: float
+    loss_idx: np.ndarray  # int64 [L]
+    target: np.ndarray    # real [F, n1, L]
+
+    @property
+    def n_cfg(self) -> int:
+        return self.C.shape[0]
+
+
+def sroute_array(nx: int = 8, ny: int = 8, seed: int = 0, n_cfg: int = 4096, grid: int = 128,
+                 planes=(0.010, 0.020, 0.030, 0.040), freqs_hz=(63.6 * MHZ,), rho=(0.5, 0.99),
+                 Z0: float = 50.0) -> SrouteWorkload:
+    """S-route inputs: nx*ny cell ports plus a drive port (n0 = nx ny + 1), one external port.
+    S0 = Q diag(rho_k e^{j phi_k}) Q^T with Q a random orthogonal matrix and rho_k in `rho`
+    (symmetric: reciprocal; spectral norm < 1: passive). The field of port k is the Bz of a
+    z-directed dipole at the port's cell centre (the drive port's at the array centre, 30 mm
+    below) times a random complex amplitude, about 1e-6 T per unit wave at 40 mm. Loads:
+    R = 0.1 ohm, C ~ U[20, 200] pF; targets |N(0,1)| x 1e-6 T at the 64-style loss points
+    above the cell centres."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n_cells = nx * ny
+    n0, n1 = n_cells + 1, 1
+    omega = 2 * np.pi * np.asarray(freqs_hz, float)
+    F = len(omega)
+    pts = _concat_points(*[grid_plane(grid, 0.250, z) for z in planes],
+                         _cell_centre_points(nx, ny, 0.055, 0.040))
+    px, py, pz = pts
+    n_grid = grid * grid * len(planes)
+    loss_idx = np.arange(n_grid, n_grid + n_cells, dtype=np.int64)
+    cx, cy, _ = _cell_centre_points(nx, ny, 0.055, 0.0)
+    sx = np.append(cx, 0.0)
+    sy = np.append(cy, 0.0)
+    sz = np.append(np.zeros(n_cells), -0.030)
+    dx = px[:, None] - sx[None, :]
+    dy = py[:, None] - sy[None, :]
+    dz = pz[:, None] - sz[None, :]
+    r2 = dx * dx + dy * dy + dz * dz + 1e-4  # 10 mm core
+    dip = (3 * dz * dz - r2) / r2 ** 2.5  # z-dipole Bz shape
+    scale = 1e-6 / (2.0 / 0.040 ** 3)
+    S0 = np.zeros((F, n0, n0), complex)
+    field = np.zeros((F, len(px), n0), complex)
+    for f in range(F):
+        Q, _ = np.linalg.qr(rng.standard_normal((n0, n0)))
+        lam = rng.uniform(rho[0], rho[1], n0) * np.exp(1j * rng.uniform(-np.pi, np.pi, n0))
+        S0[f] = (Q * lam[None, :]) @ Q.T
+        amp = rng.uniform(0.5, 1.5, n0) * np.exp(1j * rng.uniform(-np.pi, np.pi, n0))
+        field[f] = dip * (scale * amp)[None, :]
+    sc_const = np.zeros((F, n0 + n1, n0 + n1), complex)
+    sc_const[:, n0 - 1, n0] = 1.0  # matched source into the drive port
+    rows = np.arange(n_cells, dtype=np.int32)
+    R = np.full((n_cfg, n_cells), 0.1)
+    C = rng.uniform(20 * PF, 200 * PF, size=(n_cfg, n_cells))
+    target = np.abs(rng.standard_normal((F, n1, n_cells))) * 1e-6
+    return SrouteWorkload(f"sroute_{nx}x{ny}", S0, field, sc_const, rows, rows.copy(), n1, omega,
+                          R, C, Z0, loss_idx, target)

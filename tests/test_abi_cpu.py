@@ -227,3 +227,69 @@ def test_schedule_fields_are_validated(nv):
     code = L.mts_solve(ct.byref(c), nv.MTS_MIXED, ct.c_void_p(FAKE), ct.byref(ev), None, None,
                        ct.c_void_p(FAKE), tneed, None)
     assert code == nv.MTS_EINVAL
+
+
+def fake_sparams(nv, n0=4, n1=1, F=2, P=10, rows=(0, 1, 2), cols=(0, 1, 2), n_loss=0):
+    c = nv.MtsSparams()
+    c.n0, c.n1, c.n_freq, c.n_points = n0, n1, F, P
+    keep = (np.ascontiguousarray(rows, np.int32), np.ascontiguousarray(cols, np.int32))
+    c.n_svar = len(keep[0])
+    c.n_loss = n_loss
+    c.h_svar_row = keep[0].ctypes.data
+    c.h_svar_col = keep[1].ctypes.data
+    c.S0 = FAKE
+    c.field = FAKE
+    c.loss_idx = FAKE if n_loss else None
+    return c, keep
+
+
+def test_sroute_validation(nv):
+    """The scattering-parameter route's host checks: sizes, index ranges, duplicate entries,
+    the n0 <= 96 / n1 <= 8 / n_svar <= 1024 limits, and the RC preprocessing's arguments."""
+    L = nv.lib()
+    c, keep = fake_sparams(nv)
+    assert L.mts_sroute_basis_bytes(ct.byref(c), nv.MTS_MIXED) > 0
+    t1 = L.mts_sroute_tape_bytes(ct.byref(c), 10, nv.MTS_MIXED)
+    t2 = L.mts_sroute_tape_bytes(ct.byref(c), 20, nv.MTS_MIXED)
+    assert 0 < t1 < t2
+    assert L.mts_sroute_tape_bytes(ct.byref(c), 10, nv.MTS_FP64) > 0
+    assert L.mts_sroute_tape_bytes(ct.byref(c), -1, nv.MTS_FP64) == 0
+    bad = [dict(rows=(0, 0), cols=(1, 1)),        # duplicate position
+           dict(rows=(0, 5), cols=(0, 0)),        # row outside n0 + n1
+           dict(rows=(0,), cols=(-1,)),
+           dict(n0=0), dict(n1=0), dict(F=0), dict(P=-1)]
+    for kw in bad:
+        cb, kb = fake_sparams(nv, **kw)
+        assert L.mts_sroute_basis_bytes(ct.byref(cb), nv.MTS_MIXED) == 0, kw
+        assert L.mts_sroute_build(ct.byref(cb), nv.MTS_MIXED, ct.c_void_p(FAKE), 1 << 30, None) == nv.MTS_EINVAL, kw
+    for kw in (dict(n0=97), dict(n1=9), dict(rows=tuple(range(1025)), cols=tuple([0] * 1025))):
+        if "rows" in kw:
+            cb, kb = fake_sparams(nv, n0=96, n1=8, rows=[i % 104 for i in range(1025)],
+                                  cols=[i // 104 for i in range(1025)])
+        else:
+            cb, kb = fake_sparams(nv, **kw)
+        assert L.mts_sroute_build(ct.byref(cb), nv.MTS_MIXED, ct.c_void_p(FAKE), 1 << 30, None) == nv.MTS_EUNSUPPORTED, kw
+    # loss points without field points, too small a basis buffer, unaligned buffer
+    cb, kb = fake_sparams(nv, P=0, n_loss=2)
+    assert L.mts_sroute_build(ct.byref(cb), nv.MTS_MIXED, ct.c_void_p(FAKE), 1 << 30, None) == nv.MTS_EINVAL
+    need = L.mts_sroute_basis_bytes(ct.byref(c), nv.MTS_MIXED)
+    assert L.mts_sroute_build(ct.byref(c), nv.MTS_MIXED, ct.c_void_p(FAKE), need - 1, None) == nv.MTS_EWORKSPACE
+    assert L.mts_sroute_build(ct.byref(c), nv.MTS_MIXED, ct.c_void_p(FAKE + 8), need, None) == nv.MTS_EINVAL
+    # per-call inputs
+    ev = nv.MtsSrouteEval()
+    ev.n_cfg, ev.svar, ev.loss_mode = 4, FAKE, 2
+    tb = L.mts_sroute_tape_bytes(ct.byref(c), 4, nv.MTS_MIXED)
+    assert L.mts_sroute_forward(ct.byref(c), nv.MTS_MIXED, ct.c_void_p(FAKE), ct.byref(ev), None, None,
+                                None, ct.c_void_p(FAKE), tb, None) == nv.MTS_EINVAL
+    ev.loss_mode = 0
+    assert L.mts_sroute_forward(ct.byref(c), nv.MTS_MIXED, ct.c_void_p(FAKE), ct.byref(ev), None, None,
+                                ct.c_void_p(FAKE), ct.c_void_p(FAKE), tb, None) == nv.MTS_EINVAL  # loss, no target
+    assert L.mts_sroute_forward(ct.byref(c), nv.MTS_MIXED, ct.c_void_p(FAKE), ct.byref(ev), None, None,
+                                None, ct.c_void_p(FAKE), tb - 1, None) == nv.MTS_EWORKSPACE
+    assert L.mts_sroute_backward(ct.byref(c), nv.MTS_MIXED, ct.c_void_p(FAKE), ct.byref(ev),
+                                 ct.c_void_p(FAKE), tb, None, None, None, None) == nv.MTS_EINVAL
+    # RC preprocessing
+    assert L.mts_rc_reflection(2, 1, 3, FAKE, None, FAKE, 0.0, 3, 0, FAKE, None) == nv.MTS_EINVAL
+    assert L.mts_rc_reflection(2, 1, 3, FAKE, None, FAKE, 50.0, 2, 0, FAKE, None) == nv.MTS_EINVAL
+    assert L.mts_rc_reflection_vjp(2, 1, 3, FAKE, None, FAKE, 50.0, 4, 2, FAKE, None, FAKE, None) == nv.MTS_EINVAL
+    assert nv.mts_launch_count() == 0
