@@ -70,7 +70,7 @@ def parse():
     ap.add_argument("--no-fp64-path", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--n-cfg", type=int, default=N_CFG, help="configurations per GPU (profiling runs)")
-    ap.add_argument("--other-workloads", default="loop,line,fit,fit8x8",
+    ap.add_argument("--other-workloads", default="loop,line,fit,fit8x8,sroute",
                     help="comma list of extra workloads timed after the headline (loop, line, "
                          "ragged, 32x32; empty for none); reported under other_workloads")
     return ap.parse_args()
@@ -392,6 +392,10 @@ def other_workloads(args, dev, prec):
         "fit8x8": ("array_8x8: 4096 independent Adam fits (lr 1e-13) of the 64 capacitances to "
                    "the 64-point target, 200 epochs (solve + objective + adjoint + Adam, no field) "
                    "replayed from one CUDA graph", None),
+        "sroute": ("sroute_8x8: scattering-parameter route, 65 structure ports (64 RC-loaded cells "
+                   "+ a drive port fed through S_C12), 4096 configs, 63.6 MHz, 4x128x128 + 64 "
+                   "points; step = Eq. 2-3 loads, W = (1 - S11 S0)^-1 S12, Bcomb = field W, "
+                   "objective, Eq. 10 adjoint, dL/dC", None),
     }
     res = {}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -403,6 +407,9 @@ def other_workloads(args, dev, prec):
             continue
         if name == "fit8x8":
             res[name] = fit_array(desc, dev, prec)
+            continue
+        if name == "sroute":
+            res[name] = sroute_bench(desc, dev, prec, flush)
             continue
         wl = make()
         if wl.target is None:  # timing only: a zero target costs the same work
@@ -447,6 +454,81 @@ def other_workloads(args, dev, prec):
         del sim, B, tape
         torch.cuda.empty_cache()
     return res
+
+
+def sroute_bench(desc, dev, prec, flush, K=10):
+    """The scattering-parameter route on the synthetic 8x8-plus-drive workload: configs/s of
+    the whole step and the time of its parts (CUDA events, L2 flushed between steps)."""
+    import torch
+
+    from paper_2503_18479_gb300 import native as nv
+    from paper_2503_18479_gb300 import workloads as W
+    from paper_2503_18479_gb300.sroute import SRoute
+    wl = W.sroute_array(seed=0, n_cfg=N_CFG)
+    sr = SRoute(wl.S0, wl.field, wl.rows, wl.cols, wl.n1, sc_const=wl.sc_const,
+                loss_idx=wl.loss_idx, target=wl.target, precision=prec, device=dev)
+    n, F, nS = wl.n_cfg, sr.F, sr.nS
+    R = torch.from_numpy(wl.R).to(dev)
+    C = torch.from_numpy(wl.C).to(dev)
+    om = torch.from_numpy(wl.omega).to(dev)
+    svar = torch.empty((n, F, nS, 2), dtype=torch.float64, device=dev)
+    ev = nv.SrouteEval(svar, sr.target, sr.loss_mode)
+    tape = sr.alloc_tape(n)
+    B = torch.empty((n, sr.n1, F, sr.P), dtype=sr.b_dtype, device=dev)
+    loss = torch.empty(n, dtype=torch.float64, device=dev)
+    gl = torch.ones(n, dtype=torch.float64, device=dev)
+    gs = torch.empty((n, F, nS, 2), dtype=torch.float64, device=dev)
+    gC = torch.empty((n, nS), dtype=torch.float64, device=dev)
+    st = torch.cuda.current_stream()
+    ev_ = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+
+    def step(marks=False):
+        if marks:
+            ev_[0].record(st)
+        nv.mts_rc_reflection(n, F, nS, om, R, C, wl.Z0, nS, 0, svar)
+        nv.mts_sroute_forward(sr.sp, sr.prec, sr.sbasis, ev, B_out=None, loss_out=loss, tape=tape)
+        if marks:
+            ev_[1].record(st)
+        nv.mts_sroute_backward(sr.sp, sr.prec, sr.sbasis, ev, tape, grad_loss=gl, grad_svar=gs)
+        nv.mts_rc_reflection_vjp(n, F, nS, om, R, C, wl.Z0, nS, 0, gs, grad_C=gC)
+        if marks:
+            ev_[2].record(st)
+
+    def full_step():
+        nv.mts_rc_reflection(n, F, nS, om, R, C, wl.Z0, nS, 0, svar)
+        nv.mts_sroute_forward(sr.sp, sr.prec, sr.sbasis, ev, B_out=B, loss_out=loss, tape=tape)
+        nv.mts_sroute_backward(sr.sp, sr.prec, sr.sbasis, ev, tape, grad_loss=gl, grad_svar=gs)
+        nv.mts_rc_reflection_vjp(n, F, nS, om, R, C, wl.Z0, nS, 0, gs, grad_C=gC)
+
+    for _ in range(3):
+        flush.fill_(1)
+        full_step()
+    torch.cuda.synchronize()
+    code, bad = sr.status(tape, n)
+    ms = ms_nob = ms_fwd = 0.0
+    for _ in range(K):
+        flush.fill_(1)
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(st)
+        full_step()
+        a1.record(st)
+        a1.synchronize()
+        ms += a0.elapsed_time(a1)
+        flush.fill_(1)
+        step(marks=True)
+        ev_[2].synchronize()
+        ms_fwd += ev_[0].elapsed_time(ev_[1])
+        ms_nob += ev_[0].elapsed_time(ev_[2])
+    ms, ms_nob, ms_fwd = ms / K, ms_nob / K, ms_fwd / K
+    out = {"workload": desc, "precision": prec, "ms_per_step": ms,
+           "configs_per_s": n / (ms / 1e3), "field_points_per_s": n * sr.n1 * F * sr.P / (ms / 1e3),
+           "ms_loads_solve_objective": ms_fwd, "ms_adjoint_and_vjp": ms_nob - ms_fwd,
+           "ms_superposition": ms - ms_nob, "steps": K,
+           "status": {"code": code, "systems_flagged": bad}}
+    del sr, B, tape
+    torch.cuda.empty_cache()
+    return out
 
 
 def fit_sweep(desc, dev, prec, epochs=200):

@@ -122,3 +122,33 @@ def test_array_32x32_full():
     assert rel(Bg, Iref @ Hs.T) < 5e-6, rel(Bg, Iref @ Hs.T)
     assert rel(loss[idx, 0].cpu().numpy(), ref["loss"]) < 1e-6
     assert rel(g[idx].cpu().numpy(), gref) < 1e-6
+
+
+def test_sroute_array_full():
+    """The scattering-parameter route on the 8x8-plus-drive workload at the bench's size
+    (4096 configurations, 65,600 points, 65 structure ports, MTS_MIXED): 8 configurations
+    checked in full (Bcomb, objective, dL/dC through Eq. 3)."""
+    from paper_2503_18479_gb300.sroute import SRoute, rc_reflection
+    wl = W.sroute_array(seed=0)
+    sr = SRoute(wl.S0, wl.field, wl.rows, wl.cols, wl.n1, sc_const=wl.sc_const,
+                loss_idx=wl.loss_idx, target=wl.target, precision="mixed")
+    C = torch.from_numpy(wl.C).cuda().requires_grad_(True)
+    gam = rc_reflection(torch.from_numpy(wl.R).cuda(), C, torch.from_numpy(wl.omega).cuda(), wl.Z0)
+    B, loss = sr(gam)
+    loss.sum().backward()
+    torch.cuda.synchronize()
+    rng = np.random.Generator(np.random.PCG64(6))
+    cfg = np.sort(rng.choice(wl.n_cfg, size=8, replace=False))
+    w = wl.omega[None, :, None]
+    Zl = wl.R[cfg][:, None, :] - 1j / (w * wl.C[cfg][:, None, :])
+    svar = (Zl - wl.Z0) / (Zl + wl.Z0)  # Eq. 3
+    ref = oracle.sroute_pipeline(wl.S0, wl.field, wl.sc_const, wl.rows, wl.cols, svar,
+                                 wl.loss_idx, wl.target)
+    idx = torch.from_numpy(cfg).cuda()
+    assert rel(B.detach()[idx].cpu().numpy(), ref["B"]) < 1e-6
+    assert rel(loss.detach()[idx].cpu().numpy(), ref["loss"]) < 1e-6
+    g = oracle.sroute_gradient(wl.S0, wl.field, wl.sc_const, wl.rows, wl.cols, svar,
+                               wl.loss_idx, wl.target)
+    dgam = 2 * wl.Z0 / (Zl + wl.Z0) ** 2 * (1j / (w * wl.C[cfg][:, None, :] ** 2))
+    gC = np.real(np.conj(g) * dgam).sum(axis=1)
+    assert rel(C.grad[idx].cpu().numpy(), gC) < 1e-6
