@@ -66,6 +66,12 @@ def _load():
             lib.oracle_forward.restype = ct.c_int
             lib.oracle_forward.argtypes = [i32, i64, p, p, p, i64, p, i32, p, p, i32, p, p, i32,
                                            i32, p, p, p]
+            lib.oracle_forward_w.restype = ct.c_int
+            lib.oracle_forward_w.argtypes = [i32, i64, p, p, p, i64, p, i32, p, p, i32, p, p, i32,
+                                             i32, p, p, p, p, p]
+            lib.oracle_gradient_adjoint_w.restype = ct.c_int
+            lib.oracle_gradient_adjoint_w.argtypes = [i32, i64, p, p, p, i64, p, i32, p, p, i32,
+                                                      p, p, i32, i32, p, p, p]
             lib.oracle_gradient_adjoint.restype = ct.c_int
             lib.oracle_gradient_adjoint.argtypes = [i32, i64, p, p, p, i64, p, i32, p, p, i32, p,
                                                     p, i32, i32, p]
@@ -214,8 +220,11 @@ def _target_arr(target, mode):
 
 
 def forward(H, M, R, C, omega, V, loss_idx=None, target=None, mode: int = 0,
-            target_per_cfg: bool = False, want_B: bool = True, want_loss: bool = True):
-    """Forward map of one structure: returns dict with I [n_cfg,F,N], B [n_cfg,F,P], loss."""
+            target_per_cfg: bool = False, want_B: bool = True, want_loss: bool = True,
+            weight=None, offset=None):
+    """Forward map of one structure: returns dict with I [n_cfg,F,N], B [n_cfg,F,P], loss.
+    weight [F, L] real and offset [F, L] complex (optional) turn the objective term of a loss
+    point into that of weight * (B + offset) (the enhancement objective of Sec. IV-B)."""
     H, M, R, C, omega = _f64(H), _f64(M), _f64(R), _f64(np.atleast_2d(C)), _f64(np.atleast_1d(omega))
     V = _c128(np.atleast_2d(V))
     P, N = H.shape
@@ -227,14 +236,18 @@ def forward(H, M, R, C, omega, V, loss_idx=None, target=None, mode: int = 0,
     do_loss = want_loss and L > 0
     t = _target_arr(np.asarray(target), mode) if do_loss else np.zeros(1)
     loss = np.zeros(n_cfg) if do_loss else None
-    bad = _load().oracle_forward(N, P, _ptr(H), _ptr(M), _ptr(R), n_cfg, _ptr(C), F, _ptr(omega),
-                                 _ptr(V), L, _ptr(li), _ptr(t), int(target_per_cfg), int(mode),
-                                 _ptr(Iout), _ptr(Bout), _ptr(loss))
+    w = None if weight is None else _f64(weight)
+    o = None if offset is None else _c128(offset)
+    bad = _load().oracle_forward_w(N, P, _ptr(H), _ptr(M), _ptr(R), n_cfg, _ptr(C), F,
+                                   _ptr(omega), _ptr(V), L, _ptr(li), _ptr(t),
+                                   int(target_per_cfg), int(mode), _ptr(w), _ptr(o), _ptr(Iout),
+                                   _ptr(Bout), _ptr(loss))
     return {"I": Iout, "B": Bout, "loss": loss, "n_singular": int(bad)}
 
 
-def gradient(H, M, R, C, omega, V, loss_idx, target, mode: int = 0, target_per_cfg: bool = False):
-    """d loss / d C (adjoint form), shape [n_cfg, N]."""
+def gradient(H, M, R, C, omega, V, loss_idx, target, mode: int = 0, target_per_cfg: bool = False,
+             weight=None, offset=None):
+    """d loss / d C (adjoint form), shape [n_cfg, N]; weight/offset as in forward()."""
     H, M, R, C, omega = _f64(H), _f64(M), _f64(R), _f64(np.atleast_2d(C)), _f64(np.atleast_1d(omega))
     V = _c128(np.atleast_2d(V))
     P, N = H.shape
@@ -242,9 +255,11 @@ def gradient(H, M, R, C, omega, V, loss_idx, target, mode: int = 0, target_per_c
     li = _i64(loss_idx)
     t = _target_arr(np.asarray(target), mode)
     g = np.zeros((n_cfg, N))
-    _load().oracle_gradient_adjoint(N, P, _ptr(H), _ptr(M), _ptr(R), n_cfg, _ptr(C), F,
-                                    _ptr(omega), _ptr(V), len(li), _ptr(li), _ptr(t),
-                                    int(target_per_cfg), int(mode), _ptr(g))
+    w = None if weight is None else _f64(weight)
+    o = None if offset is None else _c128(offset)
+    _load().oracle_gradient_adjoint_w(N, P, _ptr(H), _ptr(M), _ptr(R), n_cfg, _ptr(C), F,
+                                      _ptr(omega), _ptr(V), len(li), _ptr(li), _ptr(t),
+                                      int(target_per_cfg), int(mode), _ptr(w), _ptr(o), _ptr(g))
     return g
 
 

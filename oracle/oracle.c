@@ -462,6 +462,23 @@ static double oracle_point_loss(int mode, double complex b, const double* t, dou
   return creal(e) * creal(e) + cimag(e) * cimag(e);
 }
 
+/* Objective term of one loss point with an optional weight w and complex offset o
+ * (NULL: 1 and 0), evaluated on w (b + o). This is the signal-enhancement objective of
+ * Sec. IV-B: the enhancement at a point is beta = |B_MTS| / |B_ref|, the field with the
+ * structure (its induced field b plus the C-independent incident field o) over the field of a
+ * reference run without it, so (beta - beta_target)^2 is the magnitude term of w (b + o) with
+ * w = 1/|B_ref| and target beta_target. G, the derivative with respect to b, is w times the
+ * derivative with respect to w (b + o). */
+static double oracle_objective_term(int mode, double complex b, const double* t,
+                                    const double* weight, const double complex* offset,
+                                    int64_t i, double complex* G) {
+  const double w = weight ? weight[i] : 1.0;
+  const double complex bb = (offset ? b + offset[i] : b) * w;
+  const double e = oracle_point_loss(mode, bb, t, G);
+  *G *= w;
+  return e;
+}
+
 /* ------------------------------------------------------------------------------------
  * Forward map of one structure for a batch of configurations (Eq. 2, 6-7, 11, 1).
  *   N loops, P points, H[P][N], M[N][N], R[N]
@@ -474,11 +491,12 @@ static double oracle_point_loss(int mode, double complex b, const double* t, dou
  * Configurations are independent; the loop over them may run in parallel threads.
  * Returns the number of singular systems.
  * ------------------------------------------------------------------------------------ */
-int oracle_forward(int32_t N, int64_t P, const double* H, const double* M, const double* R,
-                   int64_t n_cfg, const double* C, int32_t F, const double* omega,
-                   const double complex* V, int32_t L, const int64_t* loss_idx,
-                   const double* target, int32_t target_per_cfg, int32_t mode,
-                   double complex* I_out, double complex* B_out, double* loss_out) {
+int oracle_forward_w(int32_t N, int64_t P, const double* H, const double* M, const double* R,
+                     int64_t n_cfg, const double* C, int32_t F, const double* omega,
+                     const double complex* V, int32_t L, const int64_t* loss_idx,
+                     const double* target, int32_t target_per_cfg, int32_t mode,
+                     const double* weight, const double complex* offset,
+                     double complex* I_out, double complex* B_out, double* loss_out) {
   int n_bad = 0;
   const int64_t tw = (mode == 0) ? 1 : 2;
 #pragma omp parallel for schedule(static) reduction(+ : n_bad)
@@ -508,7 +526,8 @@ int oracle_forward(int32_t N, int64_t P, const double* H, const double* M, const
         for (int32_t l = 0; l < L; ++l) {
           double complex s = 0.0, G;
           for (int32_t k = 0; k < N; ++k) s += H[loss_idx[l] * N + k] * x[k];
-          acc += oracle_point_loss(mode, s, t + ((int64_t)f * L + l) * tw, &G);
+          acc += oracle_objective_term(mode, s, t + ((int64_t)f * L + l) * tw, weight, offset,
+                                       (int64_t)f * L + l, &G);
         }
       }
     }
@@ -518,6 +537,15 @@ int oracle_forward(int32_t N, int64_t P, const double* H, const double* M, const
     free(x);
   }
   return n_bad;
+}
+
+int oracle_forward(int32_t N, int64_t P, const double* H, const double* M, const double* R,
+                   int64_t n_cfg, const double* C, int32_t F, const double* omega,
+                   const double complex* V, int32_t L, const int64_t* loss_idx,
+                   const double* target, int32_t target_per_cfg, int32_t mode,
+                   double complex* I_out, double complex* B_out, double* loss_out) {
+  return oracle_forward_w(N, P, H, M, R, n_cfg, C, F, omega, V, L, loss_idx, target,
+                          target_per_cfg, mode, NULL, NULL, I_out, B_out, loss_out);
 }
 
 /* ------------------------------------------------------------------------------------
@@ -530,11 +558,12 @@ int oracle_forward(int32_t N, int64_t P, const double* H, const double* M, const
  * summed over frequencies and divided by the same F*L as the loss.
  * Writes grad_out[b][N]. Returns the number of singular systems.
  * ------------------------------------------------------------------------------------ */
-int oracle_gradient_adjoint(int32_t N, int64_t P, const double* H, const double* M,
-                            const double* R, int64_t n_cfg, const double* C, int32_t F,
-                            const double* omega, const double complex* V, int32_t L,
-                            const int64_t* loss_idx, const double* target,
-                            int32_t target_per_cfg, int32_t mode, double* grad_out) {
+int oracle_gradient_adjoint_w(int32_t N, int64_t P, const double* H, const double* M,
+                              const double* R, int64_t n_cfg, const double* C, int32_t F,
+                              const double* omega, const double complex* V, int32_t L,
+                              const int64_t* loss_idx, const double* target,
+                              int32_t target_per_cfg, int32_t mode, const double* weight,
+                              const double complex* offset, double* grad_out) {
   (void)P;
   int n_bad = 0;
   const int64_t tw = (mode == 0) ? 1 : 2;
@@ -559,7 +588,8 @@ int oracle_gradient_adjoint(int32_t N, int64_t P, const double* H, const double*
       for (int32_t l = 0; l < L; ++l) {
         double complex s = 0.0, G;
         for (int32_t k = 0; k < N; ++k) s += H[loss_idx[l] * N + k] * x[k];
-        oracle_point_loss(mode, s, t + ((int64_t)f * L + l) * tw, &G);
+        oracle_objective_term(mode, s, t + ((int64_t)f * L + l) * tw, weight, offset,
+                              (int64_t)f * L + l, &G);
         for (int32_t k = 0; k < N; ++k) mu[k] += H[loss_idx[l] * N + k] * conj(G);
       }
       oracle_lu_solve(N, A, piv, mu); /* A^T = A */
@@ -574,6 +604,15 @@ int oracle_gradient_adjoint(int32_t N, int64_t P, const double* H, const double*
     free(mu);
   }
   return n_bad;
+}
+
+int oracle_gradient_adjoint(int32_t N, int64_t P, const double* H, const double* M,
+                            const double* R, int64_t n_cfg, const double* C, int32_t F,
+                            const double* omega, const double complex* V, int32_t L,
+                            const int64_t* loss_idx, const double* target,
+                            int32_t target_per_cfg, int32_t mode, double* grad_out) {
+  return oracle_gradient_adjoint_w(N, P, H, M, R, n_cfg, C, F, omega, V, L, loss_idx, target,
+                                   target_per_cfg, mode, NULL, NULL, grad_out);
 }
 
 /* Gradients of the same objective with respect to the loop resistances R_k and the self

@@ -602,6 +602,58 @@ def _grad_case(mode=0, n=6, F=3, n_cfg=2, seed=11):
     return H, M, R, C, omega, V, li, t
 
 
+def _beta_inputs(H, li, F, seed=21):
+    rng = np.random.default_rng(seed)
+    L = len(li)
+    Bref = (rng.uniform(0.5, 1.5, (F, L)) * 3e-7) * np.exp(1j * rng.uniform(-np.pi, np.pi, (F, L)))
+    Binc = (rng.standard_normal((F, L)) + 1j * rng.standard_normal((F, L))) * 2e-7
+    beta_t = rng.uniform(0.5, 2.5, (F, L))
+    return Bref, Binc, beta_t
+
+
+def test_enhancement_objective_definition():
+    """Sec. IV-B: the enhancement beta = |B + B_inc| / |B_ref| at each loss point; the
+    weighted objective (weight 1/|B_ref|, offset B_inc, target beta_t) equals the mean of
+    (beta - beta_t)^2 computed here from the oracle's own field B."""
+    H, M, R, C, omega, V, li, _ = _grad_case(0)
+    F = len(omega)
+    Bref, Binc, bt = _beta_inputs(H, li, F)
+    out = oracle.forward(H, M, R, C, omega, V, li, bt, weight=1 / np.abs(Bref), offset=Binc)
+    B = out["B"][:, :, li]  # [n_cfg, F, L]
+    beta = np.abs(B + Binc[None]) / np.abs(Bref)[None]
+    want = ((beta - bt[None]) ** 2).mean(axis=(1, 2))
+    assert _rel(out["loss"], want) < 1e-13
+    # weight 1 and offset 0 reproduce the plain objective
+    plain = oracle.forward(H, M, R, C, omega, V, li, bt * 1e-7)["loss"]
+    same = oracle.forward(H, M, R, C, omega, V, li, bt * 1e-7, weight=np.ones((F, len(li))),
+                          offset=np.zeros((F, len(li)), complex))["loss"]
+    assert np.array_equal(plain, same)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_enhancement_gradient_central_differences(mode):
+    """The adjoint gradient of the weighted, offset objective against central differences."""
+    H, M, R, C, omega, V, li, t = _grad_case(mode)
+    F = len(omega)
+    Bref, Binc, bt = _beta_inputs(H, li, F)
+    w = 1 / np.abs(Bref)
+    tt = bt if mode == 0 else np.stack([bt, -bt], axis=-1)
+    g = oracle.gradient(H, M, R, C, omega, V, li, tt, mode=mode, weight=w, offset=Binc)
+
+    def cd(h):
+        fd = np.zeros_like(g)
+        for k in range(C.shape[1]):
+            Cp, Cm = C.copy(), C.copy()
+            Cp[:, k] += h
+            Cm[:, k] -= h
+            kw = dict(mode=mode, want_B=False, weight=w, offset=Binc)
+            fd[:, k] = (oracle.forward(H, M, R, Cp, omega, V, li, tt, **kw)["loss"]
+                        - oracle.forward(H, M, R, Cm, omega, V, li, tt, **kw)["loss"]) / (2 * h)
+        return fd
+    f1, f2 = cd(1e-15), cd(0.5e-15)  # Richardson, as in test_gradient_central_differences
+    assert _rel(g, (4 * f2 - f1) / 3) < 1e-6
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 def test_gradient_central_differences(mode):
     """Adjoint gradient versus central differences of the oracle loss, h = 1e-3 pF."""
