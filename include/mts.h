@@ -147,6 +147,12 @@ typedef struct mts_problem {
  *                 tensor cores. Memory does not depend on it.
  *   large_threads threads per system of the blocked solve for N > 64: 128 or 256; 0 selects
  *                 128 for N <= 128 and 256 above. Other values give MTS_EINVAL.
+ * Enhancement objective (Sec. IV-B: beta = |B_MTS| / |B_ref|, the field with the structure
+ * over that of a reference run without it): with loss_weight w and loss_offset o (layout of
+ * the target without its configuration blocks; either may be NULL) the objective term of a
+ * loss point is evaluated on w (B + o) instead of B, and every gradient follows. With
+ * w = 1/|B_ref|, o = the incident field and target = beta_target the objective is the mean of
+ * (beta - beta_target)^2.
  */
 typedef struct mts_eval {
   int64_t n_cfg;
@@ -160,6 +166,8 @@ typedef struct mts_eval {
   int32_t max_refine;
   int32_t simt_max_sys;
   int32_t large_threads;
+  const double* loss_weight; /* device [FL] real, or NULL (1) */
+  const double* loss_offset; /* device complex [FL], or NULL (0) */
 } mts_eval;
 
 /* Human-readable name of a status code (static string). */
@@ -376,7 +384,10 @@ typedef struct mts_sparams {
  *   svar    device complex [n_cfg][n_freq][n_svar]
  *   target  device [n_freq][n1][n_loss], real (MTS_LOSS_ABS) or complex (MTS_LOSS_COMPLEX);
  *           NULL = no objective
- *   refine_tol, max_refine as in mts_eval (0 selects 1e-8 and 8). */
+ *   refine_tol, max_refine as in mts_eval (0 selects 1e-8 and 8).
+ *   loss_weight device [n_freq][n1][n_loss] real, loss_offset device complex, same layout
+ *           (either NULL): the objective term of a loss point is taken on w (Bcomb + o), as
+ *           in mts_eval (the enhancement objective of Sec. IV-B with w = 1/|B_ref|). */
 typedef struct mts_sroute_eval {
   int64_t n_cfg;
   const double* svar;
@@ -384,6 +395,8 @@ typedef struct mts_sroute_eval {
   int32_t loss_mode; /* mts_loss_mode */
   double refine_tol;
   int32_t max_refine;
+  const double* loss_weight;
+  const double* loss_offset;
 } mts_sroute_eval;
 
 /* Basis of the route: the field as superposition operands, T[f] = S_C,const11 S0[f] (the

@@ -91,7 +91,7 @@ def _load():
             lib.oracle_dcurrents_dC.argtypes = [i32, p, p, d, p, p, p]
             lib.oracle_sroute.restype = ct.c_int
             lib.oracle_sroute.argtypes = [i32, p, p, i32, d, d, d, p, p, p]
-            sr = [i32, i32, i32, i64, i32, p, p, p, p, p, i64, p, i32, p, p, i32]
+            sr = [i32, i32, i32, i64, i32, p, p, p, p, p, i64, p, i32, p, p, i32, p, p]
             lib.oracle_sroute_forward.restype = ct.c_int
             lib.oracle_sroute_forward.argtypes = sr + [p, p, p]
             lib.oracle_sroute_gradient.restype = ct.c_int
@@ -330,10 +330,12 @@ def sroute(Z, Zload, drive: int, Z0: float, P_in: float, omega: float, C=None, w
 
 
 def sroute_pipeline(S0, field, Sconst, rows, cols, svar, loss_idx=None, target=None,
-                    mode: int = 0, want_B: bool = True, want_loss: bool = True):
+                    mode: int = 0, want_B: bool = True, want_loss: bool = True, weight=None,
+                    offset=None):
     """The S-parameter pipeline (Sec. III-A, Eq. 3-7) for a batch of variable S-parameters.
     S0 [F, n0, n0], field [F, P, n0], Sconst [F, n, n] (n = n0 + n1), svar [n_batch, F, nS],
     rows/cols [nS], target [F, n1, L] (real, or complex for mode 1).
+    weight [F, n1, L] real / offset [F, n1, L] complex: objective on weight * (B + offset).
     Returns dict W [n_batch, F, n0, n1], B [n_batch, n1, F, P], loss [n_batch], n_singular."""
     S0, field, Sconst, svar = _c128(S0), _c128(field), _c128(Sconst), _c128(svar)
     F, n0 = S0.shape[0], S0.shape[1]
@@ -349,12 +351,15 @@ def sroute_pipeline(S0, field, Sconst, rows, cols, svar, loss_idx=None, target=N
     loss = np.zeros(n_batch) if do_loss else None
     bad = _load().oracle_sroute_forward(n0, n1, F, P, nS, _ptr(_i32(rows)), _ptr(_i32(cols)),
                                         _ptr(S0), _ptr(field), _ptr(Sconst), n_batch, _ptr(svar),
-                                        L, _ptr(li), _ptr(t), int(mode), _ptr(W), _ptr(B),
-                                        _ptr(loss))
+                                        L, _ptr(li), _ptr(t), int(mode),
+                                        _ptr(None if weight is None else _f64(weight)),
+                                        _ptr(None if offset is None else _c128(offset)), _ptr(W),
+                                        _ptr(B), _ptr(loss))
     return {"W": W, "B": B, "loss": loss, "n_singular": int(bad)}
 
 
-def sroute_gradient(S0, field, Sconst, rows, cols, svar, loss_idx, target, mode: int = 0):
+def sroute_gradient(S0, field, Sconst, rows, cols, svar, loss_idx, target, mode: int = 0,
+                    weight=None, offset=None):
     """d objective / d svar (Eq. 10, forward mode), torch's convention, [n_batch, F, nS]."""
     S0, field, Sconst, svar = _c128(S0), _c128(field), _c128(Sconst), _c128(svar)
     F, n0 = S0.shape[0], S0.shape[1]
@@ -367,6 +372,8 @@ def sroute_gradient(S0, field, Sconst, rows, cols, svar, loss_idx, target, mode:
     bad = _load().oracle_sroute_gradient(n0, n1, F, P, nS, _ptr(_i32(rows)), _ptr(_i32(cols)),
                                          _ptr(S0), _ptr(field), _ptr(Sconst), n_batch,
                                          _ptr(svar), len(li), _ptr(li), _ptr(t), int(mode),
+                                         _ptr(None if weight is None else _f64(weight)),
+                                         _ptr(None if offset is None else _c128(offset)),
                                          _ptr(g))
     assert bad == 0, bad
     return g

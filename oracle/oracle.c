@@ -900,7 +900,8 @@ done:
  *   A = 1 - S11 S0;  W = A^-1 S12  (the wave ratio V+res / V-exc, n0 x n1)
  *   Bcomb[b][c][f][p] = sum_k field[f][p][k] W[k][c]
  * Objective: the point loss of oracle_point_loss on Bcomb at the loss points, target
- * [f][c][l] (mode 0 real, mode 1 complex), mean over (f, c, l).
+ * [f][c][l] (mode 0 real, mode 1 complex), mean over (f, c, l); optional weight and offset
+ * [f][c][l] as in oracle_objective_term (the enhancement objective of Sec. IV-B).
  * ------------------------------------------------------------------------------------ */
 static void oracle_sroute_assemble(int32_t n0, int32_t n1, int32_t nS, const int32_t* rows,
                                    const int32_t* cols, const double complex* S0,
@@ -934,6 +935,7 @@ int oracle_sroute_forward(int32_t n0, int32_t n1, int32_t F, int64_t P, int32_t 
                           const double complex* field, const double complex* Sconst,
                           int64_t n_batch, const double complex* svar, int32_t L,
                           const int64_t* loss_idx, const double* target, int32_t mode,
+                          const double* weight, const double complex* offset,
                           double complex* W_out, double complex* B_out, double* loss_out) {
   const int32_t n = n0 + n1;
   const int64_t tw = (mode == 0) ? 1 : 2;
@@ -967,7 +969,8 @@ int oracle_sroute_forward(int32_t n0, int32_t n1, int32_t F, int64_t P, int32_t 
           for (int32_t l = 0; l < L; ++l) {
             double complex s = 0.0, G;
             for (int32_t k = 0; k < n0; ++k) s += fd[loss_idx[l] * n0 + k] * W[k * n1 + c];
-            acc += oracle_point_loss(mode, s, target + (((int64_t)f * n1 + c) * L + l) * tw, &G);
+            const int64_t i = ((int64_t)f * n1 + c) * L + l;
+            acc += oracle_objective_term(mode, s, target + i * tw, weight, offset, i, &G);
           }
       }
     }
@@ -996,6 +999,7 @@ int oracle_sroute_gradient(int32_t n0, int32_t n1, int32_t F, int64_t P, int32_t
                            const double complex* field, const double complex* Sconst,
                            int64_t n_batch, const double complex* svar, int32_t L,
                            const int64_t* loss_idx, const double* target, int32_t mode,
+                           const double* weight, const double complex* offset,
                            double complex* grad_out) {
   const int32_t n = n0 + n1;
   const int64_t tw = (mode == 0) ? 1 : 2;
@@ -1027,7 +1031,8 @@ int oracle_sroute_gradient(int32_t n0, int32_t n1, int32_t F, int64_t P, int32_t
         for (int32_t l = 0; l < L; ++l) {
           double complex s = 0.0;
           for (int32_t k = 0; k < n0; ++k) s += fd[loss_idx[l] * n0 + k] * W[k * n1 + c];
-          oracle_point_loss(mode, s, target + (((int64_t)f * n1 + c) * L + l) * tw, &G[c * L + l]);
+          const int64_t i = ((int64_t)f * n1 + c) * L + l;
+          oracle_objective_term(mode, s, target + i * tw, weight, offset, i, &G[c * L + l]);
         }
       for (int32_t k = 0; k < n0; ++k) /* S0 W */
         for (int32_t c = 0; c < n1; ++c) {

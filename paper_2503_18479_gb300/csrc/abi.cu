@@ -232,6 +232,8 @@ static SolveArgs solve_args(const mts_problem* pb, mts_precision prec, const voi
   a.target = ev->target;
   a.target_per_cfg = ev->target_per_cfg;
   a.loss_mode = ev->loss_mode;
+  a.loss_weight = ev->loss_weight;
+  a.loss_offset = ev->loss_offset;
   a.tol = ev->refine_tol > 0.0 ? ev->refine_tol : 1e-8;
   a.max_refine = ev->max_refine > 0 ? ev->max_refine : 8;
   a.sumFN = ps.sumFN;

@@ -27,6 +27,8 @@ struct SolveArgs {
   const double* target;
   int target_per_cfg;
   int loss_mode;
+  const double* loss_weight;  // [sumFL] or nullptr
+  const double* loss_offset;  // complex [sumFL] or nullptr
   double tol;
   int max_refine;
   int64_t sumFN, sumFL;

@@ -165,6 +165,7 @@ __global__ void __launch_bounds__(NM >= 128 ? NM : 128) solve_fp64_kernel(SolveA
     const int tw = a.loss_mode == 0 ? 1 : 2;
     const double* tb = a.target + (a.target_per_cfg ? si.b * a.sumFL * tw : 0) +
                        (a.t.fl_off[si.s] + (int64_t)si.f * L) * tw;
+    const int64_t wo = a.t.fl_off[si.s] + (int64_t)si.f * L;  // weight / offset base
     for (int c0 = 0; c0 < a.max_loss; c0 += NM) {
       int l = c0 + r;
       cd Gl = {0.0, 0.0};
@@ -175,7 +176,19 @@ __global__ void __launch_bounds__(NM >= 128 ? NM : 128) solve_fp64_kernel(SolveA
           bl.x += h * xs[k].x;
           bl.y += h * xs[k].y;
         }
+        double wl = 1.0;
+        if (a.loss_offset) {
+          bl.x += a.loss_offset[2 * (wo + l)];
+          bl.y += a.loss_offset[2 * (wo + l) + 1];
+        }
+        if (a.loss_weight) {
+          wl = a.loss_weight[wo + l];
+          bl.x *= wl;
+          bl.y *= wl;
+        }
         lsum += point_loss(a.loss_mode, bl, tb + (int64_t)l * tw, &Gl);
+        Gl.x *= wl;
+        Gl.y *= wl;
       }
       Gs[r] = Gl;
       __syncthreads();

@@ -486,6 +486,7 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
       const int tw = a.loss_mode == 0 ? 1 : 2;
       const double* tb = a.target + (a.target_per_cfg ? si.b * a.sumFL * tw : 0) +
                          (a.t.fl_off[si.s] + (int64_t)si.f * Ls) * tw;
+      const int64_t wo = a.t.fl_off[si.s] + (int64_t)si.f * Ls;  // weight / offset base
       cd* Gs = reinterpret_cast<cd*>(dsm + L.pan);  // the panel is free after the LU
       double lsum = 0.0;
       for (int r = tid; r < N; r += T) rhs[r] = {0.0, 0.0};
@@ -500,7 +501,19 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
             bx = fma(h, xc[k].x, bx);
             by = fma(h, xc[k].y, by);
           }
+          double wl = 1.0;
+          if (a.loss_offset) {
+            bx += a.loss_offset[2 * (wo + l)];
+            by += a.loss_offset[2 * (wo + l) + 1];
+          }
+          if (a.loss_weight) {
+            wl = a.loss_weight[wo + l];
+            bx *= wl;
+            by *= wl;
+          }
           lsum += point_loss(a.loss_mode, cd{bx, by}, tb + (int64_t)l * tw, &Gl);
+          Gl.x *= wl;
+          Gl.y *= wl;
         }
         Gs[tid] = {Gl.x, -Gl.y};  // conj(G)
         __syncthreads();

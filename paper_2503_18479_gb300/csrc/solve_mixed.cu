@@ -643,6 +643,7 @@ __global__ void __launch_bounds__(NM >= 64 ? NM : 128, NM >= 64 ? 5 : 1) solve_m
         const int tw = a.loss_mode == 0 ? 1 : 2;
         const double* tb = a.target + (a.target_per_cfg ? si.b * a.sumFL * tw : 0) +
                            (a.t.fl_off[si.s] + (int64_t)si.f * L) * tw;
+        const int64_t wo = a.t.fl_off[si.s] + (int64_t)si.f * L;  // weight / offset base
         double lsum = 0.0;
         u64 U = 0ull;
         for (int c0 = 0; c0 < a.max_loss; c0 += NM) {
@@ -660,10 +661,20 @@ __global__ void __launch_bounds__(NM >= 64 ? NM : 128, NM >= 64 ? 5 : 1) solve_m
               const float h0 = Hl[(int64_t)l * N + k];
               b0 = ffma2(pk(h0, h0), sm.xhl[k].x, b0);
             }
-            const float2 bl = make_float2(up(b0).x + up(b1).x, up(b0).y + up(b1).y);
+            float2 bl = make_float2(up(b0).x + up(b1).x, up(b0).y + up(b1).y);
+            float wl = 1.0f;
+            if (a.loss_offset) {
+              bl.x += (float)a.loss_offset[2 * (wo + l)];
+              bl.y += (float)a.loss_offset[2 * (wo + l) + 1];
+            }
+            if (a.loss_weight) {
+              wl = (float)a.loss_weight[wo + l];
+              bl.x *= wl;
+              bl.y *= wl;
+            }
             float gx, gy;
             lsum += (double)point_loss_f(a.loss_mode, bl, tb + (int64_t)l * tw, &gx, &gy);
-            Gl = {(double)gx, (double)gy};
+            Gl = {(double)(gx * wl), (double)(gy * wl)};
           }
           sm.Gs[r] = make_float2((float)Gl.x, -(float)Gl.y);  // conj(G)
           gsync<NM>();

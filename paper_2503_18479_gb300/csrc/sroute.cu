@@ -277,6 +277,8 @@ struct SrArgs {
   const double2* field;     // [F][P][n0]
   const int64_t* loss_idx;
   const double* target;  // [F][n1][L] (x1 or x2)
+  const double* loss_weight;   // [F][n1][L] or nullptr
+  const double2* loss_offset;  // [F][n1][L] or nullptr
   const SrTables* tabs;
   double2* W;        // tape [n_cfg F][n0][n1]
   double2* W_out;    // optional copy
@@ -437,8 +439,14 @@ __global__ void __launch_bounds__(kSrThreads) sr_solve_kernel(SrArgs a) {
       const double2* fr = a.field + ((int64_t)f * a.P + a.loss_idx[l]) * n;
       double2 bl = make_double2(0.0, 0.0);
       for (int k = 0; k < n; ++k) bl = sr_add(bl, sr_mul(fr[k], w[k * n1 + c]));
+      const int64_t ti = ((int64_t)f * n1 + c) * a.L + l;
+      if (a.loss_offset) bl = sr_add(bl, a.loss_offset[ti]);
+      if (a.loss_weight) {
+        bl.x *= a.loss_weight[ti];
+        bl.y *= a.loss_weight[ti];
+      }
       double2 G;
-      acc += sr_point_loss(a.loss_mode, bl, a.target + (((int64_t)f * n1 + c) * a.L + l) * tw, &G);
+      acc += sr_point_loss(a.loss_mode, bl, a.target + ti * tw, &G);
     }
     acc = sr_block_sum(acc, red);
     if (tid == 0) a.loss_part[g] = acc;
@@ -517,9 +525,17 @@ __global__ void __launch_bounds__(kSrThreads) sr_adjoint_kernel(SrArgs a) {
         const double2* fr = a.field + ((int64_t)f * a.P + a.loss_idx[l]) * n;
         double2 bl = make_double2(0.0, 0.0);
         for (int k = 0; k < n; ++k) bl = sr_add(bl, sr_mul(fr[k], w[k * n1 + c]));
+        const int64_t ti = ((int64_t)f * n1 + c) * a.L + l;
+        double wl = 1.0;
+        if (a.loss_offset) bl = sr_add(bl, a.loss_offset[ti]);
+        if (a.loss_weight) {
+          wl = a.loss_weight[ti];
+          bl.x *= wl;
+          bl.y *= wl;
+        }
         double2 G;
-        sr_point_loss(a.loss_mode, bl, a.target + (((int64_t)f * n1 + c) * a.L + l) * tw, &G);
-        Gs[c * kSrLossChunk + (e % lc)] = make_double2(G.x * gl, G.y * gl);
+        sr_point_loss(a.loss_mode, bl, a.target + ti * tw, &G);
+        Gs[c * kSrLossChunk + (e % lc)] = make_double2(G.x * gl * wl, G.y * gl * wl);
       }
       __syncthreads();
       for (int e = tid; e < nn1; e += kSrThreads) {
@@ -977,6 +993,8 @@ static SrArgs sr_args(const mts_sparams* sp, mts_precision prec, const char* SB,
   a.field = reinterpret_cast<const double2*>(sp->field);
   a.loss_idx = sp->loss_idx;
   a.target = sp->n_loss > 0 ? ev->target : nullptr;
+  a.loss_weight = ev->loss_weight;
+  a.loss_offset = reinterpret_cast<const double2*>(ev->loss_offset);
   a.tabs = reinterpret_cast<const SrTables*>(SB + BL.tabs);
   a.W = reinterpret_cast<double2*>(T + TL.W);
   a.lu = T + TL.lu;

@@ -56,6 +56,7 @@ class MtsEval(ct.Structure):
         ("target", ct.c_void_p), ("target_per_cfg", ct.c_int32), ("loss_mode", ct.c_int32),
         ("refine_tol", ct.c_double), ("max_refine", ct.c_int32),
         ("simt_max_sys", ct.c_int32), ("large_threads", ct.c_int32),
+        ("loss_weight", ct.c_void_p), ("loss_offset", ct.c_void_p),
     ]
 
 
@@ -76,7 +77,8 @@ class MtsSparams(ct.Structure):
 
 class MtsSrouteEval(ct.Structure):
     _fields_ = [("n_cfg", ct.c_int64), ("svar", ct.c_void_p), ("target", ct.c_void_p),
-                ("loss_mode", ct.c_int32), ("refine_tol", ct.c_double), ("max_refine", ct.c_int32)]
+                ("loss_mode", ct.c_int32), ("refine_tol", ct.c_double), ("max_refine", ct.c_int32),
+                ("loss_weight", ct.c_void_p), ("loss_offset", ct.c_void_p)]
 
 
 _lock = threading.Lock()
@@ -231,8 +233,12 @@ class Eval:
     def __init__(self, C: torch.Tensor, omega: torch.Tensor, V: torch.Tensor,
                  target: Optional[torch.Tensor] = None, target_per_cfg: bool = False,
                  loss_mode: int = MTS_LOSS_ABS, refine_tol: float = 0.0, max_refine: int = 0,
-                 simt_max_sys: int = 0, large_threads: int = 0):
+                 simt_max_sys: int = 0, large_threads: int = 0,
+                 loss_weight: Optional[torch.Tensor] = None,
+                 loss_offset: Optional[torch.Tensor] = None):
         self.C = C.contiguous()
+        self.loss_weight = None if loss_weight is None else loss_weight.contiguous()
+        self.loss_offset = None if loss_offset is None else loss_offset.contiguous()
         self.omega = omega.contiguous()
         self.V = V.contiguous()
         self.target = None if target is None else target.contiguous()
@@ -248,6 +254,8 @@ class Eval:
         e.max_refine = int(max_refine)
         e.simt_max_sys = int(simt_max_sys)
         e.large_threads = int(large_threads)
+        e.loss_weight = None if self.loss_weight is None else self.loss_weight.data_ptr()
+        e.loss_offset = None if self.loss_offset is None else self.loss_offset.data_ptr()
         self.c = e
 
     @property
@@ -414,8 +422,12 @@ class SrouteEval:
     float64 view [..., 2]), target [F, n1, L] (real, or [..., 2] complex) or None."""
 
     def __init__(self, svar: torch.Tensor, target: Optional[torch.Tensor] = None,
-                 loss_mode: int = MTS_LOSS_ABS, refine_tol: float = 0.0, max_refine: int = 0):
+                 loss_mode: int = MTS_LOSS_ABS, refine_tol: float = 0.0, max_refine: int = 0,
+                 loss_weight: Optional[torch.Tensor] = None,
+                 loss_offset: Optional[torch.Tensor] = None):
         self.svar = svar.contiguous()
+        self.loss_weight = None if loss_weight is None else loss_weight.contiguous()
+        self.loss_offset = None if loss_offset is None else loss_offset.contiguous()
         self.target = None if target is None else target.contiguous()
         e = MtsSrouteEval()
         e.n_cfg = self.svar.shape[0]
@@ -424,6 +436,8 @@ class SrouteEval:
         e.loss_mode = int(loss_mode)
         e.refine_tol = float(refine_tol)
         e.max_refine = int(max_refine)
+        e.loss_weight = None if self.loss_weight is None else self.loss_weight.data_ptr()
+        e.loss_offset = None if self.loss_offset is None else self.loss_offset.data_ptr()
         self.c = e
 
     @property

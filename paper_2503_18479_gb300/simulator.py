@@ -19,7 +19,10 @@ from .workloads import Workload
 class Simulator:
     def __init__(self, wl: Workload, precision="mixed", device="cuda", target=None,
                  target_per_cfg: Optional[bool] = None, refine_tol: float = 0.0,
-                 max_refine: int = 0):
+                 max_refine: int = 0, loss_weight=None, loss_offset=None):
+        """loss_weight [FL] real and loss_offset [FL] complex (optional): the objective is
+        taken on weight * (B + offset) at the loss points -- the enhancement objective of
+        Sec. IV-B with weight 1/|B_ref| and offset the incident field."""
         self.wl = wl
         self.prec = nv._prec(precision)
         self.device = torch.device(device)
@@ -37,6 +40,10 @@ class Simulator:
         self.target = None if t is None else torch.as_tensor(np.asarray(t, np.float64)).to(self.device)
         self.target_per_cfg = wl.target_per_cfg if target_per_cfg is None else target_per_cfg
         self.loss_mode = wl.loss_mode
+        self.loss_weight = None if loss_weight is None else torch.as_tensor(
+            np.asarray(loss_weight, np.float64)).to(self.device)
+        self.loss_offset = None if loss_offset is None else torch.view_as_real(torch.as_tensor(
+            np.asarray(loss_offset, np.complex128))).contiguous().to(self.device)
         self.refine_tol = refine_tol
         self.max_refine = max_refine
         self.n_struct = len(wl.structures)
@@ -52,7 +59,7 @@ class Simulator:
     def make_eval(self, C: torch.Tensor, with_target: bool = True) -> nv.Eval:
         return nv.Eval(C, self.omega, self.V, self.target if with_target else None,
                        self.target_per_cfg, self.loss_mode, self.refine_tol, self.max_refine,
-                       **self.tuning)
+                       loss_weight=self.loss_weight, loss_offset=self.loss_offset, **self.tuning)
 
     def alloc_tape(self, n_cfg: int) -> torch.Tensor:
         return nv.alloc_bytes(nv.mts_tape_bytes(self.pb, n_cfg, self.prec), self.device)

@@ -22,7 +22,10 @@ from . import native as nv
 class SRoute:
     def __init__(self, S0, field, rows, cols, n1: int, sc_const=None, loss_idx=None,
                  target=None, loss_mode: int = nv.MTS_LOSS_ABS, precision: str = "mixed",
-                 device="cuda"):
+                 device="cuda", loss_weight=None, loss_offset=None):
+        """loss_weight [F, n1, L] real and loss_offset [F, n1, L] complex (optional): the
+        objective is taken on weight * (Bcomb + offset) at the loss points (the enhancement
+        objective of Sec. IV-B with weight 1/|B_ref|)."""
         self.device = torch.device(device)
         self.prec = nv.PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self.sp = nv.Sparams(S0, field, rows, cols, n1, sc_const=sc_const, loss_idx=loss_idx,
@@ -38,6 +41,10 @@ class SRoute:
             t = np.asarray(target)
             t = t.view(np.float64).reshape(t.shape + (2,)) if np.iscomplexobj(t) else t
             self.target = torch.from_numpy(np.ascontiguousarray(t, np.float64)).to(self.device)
+        self.loss_weight = None if loss_weight is None else torch.from_numpy(
+            np.ascontiguousarray(loss_weight, np.float64)).to(self.device)
+        self.loss_offset = None if loss_offset is None else torch.view_as_real(torch.from_numpy(
+            np.ascontiguousarray(loss_offset, np.complex128))).contiguous().to(self.device)
 
     @property
     def b_dtype(self):
@@ -48,7 +55,7 @@ class SRoute:
         if sv.dim() != 3 or sv.shape[1:] != (self.F, self.nS):
             raise ValueError(f"svar must be [n_cfg, {self.F}, {self.nS}] complex")
         return nv.SrouteEval(torch.view_as_real(sv), self.target, self.loss_mode, refine_tol,
-                             max_refine)
+                             max_refine, self.loss_weight, self.loss_offset)
 
     def alloc_tape(self, n_cfg: int):
         return nv.alloc_bytes(nv.mts_sroute_tape_bytes(self.sp, n_cfg, self.prec), self.device)

@@ -160,3 +160,24 @@ def test_size_limits(prec):
         assert rel(out["B"].cpu().numpy(), ref["B"]) < TOL[prec], (n0, rel(out["B"].cpu().numpy(), ref["B"]))
         assert rel(out["loss"].cpu().numpy(), ref["loss"]) < TOL[prec]
         assert rel(g.cpu().numpy(), gref) < TOL[prec], (n0, rel(g.cpu().numpy(), gref))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_enhancement_objective(prec):
+    """The weighted, offset objective (Sec. IV-B) of the route against the oracle's."""
+    from paper_2503_18479_gb300.sroute import SRoute
+    c = _general(seed=11, mode=0)
+    rng = np.random.default_rng(13)
+    w = rng.uniform(0.5, 2.0, c["t"].shape) * 1e6
+    o = (rng.standard_normal(c["t"].shape) + 1j * rng.standard_normal(c["t"].shape)) * 3e-7
+    t = c["t"] * 1e6
+    ref = oracle.sroute_pipeline(c["S0"], c["field"], c["sc"], c["rows"], c["cols"], c["svar"],
+                                 c["li"], t, want_B=False, weight=w, offset=o)
+    gref = oracle.sroute_gradient(c["S0"], c["field"], c["sc"], c["rows"], c["cols"], c["svar"],
+                                  c["li"], t, weight=w, offset=o)
+    sr = SRoute(c["S0"], c["field"], c["rows"], c["cols"], c["n1"], sc_const=c["sc"],
+                loss_idx=c["li"], target=t, precision=prec, loss_weight=w, loss_offset=o)
+    out = sr.forward(torch.from_numpy(c["svar"]), want_B=False)
+    g = sr.backward(out, grad_loss=torch.ones(c["svar"].shape[0], dtype=torch.float64, device="cuda"))
+    assert rel(out["loss"].cpu().numpy(), ref["loss"]) < TOL[prec]
+    assert rel(g.cpu().numpy(), gref) < TOL[prec], rel(g.cpu().numpy(), gref)

@@ -556,6 +556,33 @@ def test_sroute_gradient_central_differences(mode):
     assert np.all(g[:, :, rows >= 4] == 0)
 
 
+def test_sroute_enhancement_objective():
+    """The weighted, offset objective of the pipeline: its value is the mean of
+    (|w (B + o)| - t)^2 over (f, c, l) from the pipeline's own field, and its Eq. 10 gradient
+    matches central differences."""
+    S0, field, Sconst, rows, cols, svar, li, t = _sroute_random(0)
+    rng = np.random.default_rng(12)
+    w = rng.uniform(0.5, 2.0, t.shape)
+    o = (rng.standard_normal(t.shape) + 1j * rng.standard_normal(t.shape)) * 0.3
+    out = oracle.sroute_pipeline(S0, field, Sconst, rows, cols, svar, li, t, weight=w, offset=o)
+    Bl = np.transpose(out["B"][:, :, :, li], (0, 2, 1, 3))  # [b, F, n1, L]
+    want = ((np.abs(w[None] * (Bl + o[None])) - t[None]) ** 2).mean(axis=(1, 2, 3))
+    assert _rel(out["loss"], want) < 1e-13
+    g = oracle.sroute_gradient(S0, field, Sconst, rows, cols, svar, li, t, weight=w, offset=o)
+    h = 1e-6
+    fd = np.zeros_like(g)
+    for idx in np.ndindex(*svar.shape):
+        for unit in (1.0, 1j):
+            sp, sm = svar.copy(), svar.copy()
+            sp[idx] += h * unit
+            sm[idx] -= h * unit
+            kw = dict(want_B=False, weight=w, offset=o)
+            d = (oracle.sroute_pipeline(S0, field, Sconst, rows, cols, sp, li, t, **kw)["loss"][idx[0]]
+                 - oracle.sroute_pipeline(S0, field, Sconst, rows, cols, sm, li, t, **kw)["loss"][idx[0]]) / (2 * h)
+            fd[idx] += d * unit
+    assert _rel(g, fd) < 1e-7
+
+
 def test_sroute_gradient_through_eq3_equals_impedance_adjoint():
     """Chaining Eq. 10 through Eq. 3 (dGamma/dC = 2 Z0 / (Zl + Z0)^2 * j/(w C^2)) gives the
     impedance route's adjoint dloss/dC on the same structure and objective."""
