@@ -136,6 +136,50 @@ __device__ inline double sr_block_sum(double v, double* red) {
   return r;
 }
 
+// Double-float arithmetic on the FP32 pipe (this part's FP64 rate is 1/62 of FP32): a value
+// is an unevaluated sum hi + lo of two floats. The product of two floats is split exactly by
+// the FMA form of Dekker's TwoProd (p = a b, e = fma(a, b, -p)) and added to an accumulator
+// with Knuth's TwoSum; the rounding-mode intrinsics keep the compiler from contracting these
+// steps into fused operations.
+__device__ inline void sr_df_acc(float& hi, float& lo, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float e = fmaf(a, b, -p);
+  const float s = __fadd_rn(hi, p);
+  const float bb = __fsub_rn(s, hi);
+  const float t = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  lo = __fadd_rn(lo, __fadd_rn(t, e));
+  hi = s;
+}
+
+__device__ inline void sr_split(double2 v, float2& h, float2& l) {
+  h = make_float2((float)v.x, (float)v.y);
+  l = make_float2((float)(v.x - (double)h.x), (float)(v.y - (double)h.y));
+}
+
+// sum_j M_j x_j (conj(M_j) x_j when CONJ) for complex M = Mh + Ml (element j at j*ms) and
+// x = xh + xl (element j at j*xs): the hi x hi products exactly, the cross terms in FP32,
+// all accumulated in double-float (about 2^-44 relative).
+template <bool CONJ>
+__device__ double2 sr_df_dot(const float2* __restrict__ Mh, const float2* __restrict__ Ml,
+                             int ms, const float2* xh, const float2* xl, int xs, int n) {
+  float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+  for (int j = 0; j < n; ++j) {
+    float2 a = Mh[(int64_t)j * ms], c = Ml[(int64_t)j * ms];
+    if (CONJ) {
+      a.y = -a.y;
+      c.y = -c.y;
+    }
+    const float2 p = xh[j * xs], q = xl[j * xs];
+    sr_df_acc(rh, rl, a.x, p.x);
+    sr_df_acc(rh, rl, -a.y, p.y);
+    sr_df_acc(ih, il, a.x, p.y);
+    sr_df_acc(ih, il, a.y, p.x);
+    rl = fmaf(a.x, q.x, fmaf(-a.y, q.y, fmaf(c.x, p.x, fmaf(-c.y, p.y, rl))));
+    il = fmaf(a.x, q.y, fmaf(a.y, q.x, fmaf(c.x, p.y, fmaf(c.y, p.x, il))));
+  }
+  return make_double2((double)rh + (double)rl, (double)ih + (double)il);
+}
+
 // LU with partial pivoting of the n x n matrix a (row-major, shared memory), in place:
 // P a = L U, unit L below the diagonal. perm[i] = the original row now at row i. The pivot
 // is the first row of largest |a_ik|^2 (a NaN candidate ranks as 0). Returns 1 on a zero
@@ -191,10 +235,10 @@ __device__ int sr_factor(int n, typename SrT<LT>::V* a, int* perm, int* s_int) {
     const V inv = sr_recip(a[k * n + k]);
     for (int i = k + 1 + tid; i < n; i += kSrThreads) a[i * n + k] = sr_mul(a[i * n + k], inv);
     __syncthreads();
-    const int m = n - k - 1;
-    for (int e = tid; e < m * m; e += kSrThreads) {
-      const int i = k + 1 + e / m, j = k + 1 + e % m;
-      a[i * n + j] = sr_sub(a[i * n + j], sr_mul(a[i * n + k], a[k * n + j]));
+    // trailing update: rows over warps, columns over lanes
+    for (int i = k + 1 + warp; i < n; i += kSrWarps) {
+      const V lik = a[i * n + k];
+      for (int j = k + 1 + lane; j < n; j += 32) a[i * n + j] = sr_sub(a[i * n + j], sr_mul(lik, a[k * n + j]));
     }
     __syncthreads();
   }
@@ -206,20 +250,18 @@ template <typename V>
 __device__ void sr_solve_lu(int n, int n1, const V* a, V* x) {
   const int tid = threadIdx.x;
   for (int k = 0; k + 1 < n; ++k) {
-    const int m = (n - k - 1) * n1;
-    for (int e = tid; e < m; e += kSrThreads) {
-      const int i = k + 1 + e / n1, c = e % n1;
-      x[i * n1 + c] = sr_sub(x[i * n1 + c], sr_mul(a[i * n + k], x[k * n1 + c]));
+    for (int i = k + 1 + tid; i < n; i += kSrThreads) {
+      const V lik = a[i * n + k];
+      for (int c = 0; c < n1; ++c) x[i * n1 + c] = sr_sub(x[i * n1 + c], sr_mul(lik, x[k * n1 + c]));
     }
     __syncthreads();
   }
   for (int k = n - 1; k >= 0; --k) {
     if (tid < n1) x[k * n1 + tid] = sr_mul(x[k * n1 + tid], sr_recip(a[k * n + k]));
     __syncthreads();
-    const int m = k * n1;
-    for (int e = tid; e < m; e += kSrThreads) {
-      const int i = e / n1, c = e % n1;
-      x[i * n1 + c] = sr_sub(x[i * n1 + c], sr_mul(a[i * n + k], x[k * n1 + c]));
+    for (int i = tid; i < k; i += kSrThreads) {
+      const V uik = a[i * n + k];
+      for (int c = 0; c < n1; ++c) x[i * n1 + c] = sr_sub(x[i * n1 + c], sr_mul(uik, x[k * n1 + c]));
     }
     __syncthreads();
   }
@@ -233,18 +275,16 @@ __device__ void sr_solve_lu_h(int n, int n1, const V* a, V* x) {
   for (int k = 0; k < n; ++k) {
     if (tid < n1) x[k * n1 + tid] = sr_mul(x[k * n1 + tid], sr_recip(sr_conj(a[k * n + k])));
     __syncthreads();
-    const int m = (n - k - 1) * n1;
-    for (int e = tid; e < m; e += kSrThreads) {
-      const int i = k + 1 + e / n1, c = e % n1;
-      x[i * n1 + c] = sr_sub(x[i * n1 + c], sr_mul(sr_conj(a[k * n + i]), x[k * n1 + c]));
+    for (int i = k + 1 + tid; i < n; i += kSrThreads) {
+      const V uki = sr_conj(a[k * n + i]);
+      for (int c = 0; c < n1; ++c) x[i * n1 + c] = sr_sub(x[i * n1 + c], sr_mul(uki, x[k * n1 + c]));
     }
     __syncthreads();
   }
   for (int k = n - 1; k > 0; --k) {
-    const int m = k * n1;
-    for (int e = tid; e < m; e += kSrThreads) {
-      const int i = e / n1, c = e % n1;
-      x[i * n1 + c] = sr_sub(x[i * n1 + c], sr_mul(sr_conj(a[k * n + i]), x[k * n1 + c]));
+    for (int i = tid; i < k; i += kSrThreads) {
+      const V lki = sr_conj(a[k * n + i]);
+      for (int c = 0; c < n1; ++c) x[i * n1 + c] = sr_sub(x[i * n1 + c], sr_mul(lki, x[k * n1 + c]));
     }
     __syncthreads();
   }
@@ -280,6 +320,8 @@ struct SrArgs {
   const double* loss_weight;   // [F][n1][L] or nullptr
   const double2* loss_offset;  // [F][n1][L] or nullptr
   const SrTables* tabs;
+  // FP32 factors only: S0 and T as hi/lo float pairs, loss-point rows of the field in FP32
+  const float2 *S0h, *S0l, *Th, *Tl, *fl32;
   double2* W;        // tape [n_cfg F][n0][n1]
   double2* W_out;    // optional copy
   void* lu;          // tape [n_cfg F][n0][n0] (float2 or double2)
@@ -310,6 +352,9 @@ __host__ __device__ inline size_t sr_solve_smem(int n, int n1, int nS, size_t* o
   o[6] = off; off = sr_al16(off + 16 * (size_t)nS);  // sv
   o[7] = off; off = sr_al16(off + 4 * n);            // perm
   o[8] = off; off = sr_al16(off + 8 * 32 + 16);      // reduction scratch, ints
+  const size_t fs = v == 8 ? 8 * (size_t)n * n1 : 0;  // hi/lo split of w (FP32 factors)
+  o[9] = off; off = sr_al16(off + fs);
+  o[10] = off; off = sr_al16(off + fs);
   return off;
 }
 
@@ -322,8 +367,12 @@ __global__ void __launch_bounds__(kSrThreads) sr_solve_kernel(SrArgs a) {
   const int64_t g = blockIdx.x;
   const int64_t b = g / a.F;
   const int f = (int)(g - b * a.F);
-  size_t o[9];
+  constexpr bool kDF = sizeof(V) == 8;  // FP32 factors: double-float residuals
+  size_t o[11];
   sr_solve_smem<LT>(n, n1, a.nS, o);
+  float2* wh = reinterpret_cast<float2*>(sm_sr + o[9]);
+  float2* wlo = reinterpret_cast<float2*>(sm_sr + o[10]);
+  const int64_t fo = (int64_t)f * n * n;
   V* lu = reinterpret_cast<V*>(sm_sr + o[0]);
   double2* rhs = reinterpret_cast<double2*>(sm_sr + o[1]);
   double2* w = reinterpret_cast<double2*>(sm_sr + o[2]);
@@ -350,13 +399,25 @@ __global__ void __launch_bounds__(kSrThreads) sr_solve_kernel(SrArgs a) {
     rhs[e] = sr_add(rhs[e], sv[tb.s12_var[q]]);
   }
   // A = 1 - S_C,const11 S0 - sum over S11 entries v e_r S0[c, :]
-  for (int e = tid; e < n * n; e += kSrThreads) {
-    const int i = e / n, j = e % n;
-    double2 v = make_double2(i == j ? 1.0 : 0.0, 0.0);
-    if (tnz) v = sr_sub(v, Tf[e]);
-    for (int q = tb.r_ptr[i]; q < tb.r_ptr[i + 1]; ++q)
-      v = sr_sub(v, sr_mul(sv[tb.r_var[q]], S0f[tb.r_col[q] * n + j]));
-    lu[e] = sr_from<V>(v);
+  const int lane = tid & 31, warp = tid >> 5;
+  for (int i = warp; i < n; i += kSrWarps)
+  for (int j = lane; j < n; j += 32) {
+    const int e = i * n + j;
+    if constexpr (kDF) {  // the factors are FP32: assemble A in FP32
+      float2 v = make_float2(i == j ? 1.f : 0.f, 0.f);
+      if (tnz) v = sr_sub(v, a.Th[fo + e]);
+      for (int q = tb.r_ptr[i]; q < tb.r_ptr[i + 1]; ++q) {
+        const double2 s = sv[tb.r_var[q]];
+        v = sr_sub(v, sr_mul(make_float2((float)s.x, (float)s.y), a.S0h[fo + tb.r_col[q] * n + j]));
+      }
+      lu[e] = sr_from<V>(make_double2(v.x, v.y));
+    } else {
+      double2 v = make_double2(i == j ? 1.0 : 0.0, 0.0);
+      if (tnz) v = sr_sub(v, Tf[e]);
+      for (int q = tb.r_ptr[i]; q < tb.r_ptr[i + 1]; ++q)
+        v = sr_sub(v, sr_mul(sv[tb.r_var[q]], S0f[tb.r_col[q] * n + j]));
+      lu[e] = sr_from<V>(v);
+    }
   }
   __syncthreads();
   const int singular = sr_factor<LT>(n, lu, perm, sint);
@@ -373,19 +434,35 @@ __global__ void __launch_bounds__(kSrThreads) sr_solve_kernel(SrArgs a) {
   double dprev = sr_block_max(loc, red);
   int converged = a.max_refine == 0;
   for (int it = 0; it < a.max_refine; ++it) {
-    // residual in FP64: r = S12 - A w,  A w = w - T w - sum_q v_q e_row (S0 w)[col]
-    for (int e = tid; e < nn1; e += kSrThreads) {
-      const int i = e / n1, c = e % n1;
-      double2 acc = make_double2(0.0, 0.0);
-      for (int j = 0; j < n; ++j) acc = sr_add(acc, sr_mul(S0f[i * n + j], w[j * n1 + c]));
-      sw[e] = acc;
+    // residual in FP64 (double-float for FP32 factors): r = S12 - A w,
+    // A w = w - T w - sum_q v_q e_row (S0 w)[col]
+    if constexpr (kDF) {
+      for (int e = tid; e < nn1; e += kSrThreads) sr_split(w[e], wh[e], wlo[e]);
+      __syncthreads();
+      for (int e = tid; e < nn1; e += kSrThreads) {
+        const int i = e / n1, c = e % n1;
+        sw[e] = sr_df_dot<false>(a.S0h + fo + i * n, a.S0l + fo + i * n, 1, wh + c, wlo + c, n1, n);
+        if (tnz) r[e] = sr_df_dot<false>(a.Th + fo + i * n, a.Tl + fo + i * n, 1, wh + c, wlo + c, n1, n);
+      }
+    } else {
+      for (int e = tid; e < nn1; e += kSrThreads) {
+        const int i = e / n1, c = e % n1;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int j = 0; j < n; ++j) acc = sr_add(acc, sr_mul(S0f[i * n + j], w[j * n1 + c]));
+        sw[e] = acc;
+      }
     }
     __syncthreads();
     for (int e = tid; e < nn1; e += kSrThreads) {
       const int i = e / n1, c = e % n1;
       double2 aw = w[e];
-      if (tnz)
-        for (int j = 0; j < n; ++j) aw = sr_sub(aw, sr_mul(Tf[i * n + j], w[j * n1 + c]));
+      if (tnz) {
+        if constexpr (kDF) {
+          aw = sr_sub(aw, r[e]);
+        } else {
+          for (int j = 0; j < n; ++j) aw = sr_sub(aw, sr_mul(Tf[i * n + j], w[j * n1 + c]));
+        }
+      }
       for (int q = tb.r_ptr[i]; q < tb.r_ptr[i + 1]; ++q)
         aw = sr_sub(aw, sr_mul(sv[tb.r_var[q]], sw[tb.r_col[q] * n1 + c]));
       r[e] = sr_sub(rhs[e], aw);
@@ -430,15 +507,27 @@ __global__ void __launch_bounds__(kSrThreads) sr_solve_kernel(SrArgs a) {
   for (int e = tid; e < n * n; e += kSrThreads) luo[e] = lu[e];
   for (int i = tid; i < n; i += kSrThreads) a.perm[g * n + i] = perm[i];
 
-  // objective partial at the loss points
+  // objective partial at the loss points (FP32 rows and sums for FP32 factors, as in the
+  // register-resident solve of the impedance route)
   if (a.target != nullptr) {
     const int tw = a.loss_mode == 0 ? 1 : 2;
     double acc = 0.0;
+    if constexpr (kDF) {
+      for (int e = tid; e < nn1; e += kSrThreads) wh[e] = make_float2((float)w[e].x, (float)w[e].y);
+      __syncthreads();
+    }
     for (int e = tid; e < n1 * a.L; e += kSrThreads) {
       const int c = e / a.L, l = e % a.L;
-      const double2* fr = a.field + ((int64_t)f * a.P + a.loss_idx[l]) * n;
       double2 bl = make_double2(0.0, 0.0);
-      for (int k = 0; k < n; ++k) bl = sr_add(bl, sr_mul(fr[k], w[k * n1 + c]));
+      if constexpr (kDF) {
+        const float2* fr = a.fl32 + ((int64_t)f * a.L + l) * n;
+        float2 b32 = make_float2(0.f, 0.f);
+        for (int k = 0; k < n; ++k) b32 = sr_add(b32, sr_mul(fr[k], wh[k * n1 + c]));
+        bl = make_double2(b32.x, b32.y);
+      } else {
+        const double2* fr = a.field + ((int64_t)f * a.P + a.loss_idx[l]) * n;
+        for (int k = 0; k < n; ++k) bl = sr_add(bl, sr_mul(fr[k], w[k * n1 + c]));
+      }
       const int64_t ti = ((int64_t)f * n1 + c) * a.L + l;
       if (a.loss_offset) bl = sr_add(bl, a.loss_offset[ti]);
       if (a.loss_weight) {
@@ -474,6 +563,11 @@ __host__ __device__ inline size_t sr_adj_smem(int n, int n1, int nS, size_t* o) 
   o[7] = off; off = sr_al16(off + 16 * (size_t)nS);
   o[8] = off; off = sr_al16(off + 4 * n);
   o[9] = off; off = sr_al16(off + 8 * 32 + 16);
+  const size_t fs = v == 8 ? 8 * (size_t)n * n1 : 0;  // two hi/lo splits (FP32 factors)
+  for (int q = 10; q < 14; ++q) {
+    o[q] = off;
+    off = sr_al16(off + fs);
+  }
   return off;
 }
 
@@ -486,8 +580,14 @@ __global__ void __launch_bounds__(kSrThreads) sr_adjoint_kernel(SrArgs a) {
   const int64_t g = blockIdx.x;
   const int64_t b = g / a.F;
   const int f = (int)(g - b * a.F);
-  size_t o[10];
+  constexpr bool kDF = sizeof(V) == 8;  // FP32 factors: double-float residuals
+  size_t o[14];
   sr_adj_smem<LT>(n, n1, a.nS, o);
+  float2* ah = reinterpret_cast<float2*>(sm_sa + o[10]);
+  float2* al = reinterpret_cast<float2*>(sm_sa + o[11]);
+  float2* bh = reinterpret_cast<float2*>(sm_sa + o[12]);
+  float2* bl2 = reinterpret_cast<float2*>(sm_sa + o[13]);
+  const int64_t fo = (int64_t)f * n * n;
   V* lu = reinterpret_cast<V*>(sm_sa + o[0]);
   double2* lam = reinterpret_cast<double2*>(sm_sa + o[1]);
   double2* gw = reinterpret_cast<double2*>(sm_sa + o[2]);
@@ -510,6 +610,7 @@ __global__ void __launch_bounds__(kSrThreads) sr_adjoint_kernel(SrArgs a) {
   for (int e = tid; e < nn1; e += kSrThreads) {
     w[e] = a.W[g * nn1 + e];
     gw[e] = make_double2(0.0, 0.0);
+    if constexpr (kDF) sr_split(w[e], bh[e], bl2[e]);  // w split, kept to the end
   }
   __syncthreads();
 
@@ -522,9 +623,16 @@ __global__ void __launch_bounds__(kSrThreads) sr_adjoint_kernel(SrArgs a) {
       const int lc = min(kSrLossChunk, a.L - l0);
       for (int e = tid; e < n1 * lc; e += kSrThreads) {
         const int c = e / lc, l = l0 + e % lc;
-        const double2* fr = a.field + ((int64_t)f * a.P + a.loss_idx[l]) * n;
         double2 bl = make_double2(0.0, 0.0);
-        for (int k = 0; k < n; ++k) bl = sr_add(bl, sr_mul(fr[k], w[k * n1 + c]));
+        if constexpr (kDF) {
+          const float2* fr = a.fl32 + ((int64_t)f * a.L + l) * n;
+          float2 b32 = make_float2(0.f, 0.f);
+          for (int k = 0; k < n; ++k) b32 = sr_add(b32, sr_mul(fr[k], bh[k * n1 + c]));
+          bl = make_double2(b32.x, b32.y);
+        } else {
+          const double2* fr = a.field + ((int64_t)f * a.P + a.loss_idx[l]) * n;
+          for (int k = 0; k < n; ++k) bl = sr_add(bl, sr_mul(fr[k], w[k * n1 + c]));
+        }
         const int64_t ti = ((int64_t)f * n1 + c) * a.L + l;
         double wl = 1.0;
         if (a.loss_offset) bl = sr_add(bl, a.loss_offset[ti]);
@@ -541,9 +649,19 @@ __global__ void __launch_bounds__(kSrThreads) sr_adjoint_kernel(SrArgs a) {
       for (int e = tid; e < nn1; e += kSrThreads) {
         const int k = e / n1, c = e % n1;
         double2 acc = gw[e];
-        for (int q = 0; q < lc; ++q) {
-          const double2 fv = a.field[((int64_t)f * a.P + a.loss_idx[l0 + q]) * n + k];
-          acc = sr_add(acc, sr_mul(sr_conj(fv), Gs[c * kSrLossChunk + q]));
+        if constexpr (kDF) {
+          float2 a32 = make_float2(0.f, 0.f);
+          for (int q = 0; q < lc; ++q) {
+            const double2 gq = Gs[c * kSrLossChunk + q];
+            a32 = sr_add(a32, sr_mul(sr_conj(a.fl32[((int64_t)f * a.L + l0 + q) * n + k]),
+                                     make_float2((float)gq.x, (float)gq.y)));
+          }
+          acc = sr_add(acc, make_double2(a32.x, a32.y));
+        } else {
+          for (int q = 0; q < lc; ++q) {
+            const double2 fv = a.field[((int64_t)f * a.P + a.loss_idx[l0 + q]) * n + k];
+            acc = sr_add(acc, sr_mul(sr_conj(fv), Gs[c * kSrLossChunk + q]));
+          }
         }
         gw[e] = acc;
       }
@@ -583,16 +701,27 @@ __global__ void __launch_bounds__(kSrThreads) sr_adjoint_kernel(SrArgs a) {
       for (int q = tb.c_ptr[j]; q < tb.c_ptr[j + 1]; ++q)
         acc = sr_add(acc, sr_mul(sr_conj(sv[tb.c_var[q]]), lam[tb.c_row[q] * n1 + c]));
       y[e] = acc;
+      if constexpr (kDF) {
+        sr_split(acc, ah[e], al[e]);
+        if (tnz) sr_split(lam[e], bh[e], bl2[e]);  // lam split (w's split is redone below)
+      }
     }
     __syncthreads();
     for (int e = tid; e < nn1; e += kSrThreads) {
       const int i = e / n1, c = e % n1;
-      double2 ah = lam[e];
-      for (int j = 0; j < n; ++j) {
-        ah = sr_sub(ah, sr_mul(sr_conj(S0f[j * n + i]), y[j * n1 + c]));
-        if (tnz) ah = sr_sub(ah, sr_mul(sr_conj(Tf[j * n + i]), lam[j * n1 + c]));
+      double2 acc = lam[e];
+      if constexpr (kDF) {
+        // column i of S0 (and T): conj(S0[j][i]) at j n + i
+        acc = sr_sub(acc, sr_df_dot<true>(a.S0h + fo + i, a.S0l + fo + i, n, ah + c, al + c, n1, n));
+        if (tnz)
+          acc = sr_sub(acc, sr_df_dot<true>(a.Th + fo + i, a.Tl + fo + i, n, bh + c, bl2 + c, n1, n));
+      } else {
+        for (int j = 0; j < n; ++j) {
+          acc = sr_sub(acc, sr_mul(sr_conj(S0f[j * n + i]), y[j * n1 + c]));
+          if (tnz) acc = sr_sub(acc, sr_mul(sr_conj(Tf[j * n + i]), lam[j * n1 + c]));
+        }
       }
-      r[e] = sr_sub(gw[e], ah);
+      r[e] = sr_sub(gw[e], acc);
     }
     __syncthreads();
     for (int e = tid; e < nn1; e += kSrThreads) x[e] = sr_from<V>(r[e]);
@@ -622,11 +751,19 @@ __global__ void __launch_bounds__(kSrThreads) sr_adjoint_kernel(SrArgs a) {
   // gradient: S11 entry (r, c): sum_col lam[r][col] conj((S0 W)[c][col]); S12 entry (r, c):
   // lam[r][c - n0]; S21, S22: 0
   double2* sw = y;
+  if constexpr (kDF) {
+    for (int e = tid; e < nn1; e += kSrThreads) sr_split(w[e], bh[e], bl2[e]);
+    __syncthreads();
+  }
   for (int e = tid; e < nn1; e += kSrThreads) {
     const int i = e / n1, c = e % n1;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int j = 0; j < n; ++j) acc = sr_add(acc, sr_mul(S0f[i * n + j], w[j * n1 + c]));
-    sw[e] = acc;
+    if constexpr (kDF) {
+      sw[e] = sr_df_dot<false>(a.S0h + fo + i * n, a.S0l + fo + i * n, 1, bh + c, bl2 + c, n1, n);
+    } else {
+      double2 acc = make_double2(0.0, 0.0);
+      for (int j = 0; j < n; ++j) acc = sr_add(acc, sr_mul(S0f[i * n + j], w[j * n1 + c]));
+      sw[e] = acc;
+    }
   }
   __syncthreads();
   for (int q = tid; q < a.nS; q += kSrThreads) {
@@ -717,6 +854,28 @@ __global__ void sr_const_kernel(int n0, int n1, const double2* __restrict__ S0,
   }
 }
 
+// hi/lo float pairs of a complex FP64 array (double-float operands of the residuals)
+__global__ void sr_split_kernel(int64_t n, const double2* __restrict__ src, float2* __restrict__ hi,
+                                float2* __restrict__ lo) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    sr_split(src[i], hi[i], lo[i]);
+}
+
+// the field's rows at the loss points in FP32, [F][L][n0]
+__global__ void sr_lossrows_kernel(int F, int64_t P, int L, int n0, const double2* __restrict__ field,
+                                   const int64_t* __restrict__ loss_idx, float2* __restrict__ out) {
+  const int64_t total = (int64_t)F * L * n0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(i % n0);
+    const int64_t fl = i / n0;
+    const int f = (int)(fl / L), l = (int)(fl % L);
+    const double2 v = field[((int64_t)f * P + loss_idx[l]) * n0 + k];
+    out[i] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
 __global__ void sr_tables_kernel(SrTables t, SrTables* out) {
   const int32_t* src = reinterpret_cast<const int32_t*>(&t);
   int32_t* dst = reinterpret_cast<int32_t*>(out);
@@ -784,7 +943,7 @@ __global__ void sr_rc_vjp_kernel(int64_t n_cfg, int F, int nL, const double* __r
 // host side: layouts, the internal per-frequency problem, launch sequences
 // ---------------------------------------------------------------------------------------
 struct SrBasisLayout {
-  size_t vport, vpoint, vfreq, vbasis, T, tflag, tabs, total;
+  size_t vport, vpoint, vfreq, vbasis, T, tflag, tabs, S0h, S0l, Th, Tl, fl32, total;
   BasisLayout vb;
 };
 
@@ -837,6 +996,11 @@ static SrBasisLayout sr_basis_layout(const mts_sparams* sp, mts_precision prec, 
   L.T = o; o += align256(16 * F * n0 * n0);
   L.tflag = o; o += 256;
   L.tabs = o; o += align256(sizeof(SrTables));
+  L.S0h = o; o += align256(8 * F * n0 * n0);
+  L.S0l = o; o += align256(8 * F * n0 * n0);
+  L.Th = o; o += align256(8 * F * n0 * n0);
+  L.Tl = o; o += align256(8 * F * n0 * n0);
+  L.fl32 = o; o += align256(8 * F * (size_t)sp->n_loss * n0);
   L.total = o;
   return L;
 }
@@ -945,7 +1109,7 @@ constexpr size_t kSrMaxSmem = 227 * 1024;  // opt-in shared memory per CTA
 
 template <typename LT>
 static cudaError_t sr_launch_solve(const SrArgs& a, int64_t n_sys, cudaStream_t st) {
-  size_t o[9];
+  size_t o[11];
   const size_t sm = sr_solve_smem<LT>(a.n0, a.n1, a.nS, o);
   if (sm > kSrMaxSmem) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(sr_solve_kernel<LT>,
@@ -958,7 +1122,7 @@ static cudaError_t sr_launch_solve(const SrArgs& a, int64_t n_sys, cudaStream_t 
 
 template <typename LT>
 static cudaError_t sr_launch_adjoint(const SrArgs& a, int64_t n_sys, cudaStream_t st) {
-  size_t o[10];
+  size_t o[14];
   const size_t sm = sr_adj_smem<LT>(a.n0, a.n1, a.nS, o);
   if (sm > kSrMaxSmem) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(sr_adjoint_kernel<LT>,
@@ -996,6 +1160,11 @@ static SrArgs sr_args(const mts_sparams* sp, mts_precision prec, const char* SB,
   a.loss_weight = ev->loss_weight;
   a.loss_offset = reinterpret_cast<const double2*>(ev->loss_offset);
   a.tabs = reinterpret_cast<const SrTables*>(SB + BL.tabs);
+  a.S0h = reinterpret_cast<const float2*>(SB + BL.S0h);
+  a.S0l = reinterpret_cast<const float2*>(SB + BL.S0l);
+  a.Th = reinterpret_cast<const float2*>(SB + BL.Th);
+  a.Tl = reinterpret_cast<const float2*>(SB + BL.Tl);
+  a.fl32 = reinterpret_cast<const float2*>(SB + BL.fl32);
   a.W = reinterpret_cast<double2*>(T + TL.W);
   a.lu = T + TL.lu;
   a.perm = reinterpret_cast<int32_t*>(T + TL.perm);
@@ -1062,6 +1231,26 @@ mts_status mts_sroute_build(const mts_sparams* sp, mts_precision prec, void* sba
   }
   sr_tables_kernel<<<1, 256, 0, st>>>(sr_build_tables(sp), reinterpret_cast<SrTables*>(SB + L.tabs));
   note_launch();
+  // double-float operands and FP32 loss rows of the FP32-factor kernels
+  const int64_t nsq = (int64_t)F * n0 * n0;
+  const unsigned sb = (unsigned)((nsq + 255) / 256 < 4096 ? (nsq + 255) / 256 : 4096);
+  sr_split_kernel<<<sb, 256, 0, st>>>(nsq, reinterpret_cast<const double2*>(sp->S0),
+                                      reinterpret_cast<float2*>(SB + L.S0h),
+                                      reinterpret_cast<float2*>(SB + L.S0l));
+  note_launch();
+  if (sp->sc_const) {
+    sr_split_kernel<<<sb, 256, 0, st>>>(nsq, reinterpret_cast<const double2*>(SB + L.T),
+                                        reinterpret_cast<float2*>(SB + L.Th),
+                                        reinterpret_cast<float2*>(SB + L.Tl));
+    note_launch();
+  }
+  if (sp->n_loss > 0) {
+    const int64_t nl = (int64_t)F * sp->n_loss * n0;
+    sr_lossrows_kernel<<<(unsigned)((nl + 255) / 256 < 4096 ? (nl + 255) / 256 : 4096), 256, 0, st>>>(
+        F, sp->n_points, sp->n_loss, n0, reinterpret_cast<const double2*>(sp->field), sp->loss_idx,
+        reinterpret_cast<float2*>(SB + L.fl32));
+    note_launch();
+  }
   return sr_cuda(cudaGetLastError());
 }
 
