@@ -274,6 +274,13 @@ mts_status mts_param_grad(const mts_problem* pb, mts_precision prec, const void*
 mts_status mts_tape_status(const mts_problem* pb, int64_t n_cfg, mts_precision prec,
                            const void* tape, int64_t* n_bad, mts_stream stream);
 
+/* Per-system status of the last forward on this tape, copied to status_out (device int32
+ * [n_cfg][n_freq], the frequency index global as in mts_eval.omega): 0 converged, 1 missed
+ * the refinement tolerance, 2 zero pivot or non-finite value (results written either way).
+ * Enqueued on `stream`; no synchronisation. */
+mts_status mts_system_status(const mts_problem* pb, int64_t n_cfg, mts_precision prec,
+                             const void* tape, int32_t* status_out, mts_stream stream);
+
 /* ---------------------------------------------------------------------------------
  * mts_solve_static: mts_solve without a tape, for callers that cannot allocate device
  * memory when they solve (a real-time loop that may not call the allocator, a plugin

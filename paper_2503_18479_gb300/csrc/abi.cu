@@ -528,6 +528,18 @@ mts_status mts_tape_status(const mts_problem* pb, int64_t n_cfg, mts_precision p
   return h[1] ? MTS_ENOCONV : MTS_OK;
 }
 
+mts_status mts_system_status(const mts_problem* pb, int64_t n_cfg, mts_precision prec,
+                             const void* tape, int32_t* status_out, mts_stream stream) {
+  mts_status v = validate_problem(pb);
+  if (v != MTS_OK) return v;
+  if (validate_prec(prec) != MTS_OK || !tape || !status_out || n_cfg < 0) return MTS_EINVAL;
+  if (n_cfg == 0 || pb->n_freq == 0) return MTS_OK;
+  TapeLayout tl = tape_layout(pb, n_cfg, prec);
+  return cuda_status(cudaMemcpyAsync(status_out, static_cast<const char*>(tape) + tl.status,
+                                     sizeof(int32_t) * (size_t)n_cfg * pb->n_freq,
+                                     cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+}
+
 mts_status mts_param_grad(const mts_problem* pb, mts_precision prec, const void* basis,
                           const mts_eval* ev, const void* tape, size_t tape_bytes,
                           const double* grad_loss, double* grad_R, double* grad_L,

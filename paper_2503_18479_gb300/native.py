@@ -29,7 +29,7 @@ EXPORTED = ["mts_status_string", "mts_version", "mts_launch_count", "mts_basis_b
             "mts_solve_static", "mts_adam_step", "mts_param_grad", "mts_sroute_basis_bytes",
             "mts_sroute_build", "mts_sroute_tape_bytes", "mts_sroute_forward",
             "mts_sroute_backward", "mts_sroute_status", "mts_rc_reflection",
-            "mts_rc_reflection_vjp"]
+            "mts_rc_reflection_vjp", "mts_system_status"]
 MTS_PROJ_NONE, MTS_PROJ_CLIP, MTS_PROJ_TANH = 0, 1, 2
 PROJECTIONS = {None: MTS_PROJ_NONE, "none": MTS_PROJ_NONE, "clip": MTS_PROJ_CLIP, "tanh": MTS_PROJ_TANH}
 
@@ -144,6 +144,8 @@ def lib():
             L.mts_rc_reflection.argtypes = [i64, i32, i32, p, p, p, d, i32, i32, p, p]
             L.mts_rc_reflection_vjp.restype = ct.c_int
             L.mts_rc_reflection_vjp.argtypes = [i64, i32, i32, p, p, p, d, i32, i32, p, p, p, p]
+            L.mts_system_status.restype = ct.c_int
+            L.mts_system_status.argtypes = [PP, i64, ct.c_int, p, p, p]
             L.mts_tape_status.restype = ct.c_int
             L.mts_tape_status.argtypes = [PP, i64, ct.c_int, p, ct.POINTER(ct.c_int64), p]
             _lib = L
@@ -334,6 +336,12 @@ def mts_tape_status(pb, n_cfg: int, prec, tape, stream=None):
     code = lib().mts_tape_status(pb.ref, int(n_cfg), _prec(prec), _ptr(tape), ct.byref(n_bad),
                                  _stream(stream))
     return int(code), int(n_bad.value)
+
+
+def mts_system_status(pb, n_cfg: int, prec, tape, status_out, stream=None):
+    """Per-system status words [n_cfg, n_freq] (int32 device tensor) of the last forward."""
+    _check(lib().mts_system_status(pb.ref, int(n_cfg), _prec(prec), _ptr(tape), _ptr(status_out),
+                                   _stream(stream)), "mts_system_status")
 
 
 def mts_solve_static(pb, prec, basis, ev: Eval, I_out=None, loss_out=None, dloss_dC_out=None,

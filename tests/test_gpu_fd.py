@@ -68,6 +68,12 @@ def test_non_finite_capacitance_is_flagged(prec):
     torch.cuda.synchronize()
     code, n_bad = sim.status(out["tape"], wl.n_cfg)
     assert n_bad == 1 and code != 0
+    # which system: mts_system_status copies the per-system words
+    from paper_2503_18479_gb300 import native as nv
+    words = torch.full((wl.n_cfg, sim.omega.numel()), -1, dtype=torch.int32, device="cuda")
+    nv.mts_system_status(sim.pb, wl.n_cfg, sim.prec, out["tape"], words)
+    w = words.cpu().numpy()
+    assert w[3, 0] == 2 and np.count_nonzero(w) == 1, w
     keep = [b for b in range(8) if b != 3]
     assert torch.equal(out["B"][keep], ref["B"][keep])
     assert torch.equal(out["loss"][keep], ref["loss"][keep])
