@@ -211,6 +211,15 @@ __global__ void __launch_bounds__(NM >= 64 ? NM : 128, NM >= 64 ? 5 : 1) solve_m
   const float* __restrict__ Ml = a.M32lo + mo;
 
   // ---- row r of A (FP32), identity rows for padding ----
+  // The diagonal entry needs FP64 (w (M_rr hi + lo) + Im D_r, then rounded): it is computed
+  // once per thread here, not inside the unrolled column loop, where each column's branch
+  // would run its FP64 instructions for the one lane with c == r (this part's FP64 rate is
+  // 1/62 of FP32).
+  float dre = 1.0f, dim = 0.0f;
+  if (real_row) {
+    dre = (float)Dr.x;
+    dim = (float)(w * ((double)__ldg(Mh + r * N + r) + (double)__ldg(Ml + r * N + r)) + Dr.y);
+  }
   u64 ReP[NB][4], ImP[NB][4];
 #pragma unroll
   for (int b = 0; b < NB; ++b)
@@ -220,18 +229,9 @@ __global__ void __launch_bounds__(NM >= 64 ? NM : 128, NM >= 64 ? 5 : 1) solve_m
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int c = 8 * b + 2 * m + h;
-        float mm = (real_row && c < N) ? w32 * __ldg(Mh + c * N + r) : 0.0f;  // M symmetric
-        float re = 0.0f;
-        if (c == r) {
-          if (real_row) {
-            re = (float)Dr.x;
-            mm = (float)(w * ((double)__ldg(Mh + r * N + r) + (double)__ldg(Ml + r * N + r)) + Dr.y);
-          } else {
-            re = 1.0f;
-          }
-        }
-        re2[h] = re;
-        im2[h] = mm;
+        const float mm = (real_row && c < N) ? w32 * __ldg(Mh + c * N + r) : 0.0f;  // M symmetric
+        re2[h] = (c == r) ? dre : 0.0f;
+        im2[h] = (c == r) ? dim : mm;
       }
       ReP[b][m] = pk(re2[0], re2[1]);
       ImP[b][m] = pk(im2[0], im2[1]);
