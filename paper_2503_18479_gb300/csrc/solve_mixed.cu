@@ -262,8 +262,9 @@ __global__ void __launch_bounds__(NM >= 64 ? NM : 128, NM >= 64 ? 5 : 1) solve_m
           if ((r & 31) == 0) sm.ukey[par][wv] = wmax;
           if (r == cand) {  // this warp's candidate publishes its row speculatively
 #pragma unroll
-            for (int b = 0; b < NB; ++b)
-              if (b < nact) {
+            for (int b = 0; b < NB; ++b) {
+              if (b >= nact) break;  // finished panels sit at the end: skip them by a jump
+              {
                 ulonglong2* dr = reinterpret_cast<ulonglong2*>(&sm.prow_re[par][wv][8 * b]);
                 ulonglong2* di = reinterpret_cast<ulonglong2*>(&sm.prow_im[par][wv][8 * b]);
                 dr[0] = make_ulonglong2(ReP[b][0], ReP[b][1]);
@@ -271,6 +272,7 @@ __global__ void __launch_bounds__(NM >= 64 ? NM : 128, NM >= 64 ? 5 : 1) solve_m
                 di[0] = make_ulonglong2(ImP[b][0], ImP[b][1]);
                 di[1] = make_ulonglong2(ImP[b][2], ImP[b][3]);
               }
+            }
           }
           __syncthreads();
           unsigned best = sm.ukey[par][0];
@@ -322,7 +324,8 @@ __global__ void __launch_bounds__(NM >= 64 ? NM : 128, NM >= 64 ? 5 : 1) solve_m
         set_elem(ReP[0], ImP[0], kk, l);
 #pragma unroll
         for (int b = 1; b < NB; ++b) {
-          if (b < nact) {
+          if (b >= nact) break;  // finished panels sit at the end: skip them by a jump
+          {
             const ulonglong2 x0 = reinterpret_cast<const ulonglong2*>(ur)[2 * b];
             const ulonglong2 x1 = reinterpret_cast<const ulonglong2*>(ur)[2 * b + 1];
             const ulonglong2 y0 = reinterpret_cast<const ulonglong2*>(ui)[2 * b];
