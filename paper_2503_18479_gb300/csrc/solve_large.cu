@@ -17,8 +17,12 @@
 // the other rows take the panel's contribution (thread per row).
 //
 //   R = double: FP64 factors and one solve (MTS_FP64, NB = 8).
-//   R = float : FP32 factors (NB = 16) and iterative refinement on FP64 residuals
-//               rhs - A x, stopped by the same predictive estimate as the small systems.
+//   R = float : FP32 factors (NB = 16) and iterative refinement on residuals rhs - A x
+//               taken in double-float on the FP32 pipe (M = hi + lo, x = hi + lo), stopped
+//               by the same predictive estimate as the small systems. A, the pivot
+//               magnitudes and the loss-point fields are FP32 too: this part's FP64 rate is
+//               1/62 of FP32, and FP64 arithmetic there (an N^2 residual, per-step FP64
+//               arg-max compares) outweighed the FP32 LU for N = 128.
 // The objective at the loss points, the adjoint solve with the same matrix (A^T = A) and
 // dloss/dC_k = Im(mu_k I_k)/(w C_k^2) (Eq. 8-9) are as in solve.cu.
 #include <cuda_bf16.h>
@@ -61,6 +65,7 @@ struct LargeCfg<double> {
 
 struct BlockRed {
   double key[kLargeMaxWarps];
+  float keyf[kLargeMaxWarps];
   int idx[kLargeMaxWarps];
 };
 
@@ -109,6 +114,38 @@ __device__ inline int block_argmax(double key, int idx, BlockRed* red) {
       ib = red->idx[q];
     }
   return ib;
+}
+
+// the same over FP32 keys
+template <int W>
+__device__ inline int block_argmax_f(float key, int idx, BlockRed* red) {
+  argmax_shfl(key, idx, 32);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    red->keyf[threadIdx.x >> 5] = key;
+    red->idx[threadIdx.x >> 5] = idx;
+  }
+  __syncthreads();
+  float kb = red->keyf[0];
+  int ib = red->idx[0];
+#pragma unroll
+  for (int q = 1; q < W; ++q)
+    if (red->keyf[q] > kb || (red->keyf[q] == kb && red->idx[q] < ib)) {
+      kb = red->keyf[q];
+      ib = red->idx[q];
+    }
+  return ib;
+}
+
+// hi += a b exactly-split (FMA form of Dekker's TwoProd, Knuth's TwoSum) with the error in lo
+__device__ inline void lg_df_acc(float& hi, float& lo, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float e = fmaf(a, b, -p);
+  const float s = __fadd_rn(hi, p);
+  const float bb = __fsub_rn(s, hi);
+  const float t = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  lo = __fadd_rn(lo, __fadd_rn(t, e));
+  hi = s;
 }
 
 template <int W>
@@ -162,6 +199,12 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
   cd* xc = reinterpret_cast<cd*>(dsm + L.xc);
   BlockRed* red = reinterpret_cast<BlockRed*>(dsm + L.red);
   Cx<R>* pvec = reinterpret_cast<Cx<R>*>(dsm + L.pvec);
+  // float2 hi / lo split of an FP64 vector for the double-float residual and the FP32
+  // objective; they reuse the triangular-solve vector (n elements of at least 8 bytes) and
+  // the U12 chunk (NB x CW >= n elements), both idle outside the LU and the solves
+  float2* xh = reinterpret_cast<float2*>(dsm + L.wv);
+  float2* xl = reinterpret_cast<float2*>(dsm + L.u12);
+  constexpr bool kF = sizeof(R) == 4;  // FP32 factors: no FP64 on the per-element paths
   const int NP = N + 1;  // panel pitch
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -175,6 +218,28 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
 
   // ---- assemble A (Eq. 2, 11), four independent loads of M in flight per thread ----
   const int NN = N * N;
+  if constexpr (kF) {
+    // off-diagonal (and the diagonal's placeholder) in FP32 from the FP32 part of M
+    const float w32 = (float)w;
+    const float* __restrict__ M32 = a.M32hi + a.t.nn_off[si.s];
+    for (int e0 = 0; e0 < NN; e0 += 4 * T) {
+      float mv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = e0 + q * T + tid;
+        mv[q] = e < NN ? M32[e] : 0.0f;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = e0 + q * T + tid;
+        if (e < NN) A[e] = {(R)0, (R)(w32 * mv[q])};
+      }
+    }
+    __syncthreads();
+    // the diagonal once per row in FP64: R_r + j (w M_rr - 1/(w C_r))
+    for (int r = tid; r < N; r += T)
+      A[(int64_t)r * N + r] = {(R)Rk[r], (R)(w * M[(int64_t)r * N + r] - 1.0 / (w * Cb[r]))};
+  } else
   for (int e0 = 0; e0 < NN; e0 += 4 * T) {
     double mv[4];
 #pragma unroll
@@ -210,19 +275,36 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
     }
     __syncthreads();
     for (int kk = 0; kk < nb; ++kk) {
-      double best = -1.0;
-      int bi = N;
-      for (int r = tid; r < N; r += T)
-        if (pivstep[r] == N) {
-          const Cx<R> v = pan[kk * NP + r];
-          double m = (double)v.x * v.x + (double)v.y * v.y;
-          if (!(m >= 0.0)) m = 0.0;  // NaN: still a candidate, so a row is always chosen
-          if (m > best) {
-            best = m;
-            bi = r;
+      int p;
+      if constexpr (kF) {
+        float best = -1.0f;
+        int bi = N;
+        for (int r = tid; r < N; r += T)
+          if (pivstep[r] == N) {
+            const Cx<R> v = pan[kk * NP + r];
+            float m = v.x * v.x + v.y * v.y;
+            if (!(m >= 0.0f)) m = 0.0f;  // NaN: still a candidate, so a row is always chosen
+            if (m > best) {
+              best = m;
+              bi = r;
+            }
           }
-        }
-      const int p = block_argmax<W>(best, bi, red);
+        p = block_argmax_f<W>(best, bi, red);
+      } else {
+        double best = -1.0;
+        int bi = N;
+        for (int r = tid; r < N; r += T)
+          if (pivstep[r] == N) {
+            const Cx<R> v = pan[kk * NP + r];
+            double m = (double)v.x * v.x + (double)v.y * v.y;
+            if (!(m >= 0.0)) m = 0.0;  // NaN: still a candidate, so a row is always chosen
+            if (m > best) {
+              best = m;
+              bi = r;
+            }
+          }
+        p = block_argmax<W>(best, bi, red);
+      }
       const Cx<R> piv = pan[kk * NP + p];
       for (int r = tid; r < N; r += T)
         if (pivstep[r] == N && r != p) {
@@ -390,15 +472,27 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
     if (sizeof(R) < 8) {
       double dprev = block_max<W>(xm, red);  // its barriers also publish xk
       conv = a.max_refine == 0;
+      const float* __restrict__ Mh = a.M32hi + a.t.nn_off[si.s];
+      const float* __restrict__ Ml = a.M32lo + a.t.nn_off[si.s];
       for (int it = 0; it < a.max_refine; ++it) {
-        for (int r = tid; r < N; r += T) {  // FP64 residual sv - A xk
-          double sx = 0.0, sy = 0.0;
-#pragma unroll 8
+        for (int k = tid; k < N; k += T) {  // x = hi + lo
+          const float hx = (float)xk[k].x, hy = (float)xk[k].y;
+          xh[k] = make_float2(hx, hy);
+          xl[k] = make_float2((float)(xk[k].x - (double)hx), (float)(xk[k].y - (double)hy));
+        }
+        __syncthreads();
+        for (int r = tid; r < N; r += T) {  // residual sv - A xk, M x in double-float
+          float shx = 0.f, slx = 0.f, shy = 0.f, sly = 0.f;
+#pragma unroll 4
           for (int j = 0; j < N; ++j) {
-            const double m = M[(int64_t)j * N + r];  // M symmetric: column r, coalesced
-            sx = fma(m, xk[j].x, sx);
-            sy = fma(m, xk[j].y, sy);
+            const float mh = Mh[(int64_t)j * N + r], ml = Ml[(int64_t)j * N + r];  // column r
+            const float2 ph = xh[j], pl = xl[j];
+            lg_df_acc(shx, slx, mh, ph.x);
+            lg_df_acc(shy, sly, mh, ph.y);
+            slx = fmaf(mh, pl.x, fmaf(ml, ph.x, slx));
+            sly = fmaf(mh, pl.y, fmaf(ml, ph.y, sly));
           }
+          const double sx = (double)shx + (double)slx, sy = (double)shy + (double)sly;
           const double dx = Rk[r], dy = -1.0 / (w * Cb[r]);
           const double ax = dx * xk[r].x - dy * xk[r].y - w * sy;
           const double ay = dx * xk[r].y + dy * xk[r].x + w * sx;
@@ -488,18 +582,45 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
                          (a.t.fl_off[si.s] + (int64_t)si.f * Ls) * tw;
       const int64_t wo = a.t.fl_off[si.s] + (int64_t)si.f * Ls;  // weight / offset base
       cd* Gs = reinterpret_cast<cd*>(dsm + L.pan);  // the panel is free after the LU
+      float2* Gh = reinterpret_cast<float2*>(dsm + L.pan);  // conj(G) = hi + lo (FP32)
+      float2* Glo = Gh + T;
+      const float* __restrict__ Hl32 = a.Hl32 + a.t.ln_off[si.s];
       double lsum = 0.0;
       for (int r = tid; r < N; r += T) rhs[r] = {0.0, 0.0};
+      if constexpr (kF) {  // currents as hi + lo floats for the double-float sums below
+        for (int k = tid; k < N; k += T) {
+          const float hx = (float)xc[k].x, hy = (float)xc[k].y;
+          xh[k] = make_float2(hx, hy);
+          xl[k] = make_float2((float)(xc[k].x - (double)hx), (float)(xc[k].y - (double)hy));
+        }
+        __syncthreads();
+      }
       for (int c0 = 0; c0 < Ls; c0 += T) {
         const int l = c0 + tid;
         cd Gl = {0.0, 0.0};
         if (l < Ls) {
           double bx = 0.0, by = 0.0;
+          if constexpr (kF) {
+            // FP32 rows (the basis is FP32), double-float sums: N terms with cancellation
+            // (sum |H x| / |b| reaches ~100 at N = 1024) need more than FP32 accumulation
+            float hx = 0.f, lx = 0.f, hy = 0.f, ly = 0.f;
+#pragma unroll 4
+            for (int k = 0; k < N; ++k) {
+              const float h = Hl32[(int64_t)l * N + k];
+              lg_df_acc(hx, lx, h, xh[k].x);
+              lg_df_acc(hy, ly, h, xh[k].y);
+              lx = fmaf(h, xl[k].x, lx);
+              ly = fmaf(h, xl[k].y, ly);
+            }
+            bx = (double)hx + (double)lx;
+            by = (double)hy + (double)ly;
+          } else {
 #pragma unroll 8
-          for (int k = 0; k < N; ++k) {
-            const double h = Hl[(int64_t)l * N + k];
-            bx = fma(h, xc[k].x, bx);
-            by = fma(h, xc[k].y, by);
+            for (int k = 0; k < N; ++k) {
+              const double h = Hl[(int64_t)l * N + k];
+              bx = fma(h, xc[k].x, bx);
+              by = fma(h, xc[k].y, by);
+            }
           }
           double wl = 1.0;
           if (a.loss_offset) {
@@ -515,18 +636,37 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
           Gl.x *= wl;
           Gl.y *= wl;
         }
-        Gs[tid] = {Gl.x, -Gl.y};  // conj(G)
+        if constexpr (kF) {  // conj(G)
+          const float gx = (float)Gl.x, gy = (float)(-Gl.y);
+          Gh[tid] = make_float2(gx, gy);
+          Glo[tid] = make_float2((float)(Gl.x - (double)gx), (float)(-Gl.y - (double)gy));
+        } else {
+          Gs[tid] = {Gl.x, -Gl.y};
+        }
         __syncthreads();
         const int lc = min(T, Ls - c0);
         for (int r = tid; r < N; r += T) {
-          double ux = rhs[r].x, uy = rhs[r].y;
+          if constexpr (kF) {
+            float hx = 0.f, lx = 0.f, hy = 0.f, ly = 0.f;
+#pragma unroll 4
+            for (int q = 0; q < lc; ++q) {
+              const float h = Hl32[(int64_t)(c0 + q) * N + r];
+              lg_df_acc(hx, lx, h, Gh[q].x);
+              lg_df_acc(hy, ly, h, Gh[q].y);
+              lx = fmaf(h, Glo[q].x, lx);
+              ly = fmaf(h, Glo[q].y, ly);
+            }
+            rhs[r] = {rhs[r].x + ((double)hx + (double)lx), rhs[r].y + ((double)hy + (double)ly)};
+          } else {
+            double ux = rhs[r].x, uy = rhs[r].y;
 #pragma unroll 8
-          for (int q = 0; q < lc; ++q) {
-            const double h = Hl[(int64_t)(c0 + q) * N + r];
-            ux = fma(h, Gs[q].x, ux);
-            uy = fma(h, Gs[q].y, uy);
+            for (int q = 0; q < lc; ++q) {
+              const double h = Hl[(int64_t)(c0 + q) * N + r];
+              ux = fma(h, Gs[q].x, ux);
+              uy = fma(h, Gs[q].y, uy);
+            }
+            rhs[r] = {ux, uy};
           }
-          rhs[r] = {ux, uy};
         }
         __syncthreads();
       }
