@@ -244,9 +244,14 @@ __global__ void __launch_bounds__(kThreads, 1) superpose_tc_kernel(SuperposeArgs
       bool ok = true;
       uint32_t last_phase[NSTAGE];
       bool used[NSTAGE];
+      // the B-operand tile (structure, column tile, K chunk) each stage holds: consecutive
+      // units of a CTA usually share it (units advance along the point tiles first), and a
+      // stage whose B image is already the one needed only refills its A pieces
+      uint64_t bkey[NSTAGE];
       for (int i = 0; i < NSTAGE; ++i) {
         used[i] = false;
         last_phase[i] = 0;
+        bkey[i] = ~0ull;
       }
       for (int64_t u = u_begin; u < u_end && ok; ++u) {
         Unit x = unit_info(a, u);
@@ -261,15 +266,20 @@ __global__ void __launch_bounds__(kThreads, 1) superpose_tc_kernel(SuperposeArgs
           }
           unsigned char* sA = stages + stage * kStageBytes;
           unsigned char* sB = sA + NPIECE * kTileBytes;
-          mbar_arrive_expect_tx(&full[stage], kStageBytes);
+          const uint64_t key = ((uint64_t)x.s << 44) | ((uint64_t)x.nt << 12) | (uint64_t)kc;
+          const bool needB = bkey[stage] != key;
+          mbar_arrive_expect_tx(&full[stage], needB ? kStageBytes : NPIECE * kTileBytes);
           for (int q = 0; q < NPIECE; ++q) {
             const unsigned char* ga =
                 Ab + ((size_t)(q * x.nptile + x.pt) * x.nkc + kc) * kTileBytes;
-            const unsigned char* gb =
-                Bb + ((size_t)(q * x.nntile + x.nt) * x.nkc + kc) * kTileBytes;
             bulk_g2s(sA + q * kTileBytes, ga, kTileBytes, &full[stage]);
-            bulk_g2s(sB + q * kTileBytes, gb, kTileBytes, &full[stage]);
+            if (needB) {
+              const unsigned char* gb =
+                  Bb + ((size_t)(q * x.nntile + x.nt) * x.nkc + kc) * kTileBytes;
+              bulk_g2s(sB + q * kTileBytes, gb, kTileBytes, &full[stage]);
+            }
           }
+          bkey[stage] = key;
           used[stage] = true;
           last_phase[stage] = phase;
           if (++stage == NSTAGE) {
