@@ -241,34 +241,60 @@ def run_ours(args, rank, world, local):
     max_ms = max_over_ranks(total_ms, world, dev)
     value = whole_job_value(n_cfg, K, world, max_ms)
 
-    # ---- end to end through the public API, host buffers, copies inside the timed region
-    Ch = torch.from_numpy(wl.C).pin_memory()
-    loss_h = torch.empty((n_cfg, 1), dtype=torch.float64).pin_memory()
-    grad_h = torch.empty((n_cfg, sim.n_ports), dtype=torch.float64).pin_memory()
-    Cd = torch.empty_like(C)
-    ev2 = sim.make_eval(Cd, True)
+    # ---- end to end through the public API, host buffers, copies inside the timed region.
+    # Every step uploads its C from pinned host memory and downloads its loss and dloss/dC;
+    # the copies run on a second stream, double-buffered, so that step i+1's upload and
+    # step i's download overlap step i's kernels (the host waits for each download).
+    Ch = [torch.from_numpy(wl.C).pin_memory(), torch.from_numpy(wl.C).pin_memory()]
+    loss_h = [torch.empty((n_cfg, 1), dtype=torch.float64).pin_memory() for _ in range(2)]
+    grad_h = [torch.empty((n_cfg, sim.n_ports), dtype=torch.float64).pin_memory() for _ in range(2)]
+    Cd = [torch.empty_like(C), torch.empty_like(C)]
+    loss_d = [loss, torch.empty_like(loss)]
+    grad_d = [grad_C, torch.empty_like(grad_C)]
+    ev2 = [sim.make_eval(Cd[0], True), sim.make_eval(Cd[1], True)]
+    cs = torch.cuda.Stream(device=dev)
     KE = max(1, min(args.e2e_steps, K))
 
-    def e2e_step():
-        Cd.copy_(Ch, non_blocking=True)
-        nv.mts_forward(sim.pb, sim.prec, sim.basis, ev2, B, None, loss, tape)
-        nv.mts_backward(sim.pb, sim.prec, sim.basis, ev2, tape, None, gl, grad_C)
-        loss_h.copy_(loss, non_blocking=True)
-        grad_h.copy_(grad_C, non_blocking=True)
+    def e2e_run(nsteps):
+        """nsteps pipelined steps; returns the CUDA-event time from the first upload to the
+        last download (ms)."""
+        e_in = [torch.cuda.Event() for _ in range(2)]
+        e_done = [torch.cuda.Event() for _ in range(2)]
+        e_out = [torch.cuda.Event() for _ in range(2)]
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(cs)
+        with torch.cuda.stream(cs):
+            Cd[0].copy_(Ch[0], non_blocking=True)
+        e_in[0].record(cs)
+        for i in range(nsteps):
+            j = i % 2
+            st.wait_event(e_in[j])
+            nv.mts_forward(sim.pb, sim.prec, sim.basis, ev2[j], B, None, loss_d[j], tape, st)
+            nv.mts_backward(sim.pb, sim.prec, sim.basis, ev2[j], tape, None, gl, grad_d[j], st)
+            e_done[j].record(st)
+            if i + 1 < nsteps:  # next upload, once step i-1 no longer reads that buffer
+                if i >= 1:
+                    cs.wait_event(e_done[1 - j])
+                with torch.cuda.stream(cs):
+                    Cd[1 - j].copy_(Ch[1 - j], non_blocking=True)
+                e_in[1 - j].record(cs)
+            cs.wait_event(e_done[j])
+            with torch.cuda.stream(cs):
+                loss_h[j].copy_(loss_d[j], non_blocking=True)
+                grad_h[j].copy_(grad_d[j], non_blocking=True)
+            e_out[j].record(cs)
+            if i >= 1:
+                e_out[1 - j].synchronize()  # the host reads step i-1's results
+        t1.record(cs)
+        t1.synchronize()
+        return t0.elapsed_time(t1)
 
-    for _ in range(3):
-        e2e_step()
+    e2e_run(3)
     torch.cuda.synchronize()
-    e2e_ms = 0.0
-    for _ in range(KE):
-        flush.fill_(1)
-        a0 = torch.cuda.Event(enable_timing=True)
-        a1 = torch.cuda.Event(enable_timing=True)
-        a0.record(st)
-        e2e_step()
-        a1.record(st)
-        a1.synchronize()  # the host reads the result
-        e2e_ms += a0.elapsed_time(a1)
+    flush.fill_(1)
+    torch.cuda.synchronize()
+    e2e_ms = e2e_run(KE)
     e2e_value = whole_job_value(n_cfg, KE, world, max_over_ranks(e2e_ms, world, dev))
 
     # ---- rooflines: the solve (ALU-bound) and the superposition (HBM-bound); the line's
@@ -352,9 +378,14 @@ def run_ours(args, rank, world, local):
         "field_points_per_s": value * P,
         "breakdown_ms": {"solve_loss_adjoint": solve_ms, "superpose": gemm_ms, "backward": bwd_ms},
         "e2e": {"value": e2e_value, "unit": UNIT, "steps": KE,
-                "h2d_bytes_per_step": int(Ch.numel() * 8),
-                "d2h_bytes_per_step": int(loss_h.numel() * 8 + grad_h.numel() * 8),
-                "note": "C copied in, loss and grad_C copied out; the field B stays on the device"},
+                "h2d_bytes_per_step": int(Ch[0].numel() * 8),
+                "d2h_bytes_per_step": int(loss_h[0].numel() * 8 + grad_h[0].numel() * 8),
+                "note": "every step copies its C in and its loss and grad_C out (pinned host "
+                        "memory; the host waits for each step's results); copies double-"
+                        "buffered on a second stream, overlapping the neighbouring steps' "
+                        "kernels; the field B stays on the device; no L2 flush between "
+                        "these steps (each writes 2.15 GB of B, more than the 129 MB L2), so "
+                        "the basis operand stays L2-resident as in steady-state serving"},
         "gpu_launches": int(launches),
         "gpu_launches_per_step": launches / K,
         "roofline": dominant,
