@@ -71,6 +71,7 @@ BasisLayout basis_layout(const mts_problem* pb, mts_precision prec) {
   b.H = o; o += align256((size_t)b.h_elem * ps.sumPN);
   b.Hloss64 = o; o += align256(sizeof(double) * ps.sumLN);
   b.Hloss32 = o; o += align256(sizeof(float) * ps.sumLN);
+  b.HlossT32 = o; o += align256(sizeof(float) * ps.sumLN);
   b.M32hi = o; o += align256(sizeof(float) * ps.sumNN);
   b.M32lo = o; o += align256(sizeof(float) * ps.sumNN);
   b.Aop = o; o += align256(2 * (size_t)ps.sumAop);
@@ -225,6 +226,7 @@ static SolveArgs solve_args(const mts_problem* pb, mts_precision prec, const voi
   a.M32lo = reinterpret_cast<const float*>(B + bl.M32lo);
   a.Hl64 = reinterpret_cast<const double*>(B + bl.Hloss64);
   a.Hl32 = reinterpret_cast<const float*>(B + bl.Hloss32);
+  a.HlT32 = reinterpret_cast<const float*>(B + bl.HlossT32);
   a.n_cfg = ev->n_cfg;
   a.C = ev->C;
   a.omega = ev->omega;

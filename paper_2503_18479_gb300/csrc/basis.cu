@@ -525,7 +525,8 @@ __global__ void hloss_kernel(int n_struct, int n_loss, const int32_t* __restrict
                              const int64_t* __restrict__ point_off,
                              const int64_t* __restrict__ pn_off,
                              const int64_t* __restrict__ ln_off, const HT* __restrict__ H,
-                             double* __restrict__ Hl64, float* __restrict__ Hl32) {
+                             double* __restrict__ Hl64, float* __restrict__ Hl32,
+                             float* __restrict__ HlT32) {
   int l = blockIdx.x;
   if (l >= n_loss) return;
   int s = find_struct_i32(loss_off, n_struct, l);
@@ -536,6 +537,7 @@ __global__ void hloss_kernel(int n_struct, int n_loss, const int32_t* __restrict
     double h = (double)H[pn_off[s] + lp * N + k];
     Hl64[ln_off[s] + (int64_t)ll * N + k] = h;
     Hl32[ln_off[s] + (int64_t)ll * N + k] = (float)h;
+    HlT32[ln_off[s] + (int64_t)k * (loss_off[s + 1] - loss_off[s]) + ll] = (float)h;
   }
 }
 
@@ -683,12 +685,12 @@ cudaError_t launch_build_basis(const mts_problem* pb, mts_precision prec, void* 
       hloss_kernel<double><<<pb->n_loss, 128, 0, st>>>(
           pb->n_struct, pb->n_loss, pb->loss_off, pb->loss_idx, pb->port_off, pb->point_off,
           t.pn_off, t.ln_off, (const double*)(B + bl.H), (double*)(B + bl.Hloss64),
-          (float*)(B + bl.Hloss32));
+          (float*)(B + bl.Hloss32), (float*)(B + bl.HlossT32));
     else
       hloss_kernel<float><<<pb->n_loss, 128, 0, st>>>(
           pb->n_struct, pb->n_loss, pb->loss_off, pb->loss_idx, pb->port_off, pb->point_off,
           t.pn_off, t.ln_off, (const float*)(B + bl.H), (double*)(B + bl.Hloss64),
-          (float*)(B + bl.Hloss32));
+          (float*)(B + bl.Hloss32), (float*)(B + bl.HlossT32));
     note_launch();
   }
   e = cudaGetLastError();

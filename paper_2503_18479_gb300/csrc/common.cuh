@@ -10,6 +10,8 @@
 //              multiple of 32 elements: field basis, points x loops
 //   Hloss64    FP64 [sum_s L_s N_s]             rows of H at the loss points
 //   Hloss32    FP32 [sum_s L_s N_s]
+//   HlossT32   FP32 [sum_s N_s L_s]              the same rows transposed (k-major), for
+//                                                coalesced loads with one loss point per lane
 //   M32hi/lo   FP32 [sum_s N_s^2]               M = hi + lo (double-float split)
 //   Aop        bf16 tensor-core operand of H (MTS_MIXED: 3 pieces, MTS_BF16: 1),
 //              per structure [piece][p_tile][k_chunk][128 rows x 64 k] in the
@@ -96,7 +98,7 @@ struct ProblemSums {
 };
 
 struct BasisLayout {
-  size_t tables = 0, M64 = 0, H = 0, Hloss64 = 0, Hloss32 = 0, M32hi = 0, M32lo = 0, Aop = 0,
+  size_t tables = 0, M64 = 0, H = 0, Hloss64 = 0, Hloss32 = 0, HlossT32 = 0, M32hi = 0, M32lo = 0, Aop = 0,
          status = 0, total = 0;
   int h_elem = 8;
 };

@@ -20,6 +20,7 @@ struct SolveArgs {
   const float* M32lo;
   const double* Hl64;
   const float* Hl32;
+  const float* HlT32;  // Hl32 transposed per structure: [N_s][L_s]
   int64_t n_cfg;
   const double* C;
   const double* omega;

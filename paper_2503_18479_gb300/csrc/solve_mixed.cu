@@ -643,6 +643,7 @@ __global__ void __launch_bounds__(NM >= 64 ? NM : 128, NM >= 64 ? 5 : 1) solve_m
         publish(x);
         const int L = a.loss_off[si.s + 1] - a.loss_off[si.s];
         const float* Hl = a.Hl32 + a.t.ln_off[si.s];
+        const float* HlT = a.HlT32 + a.t.ln_off[si.s];  // [k][l]: lanes l read consecutively
         const int tw = a.loss_mode == 0 ? 1 : 2;
         const double* tb = a.target + (a.target_per_cfg ? si.b * a.sumFL * tw : 0) +
                            (a.t.fl_off[si.s] + (int64_t)si.f * L) * tw;
@@ -656,12 +657,12 @@ __global__ void __launch_bounds__(NM >= 64 ? NM : 128, NM >= 64 ? 5 : 1) solve_m
             u64 b0 = 0ull, b1 = 0ull;
             int k = 0;
             for (; k + 1 < N; k += 2) {
-              const float h0 = Hl[(int64_t)l * N + k], h1 = Hl[(int64_t)l * N + k + 1];
+              const float h0 = HlT[(int64_t)k * L + l], h1 = HlT[(int64_t)(k + 1) * L + l];
               b0 = ffma2(pk(h0, h0), sm.xhl[k].x, b0);
               b1 = ffma2(pk(h1, h1), sm.xhl[k + 1].x, b1);
             }
             if (k < N) {
-              const float h0 = Hl[(int64_t)l * N + k];
+              const float h0 = HlT[(int64_t)k * L + l];
               b0 = ffma2(pk(h0, h0), sm.xhl[k].x, b0);
             }
             float2 bl = make_float2(up(b0).x + up(b1).x, up(b0).y + up(b1).y);
