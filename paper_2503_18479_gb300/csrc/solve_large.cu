@@ -585,6 +585,7 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
       float2* Gh = reinterpret_cast<float2*>(dsm + L.pan);  // conj(G) = hi + lo (FP32)
       float2* Glo = Gh + T;
       const float* __restrict__ Hl32 = a.Hl32 + a.t.ln_off[si.s];
+      const float* __restrict__ HlT32 = a.HlT32 + a.t.ln_off[si.s];  // [k][l]
       double lsum = 0.0;
       for (int r = tid; r < N; r += T) rhs[r] = {0.0, 0.0};
       if constexpr (kF) {  // currents as hi + lo floats for the double-float sums below
@@ -606,7 +607,7 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
             float hx = 0.f, lx = 0.f, hy = 0.f, ly = 0.f;
 #pragma unroll 4
             for (int k = 0; k < N; ++k) {
-              const float h = Hl32[(int64_t)l * N + k];
+              const float h = HlT32[(int64_t)k * Ls + l];  // lanes l read consecutively
               lg_df_acc(hx, lx, h, xh[k].x);
               lg_df_acc(hy, ly, h, xh[k].y);
               lx = fmaf(h, xl[k].x, lx);
