@@ -45,6 +45,14 @@ __device__ inline Cx<R> cx_div(Cx<R> a, Cx<R> b) {
   const R d = b.x * b.x + b.y * b.y;
   return {(a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d};
 }
+// FP32 factors: a / b through the hardware approximate reciprocal of |b|^2 (<= 1 ulp; the
+// rounding is removed by refinement), off the IEEE division's slow path
+template <>
+__device__ inline Cx<float> cx_div<float>(Cx<float> a, Cx<float> b) {
+  float inv;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(b.x * b.x + b.y * b.y));
+  return {(a.x * b.x + a.y * b.y) * inv, (a.y * b.x - a.x * b.y) * inv};
+}
 // v -= l * u
 template <typename R>
 __device__ inline void cx_fnma(Cx<R>& v, Cx<R> l, Cx<R> u) {
