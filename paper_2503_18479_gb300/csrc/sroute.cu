@@ -92,6 +92,13 @@ __device__ inline V sr_recip(V a) {
   r.y = -a.y / d;
   return r;
 }
+// FP32 factors: the hardware approximate reciprocal (<= 1 ulp; refinement removes it)
+template <>
+__device__ inline float2 sr_recip<float2>(float2 a) {
+  float inv;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(a.x * a.x + a.y * a.y));
+  return make_float2(a.x * inv, -a.y * inv);
+}
 template <typename V>
 __device__ inline V sr_sub(V a, V b) {
   a.x -= b.x;
