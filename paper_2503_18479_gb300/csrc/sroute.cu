@@ -252,49 +252,109 @@ __device__ int sr_factor(int n, typename SrT<LT>::V* a, int* perm, int* s_int) {
   return bad;
 }
 
-// x <- U^-1 L^-1 x for the n1 columns of x ([n][n1]; x already row-permuted by P).
+// Triangular sweeps with the factors of sr_factor, one warp per right-hand-side column (n1
+// columns, warps take columns w, w + 4, ...): lane l holds the unknowns of rows l, l + 32,
+// l + 64 in registers; the unknown of step k is broadcast from its lane by a shuffle, so a
+// sweep needs no CTA barrier (one at the end publishes x).
 template <typename V>
-__device__ void sr_solve_lu(int n, int n1, const V* a, V* x) {
-  const int tid = threadIdx.x;
-  for (int k = 0; k + 1 < n; ++k) {
-    for (int i = k + 1 + tid; i < n; i += kSrThreads) {
-      const V lik = a[i * n + k];
-      for (int c = 0; c < n1; ++c) x[i * n1 + c] = sr_sub(x[i * n1 + c], sr_mul(lik, x[k * n1 + c]));
-    }
-    __syncthreads();
-  }
-  for (int k = n - 1; k >= 0; --k) {
-    if (tid < n1) x[k * n1 + tid] = sr_mul(x[k * n1 + tid], sr_recip(a[k * n + k]));
-    __syncthreads();
-    for (int i = tid; i < k; i += kSrThreads) {
-      const V uik = a[i * n + k];
-      for (int c = 0; c < n1; ++c) x[i * n1 + c] = sr_sub(x[i * n1 + c], sr_mul(uik, x[k * n1 + c]));
-    }
-    __syncthreads();
-  }
+__device__ inline V sr_bcast(V v, int src) {
+  V r;
+  r.x = __shfl_sync(0xffffffffu, v.x, src);
+  r.y = __shfl_sync(0xffffffffu, v.y, src);
+  return r;
 }
 
-// x <- (U^H)^-1 ... then (L^H)^-1: with P A = L U, A^H = U^H L^H P, so A^H z = g is
-// z = P^T (L^H)^-1 (U^H)^-1 g; the caller applies P^T (z[perm[i]] = x[i]).
+// x <- U^-1 L^-1 x for the n1 columns of x ([n][n1]; x already row-permuted by P), n <= 96.
+template <typename V>
+__device__ void sr_solve_lu(int n, int n1, const V* a, V* x) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c = warp; c < n1; c += kSrWarps) {
+    V v[3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      const int i = lane + 32 * s;
+      v[s] = i < n ? x[i * n1 + c] : V{0, 0};
+    }
+    for (int k = 0; k + 1 < n; ++k) {  // L y = P b (unit diagonal)
+      const int ks = k >> 5;
+      const V mine = ks == 0 ? v[0] : (ks == 1 ? v[1] : v[2]);
+      const V xk = sr_bcast(mine, k & 31);
+#pragma unroll
+      for (int s = 0; s < 3; ++s) {
+        const int i = lane + 32 * s;
+        if (i > k && i < n) v[s] = sr_sub(v[s], sr_mul(a[i * n + k], xk));
+      }
+    }
+    for (int k = n - 1; k >= 0; --k) {  // U x = y
+      const int ks = k >> 5;
+      if (lane == (k & 31)) {
+        const V d = sr_recip(a[k * n + k]);
+        if (ks == 0) v[0] = sr_mul(v[0], d);
+        else if (ks == 1) v[1] = sr_mul(v[1], d);
+        else v[2] = sr_mul(v[2], d);
+      }
+      const V mine = ks == 0 ? v[0] : (ks == 1 ? v[1] : v[2]);
+      const V xk = sr_bcast(mine, k & 31);
+#pragma unroll
+      for (int s = 0; s < 3; ++s) {
+        const int i = lane + 32 * s;
+        if (i < k) v[s] = sr_sub(v[s], sr_mul(a[i * n + k], xk));
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      const int i = lane + 32 * s;
+      if (i < n) x[i * n1 + c] = v[s];
+    }
+  }
+  __syncthreads();
+}
+
+// With P A = L U, A^H = U^H L^H P, so A^H z = g is z = P^T (L^H)^-1 (U^H)^-1 g; this applies
+// (L^H)^-1 (U^H)^-1 and the caller applies P^T (z[perm[i]] = x[i]).
 template <typename V>
 __device__ void sr_solve_lu_h(int n, int n1, const V* a, V* x) {
-  const int tid = threadIdx.x;
-  for (int k = 0; k < n; ++k) {
-    if (tid < n1) x[k * n1 + tid] = sr_mul(x[k * n1 + tid], sr_recip(sr_conj(a[k * n + k])));
-    __syncthreads();
-    for (int i = k + 1 + tid; i < n; i += kSrThreads) {
-      const V uki = sr_conj(a[k * n + i]);
-      for (int c = 0; c < n1; ++c) x[i * n1 + c] = sr_sub(x[i * n1 + c], sr_mul(uki, x[k * n1 + c]));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c = warp; c < n1; c += kSrWarps) {
+    V v[3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      const int i = lane + 32 * s;
+      v[s] = i < n ? x[i * n1 + c] : V{0, 0};
     }
-    __syncthreads();
-  }
-  for (int k = n - 1; k > 0; --k) {
-    for (int i = tid; i < k; i += kSrThreads) {
-      const V lki = sr_conj(a[k * n + i]);
-      for (int c = 0; c < n1; ++c) x[i * n1 + c] = sr_sub(x[i * n1 + c], sr_mul(lki, x[k * n1 + c]));
+    for (int k = 0; k < n; ++k) {  // U^H t = g: row i of U^H is conj(column i of U)
+      const int ks = k >> 5;
+      if (lane == (k & 31)) {
+        const V d = sr_recip(sr_conj(a[k * n + k]));
+        if (ks == 0) v[0] = sr_mul(v[0], d);
+        else if (ks == 1) v[1] = sr_mul(v[1], d);
+        else v[2] = sr_mul(v[2], d);
+      }
+      const V mine = ks == 0 ? v[0] : (ks == 1 ? v[1] : v[2]);
+      const V xk = sr_bcast(mine, k & 31);
+#pragma unroll
+      for (int s = 0; s < 3; ++s) {
+        const int i = lane + 32 * s;
+        if (i > k && i < n) v[s] = sr_sub(v[s], sr_mul(sr_conj(a[k * n + i]), xk));
+      }
     }
-    __syncthreads();
+    for (int k = n - 1; k > 0; --k) {  // L^H s = t (unit diagonal)
+      const int ks = k >> 5;
+      const V mine = ks == 0 ? v[0] : (ks == 1 ? v[1] : v[2]);
+      const V xk = sr_bcast(mine, k & 31);
+#pragma unroll
+      for (int s = 0; s < 3; ++s) {
+        const int i = lane + 32 * s;
+        if (i < k) v[s] = sr_sub(v[s], sr_mul(sr_conj(a[k * n + i]), xk));
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      const int i = lane + 32 * s;
+      if (i < n) x[i * n1 + c] = v[s];
+    }
   }
+  __syncthreads();
 }
 
 // objective term of one point and its field derivative (mode 0: (|b| - t)^2,
