@@ -293,3 +293,19 @@ def test_sroute_validation(nv):
     assert L.mts_rc_reflection(2, 1, 3, FAKE, None, FAKE, 50.0, 2, 0, FAKE, None) == nv.MTS_EINVAL
     assert L.mts_rc_reflection_vjp(2, 1, 3, FAKE, None, FAKE, 50.0, 4, 2, FAKE, None, FAKE, None) == nv.MTS_EINVAL
     assert nv.mts_launch_count() == 0
+
+
+def test_system_status_validation(nv):
+    """mts_system_status checks its arguments before touching the device; zero
+    configurations is a no-op."""
+    L = nv.lib()
+    wl = W.array_8x8(n_cfg=2, grid=8, planes=(0.02,))
+    c, keep = fake_problem(nv, wl)
+    assert L.mts_system_status(ct.byref(c), 2, nv.MTS_MIXED, None, ct.c_void_p(FAKE), None) == nv.MTS_EINVAL
+    assert L.mts_system_status(ct.byref(c), 2, nv.MTS_MIXED, ct.c_void_p(FAKE), None, None) == nv.MTS_EINVAL
+    assert L.mts_system_status(ct.byref(c), -1, nv.MTS_MIXED, ct.c_void_p(FAKE), ct.c_void_p(FAKE), None) == nv.MTS_EINVAL
+    assert L.mts_system_status(ct.byref(c), 2, 7, ct.c_void_p(FAKE), ct.c_void_p(FAKE), None) == nv.MTS_EINVAL
+    assert L.mts_system_status(ct.byref(c), 0, nv.MTS_MIXED, ct.c_void_p(FAKE), ct.c_void_p(FAKE), None) == nv.MTS_OK
+    cb, kb = fake_problem(nv, wl, n_struct=0)
+    assert L.mts_system_status(ct.byref(cb), 2, nv.MTS_MIXED, ct.c_void_p(FAKE), ct.c_void_p(FAKE), None) == nv.MTS_EINVAL
+    assert nv.mts_launch_count() == 0
