@@ -133,6 +133,20 @@ __device__ inline double sr_block_max(double v, double* red) {
   return r;
 }
 
+// the same over FP32 values (convergence norms: a rough magnitude is all they need)
+__device__ inline float sr_block_maxf(float v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)v;
+  __syncthreads();
+  float r = (float)red[0];
+  for (int w = 1; w < kSrWarps; ++w) r = fmaxf(r, (float)red[w]);
+  return r;
+}
+
+// |re| + |im| of a complex FP64 value, as FP32 (one FP64 add)
+__device__ inline float sr_mag1(double2 v) { return (float)(fabs(v.x) + fabs(v.y)); }
+
 __device__ inline double sr_block_sum(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   __syncthreads();
@@ -493,12 +507,12 @@ __global__ void __launch_bounds__(kSrThreads) sr_solve_kernel(SrArgs a) {
   for (int e = tid; e < nn1; e += kSrThreads) x[e] = sr_from<V>(rhs[perm[e / n1] * n1 + e % n1]);
   __syncthreads();
   sr_solve_lu(n, n1, lu, x);
-  double loc = 0.0;
+  float loc = 0.0f;
   for (int e = tid; e < nn1; e += kSrThreads) {
     w[e] = sr_to64(x[e]);
-    loc = fmax(loc, hypot(w[e].x, w[e].y));
+    loc = fmaxf(loc, sr_mag1(w[e]));
   }
-  double dprev = sr_block_max(loc, red);
+  float dprev = sr_block_maxf(loc, red);
   int converged = a.max_refine == 0;
   for (int it = 0; it < a.max_refine; ++it) {
     // residual in FP64 (double-float for FP32 factors): r = S12 - A w,
@@ -538,16 +552,16 @@ __global__ void __launch_bounds__(kSrThreads) sr_solve_kernel(SrArgs a) {
     for (int e = tid; e < nn1; e += kSrThreads) x[e] = sr_from<V>(r[perm[e / n1] * n1 + e % n1]);
     __syncthreads();
     sr_solve_lu(n, n1, lu, x);
-    double dl = 0.0, wl = 0.0;
+    float dl = 0.0f, wl = 0.0f;
     for (int e = tid; e < nn1; e += kSrThreads) {
       const double2 d = sr_to64(x[e]);
       w[e] = sr_add(w[e], d);
-      dl = fmax(dl, hypot(d.x, d.y));
-      wl = fmax(wl, hypot(w[e].x, w[e].y));
+      dl = fmaxf(dl, sr_mag1(d));
+      wl = fmaxf(wl, sr_mag1(w[e]));
     }
-    const double dn = sr_block_max(dl, red);
-    const double wn = sr_block_max(wl, red);
-    const double est = dn == 0.0 ? 0.0 : dn * dn / dprev / wn;
+    const float dn = sr_block_maxf(dl, red);
+    const float wn = sr_block_maxf(wl, red);
+    const double est = dn == 0.0f ? 0.0 : (double)dn * dn / dprev / wn;
     if (est <= a.tol) {
       converged = 1;
       break;
@@ -751,14 +765,14 @@ __global__ void __launch_bounds__(kSrThreads) sr_adjoint_kernel(SrArgs a) {
   for (int e = tid; e < nn1; e += kSrThreads) x[e] = sr_from<V>(gw[e]);
   __syncthreads();
   sr_solve_lu_h(n, n1, lu, x);
-  double loc = 0.0;
+  float loc = 0.0f;
   for (int e = tid; e < nn1; e += kSrThreads) {
     const int i = e / n1, c = e % n1;
     const double2 v = sr_to64(x[e]);
     lam[perm[i] * n1 + c] = v;
-    loc = fmax(loc, hypot(v.x, v.y));
+    loc = fmaxf(loc, sr_mag1(v));
   }
-  double dprev = sr_block_max(loc, red);
+  float dprev = sr_block_maxf(loc, red);
   int converged = a.max_refine == 0;
   for (int it = 0; it < a.max_refine; ++it) {
     // r = g_W - A^H lam,  A^H lam = lam - T^H lam - S0^H y,  y = sum_q conj(v_q) e_col lam[row]
@@ -794,19 +808,19 @@ __global__ void __launch_bounds__(kSrThreads) sr_adjoint_kernel(SrArgs a) {
     for (int e = tid; e < nn1; e += kSrThreads) x[e] = sr_from<V>(r[e]);
     __syncthreads();
     sr_solve_lu_h(n, n1, lu, x);
-    double dl = 0.0, ll = 0.0;
+    float dl = 0.0f, ll = 0.0f;
     for (int e = tid; e < nn1; e += kSrThreads) {
       const int i = e / n1, c = e % n1;
       const double2 d = sr_to64(x[e]);
       const int t = perm[i] * n1 + c;
       lam[t] = sr_add(lam[t], d);
-      dl = fmax(dl, hypot(d.x, d.y));
+      dl = fmaxf(dl, sr_mag1(d));
     }
     __syncthreads();
-    for (int e = tid; e < nn1; e += kSrThreads) ll = fmax(ll, hypot(lam[e].x, lam[e].y));
-    const double dn = sr_block_max(dl, red);
-    const double ln = sr_block_max(ll, red);
-    const double est = dn == 0.0 ? 0.0 : dn * dn / dprev / ln;
+    for (int e = tid; e < nn1; e += kSrThreads) ll = fmaxf(ll, sr_mag1(lam[e]));
+    const float dn = sr_block_maxf(dl, red);
+    const float ln = sr_block_maxf(ll, red);
+    const double est = dn == 0.0f ? 0.0 : (double)dn * dn / dprev / ln;
     if (est <= a.tol) {
       converged = 1;
       break;
