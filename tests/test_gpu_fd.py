@@ -1,12 +1,13 @@
 """The adjoint gradient of the CUDA path against central finite differences of the CUDA
 path's own objective (MTS_FP64, so that the difference quotient is not lost in rounding),
 h = 1e-3 pF as the paper-shaped workloads prescribe, on 16 capacitors; and systems with a
-non-finite capacitance are flagged without disturbing the others."""
+non-finite capacitance, or too ill-conditioned for FP32 factors to converge, are flagged
+without disturbing the others."""
 import numpy as np
 import pytest
 import torch
 
-from helpers import small_8x8, small_rect
+from helpers import small_8x8, small_rect, structure_basis
 from paper_2503_18479_gb300 import build_lib
 from paper_2503_18479_gb300 import workloads as W
 
@@ -77,3 +78,46 @@ def test_non_finite_capacitance_is_flagged(prec):
     keep = [b for b in range(8) if b != 3]
     assert torch.equal(out["B"][keep], ref["B"][keep])
     assert torch.equal(out["loss"][keep], ref["loss"][keep])
+
+
+@pytest.mark.parametrize("prec", ["mixed", "bf16"])
+@pytest.mark.parametrize("shape", [(4, 4), (8, 8), (9, 8)])
+def test_unconverged_system_is_flagged(prec, shape):
+    """A configuration tuned so that A = R + jwM + 1/(jwC) has an eigenvalue of about R =
+    1e-9 ohm (every C at 1/(w^2 mu), mu the smallest eigenvalue of M; condition number about
+    3e10) cannot be solved from FP32 factors: rounding A to FP32 moves that eigenvalue by
+    about 1e-6 ohm, so each refinement correction is as large as the last and the system
+    must report status 1 (missed the tolerance) at that frequency only. Covers the
+    register kernels for 16 and 64 ports and the blocked kernel for 72; the other systems
+    (condition numbers below 1e3) keep status 0 and bit-identical results."""
+    import dataclasses
+    from paper_2503_18479_gb300 import native as nv
+    from paper_2503_18479_gb300.simulator import Simulator
+    nx, ny = shape
+    wl = small_rect(nx, ny, n_cfg=6)
+    st = dataclasses.replace(wl.structures[0], R=np.full(wl.structures[0].n_ports, 1e-9))
+    wl = dataclasses.replace(wl, structures=[st])
+    _, M = structure_basis(wl, 0)  # the oracle's inductances choose the planted input
+    w0 = float(st.omega[0])
+    C0 = 1.0 / (w0 * w0 * float(np.linalg.eigvalsh(M)[0]))
+    sim = Simulator(wl, prec)
+    C = torch.from_numpy(wl.C).cuda()
+    ref = sim.forward(C)
+    bad_cfg = 2
+    Cbad = C.clone()
+    Cbad[bad_cfg, :] = C0
+    out = sim.forward(Cbad)
+    code, n_bad = sim.status(out["tape"], wl.n_cfg)
+    assert code == nv.MTS_ENOCONV and n_bad == 1, (code, n_bad)
+    words = torch.full((wl.n_cfg, sim.omega.numel()), -1, dtype=torch.int32, device="cuda")
+    nv.mts_system_status(sim.pb, wl.n_cfg, sim.prec, out["tape"], words)
+    w = words.cpu().numpy()
+    want = np.zeros_like(w)
+    want[bad_cfg, 0] = 1
+    assert np.array_equal(w, want), w
+    code_ref, n_ref = sim.status(ref["tape"], wl.n_cfg)
+    assert code_ref == nv.MTS_OK and n_ref == 0
+    keep = [b for b in range(wl.n_cfg) if b != bad_cfg]
+    assert torch.equal(out["B"][keep], ref["B"][keep])
+    assert torch.equal(out["loss"][keep], ref["loss"][keep])
+    assert torch.isfinite(out["B"][bad_cfg]).all()  # results are written either way

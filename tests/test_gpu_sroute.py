@@ -4,7 +4,7 @@ a general network (variable S11 diagonal and off-diagonal entries, S12, S21 and 
 a nonzero S_C,const) on several point tiles with a ragged tail and enough configurations for
 the tensor-core superposition; the synthetic 8x8-plus-drive workload with series RC loads
 (Eq. 2-3 on the GPU, gradient with respect to C through its vector-Jacobian product); a field
-cotangent; the size limits.
+cotangent; the size limits; a system too ill-conditioned for FP32 factors is flagged.
 
 Tolerances: MTS_FP64 1e-10; MTS_MIXED 1e-6 on Bcomb, W, the objective and dL/dsvar;
 MTS_BF16 1e-2 on Bcomb."""
@@ -181,3 +181,39 @@ def test_enhancement_objective(prec):
     g = sr.backward(out, grad_loss=torch.ones(c["svar"].shape[0], dtype=torch.float64, device="cuda"))
     assert rel(out["loss"].cpu().numpy(), ref["loss"]) < TOL[prec]
     assert rel(g.cpu().numpy(), gref) < TOL[prec], rel(g.cpu().numpy(), gref)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "bf16"])
+def test_unconverged_system_is_flagged(prec):
+    """One S11 diagonal entry of one (configuration, frequency) moved to s*(1 + 1e-9), where
+    A(s) = 1 - S11(s) S0 (a rank-one function of s) is singular at s*: condition number
+    about 6e9, far beyond what FP32 factors can refine (rounding A to FP32 moves its smallest
+    singular value by about 1e-7 of the norm, so successive corrections stay the same
+    size). The status reader must count exactly that system; every other system keeps
+    bit-identical W, Bcomb and objective."""
+    from paper_2503_18479_gb300 import native as nv
+    c = _general()
+    S0, sc, rows, cols = c["S0"], c["sc"], c["rows"], c["cols"]
+    n0 = S0.shape[1]
+    b, f = 5, 0
+    k0 = int(np.nonzero((rows == 0) & (cols == 0))[0][0])
+    S = sc[f].copy()
+    S[rows, cols] += c["svar"][b, f]
+    A = np.eye(n0) - S[:n0, :n0] @ S0[f]
+    e0 = np.zeros(n0)
+    e0[0] = 1.0
+    # A(s) = A - (s - s_old) e0 (e0^T S0) is singular where (s - s_old) e0^T S0 A^-1 e0 = 1
+    s_star = c["svar"][b, f, k0] + 1.0 / ((e0 @ S0[f]) @ np.linalg.solve(A, e0))
+    bad = c["svar"].copy()
+    bad[b, f, k0] = s_star * (1.0 + 1e-9)
+    sr = _route(c, prec)
+    n_cfg = c["svar"].shape[0]
+    ref = sr.forward(torch.from_numpy(c["svar"]), want_B=True, want_W=True)
+    assert sr.status(ref["tape"], n_cfg) == (nv.MTS_OK, 0)
+    out = sr.forward(torch.from_numpy(bad), want_B=True, want_W=True)
+    assert sr.status(out["tape"], n_cfg) == (nv.MTS_ENOCONV, 1)
+    keep = [i for i in range(n_cfg) if i != b]
+    for key in ("B", "W", "loss"):
+        assert torch.equal(out[key][keep], ref[key][keep]), key
+    # the planted configuration's other frequencies are separate systems and still converge
+    assert torch.equal(out["W"][b, 1:], ref["W"][b, 1:])
