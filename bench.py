@@ -368,9 +368,12 @@ def run_ours(args, rank, world, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": max_ms / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"mixed": "f32 LU + df64 residual + bf16x3 tensor-core (f32 accum)",
-                  "bf16": "f32 LU + df64 residual + bf16 tensor-core (f32 accum)",
-                  "fp64": "f64"}[prec],
+        "dtype": {"mixed": "f32", "bf16": "f32", "fp64": "f64"}[prec],
+        "dtype_detail": {"mixed": "f32 LU + double-float (f32 pair) residuals + bf16x3 pieces on "
+                                  "the tensor cores with f32 accumulation",
+                         "bf16": "f32 LU + double-float (f32 pair) residuals + bf16 operands on "
+                                 "the tensor cores with f32 accumulation",
+                         "fp64": "f64 throughout"}[prec],
         "data": "synthetic (seeded PCG64 per rank); shapes of the paper's 8x8 metasurface",
         "config": {"workload": WORKLOAD, "n_cfg_per_gpu": n_cfg, "points": P, "ports": 64,
                    "precision": prec, "l2": "flushed between timed steps (256 MB write)",
