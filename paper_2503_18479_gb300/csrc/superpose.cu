@@ -13,41 +13,104 @@
 
 namespace mts {
 
-__global__ void plan_kernel(int n_struct, int64_t n_cfg, const int32_t* __restrict__ port_off,
-                            const int64_t* __restrict__ point_off,
-                            const int32_t* __restrict__ freq_off, int npieces,
-                            int64_t simt_max_sys, int64_t* bop_off, int64_t* unit_off,
-                            int64_t* lu_off, int64_t* simt_off) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  int64_t a = 0, u = 0, f = 0, v = 0;
-  for (int s = 0; s < n_struct; ++s) {
-    bop_off[s] = a;
-    unit_off[s] = u;
-    lu_off[s] = f;
-    simt_off[s] = v;
-    int64_t N = port_off[s + 1] - port_off[s];
-    int64_t P = point_off[s + 1] - point_off[s];
-    int64_t F = freq_off[s + 1] - freq_off[s];
-    // the B operand exists for every structure (the schedule does not change memory)
-    const int64_t nn = (2 * n_cfg * F + kTileN - 1) / kTileN;
-    a += (int64_t)npieces * nn * ((N + kChunkK - 1) / kChunkK) * kTileN * kChunkK;
-    if (use_tensor_path(npieces, n_cfg, F, simt_max_sys)) {
-      u += (P + kTileP - 1) / kTileP * nn;
-    } else {
-      v += (P + kSimtPts - 1) / kSimtPts * ((n_cfg * F + kSimtSys - 1) / kSimtSys);
-    }
-    if (N > kRegMaxPorts) f += F * N * N;
+// Per-structure work of the plan: B-operand elements, tensor-core units, LU scratch
+// elements and SIMT units of structure s.
+struct PlanWork {
+  int64_t a, u, f, v;
+};
+
+__device__ inline PlanWork plan_work(int s, int64_t n_cfg, const int32_t* __restrict__ port_off,
+                                     const int64_t* __restrict__ point_off,
+                                     const int32_t* __restrict__ freq_off, int npieces,
+                                     int64_t simt_max_sys) {
+  const int64_t N = port_off[s + 1] - port_off[s];
+  const int64_t P = point_off[s + 1] - point_off[s];
+  const int64_t F = freq_off[s + 1] - freq_off[s];
+  PlanWork w{0, 0, 0, 0};
+  // the B operand exists for every structure (the schedule does not change memory)
+  const int64_t nn = (2 * n_cfg * F + kTileN - 1) / kTileN;
+  w.a = (int64_t)npieces * nn * ((N + kChunkK - 1) / kChunkK) * kTileN * kChunkK;
+  if (use_tensor_path(npieces, n_cfg, F, simt_max_sys))
+    w.u = (P + kTileP - 1) / kTileP * nn;
+  else
+    w.v = (P + kSimtPts - 1) / kSimtPts * ((n_cfg * F + kSimtSys - 1) / kSimtSys);
+  if (N > kRegMaxPorts) w.f = F * N * N;
+  return w;
+}
+
+// Exclusive prefix sums of the per-structure work, one CTA of kPlanThreads: thread t sums a
+// contiguous run of structures, the runs' totals are scanned across the CTA (warp shuffles,
+// then the warp totals), and each thread writes the offsets of its run. Entry n_struct holds
+// the totals. Integer sums: the same values as a serial scan.
+constexpr int kPlanThreads = 1024;
+
+__device__ inline int64_t plan_warp_incl(int64_t v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += y;
   }
-  bop_off[n_struct] = a;
-  unit_off[n_struct] = u;
-  lu_off[n_struct] = f;
-  simt_off[n_struct] = v;
+  return v;
+}
+
+__global__ void __launch_bounds__(kPlanThreads) plan_kernel(
+    int n_struct, int64_t n_cfg, const int32_t* __restrict__ port_off,
+    const int64_t* __restrict__ point_off, const int32_t* __restrict__ freq_off, int npieces,
+    int64_t simt_max_sys, int64_t* bop_off, int64_t* unit_off, int64_t* lu_off,
+    int64_t* simt_off) {
+  __shared__ int64_t wsum[4][kPlanThreads / 32];
+  const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
+  const int per = (n_struct + kPlanThreads - 1) / kPlanThreads;
+  const int s0 = min(n_struct, t * per), s1 = min(n_struct, s0 + per);
+  int64_t run[4] = {0, 0, 0, 0};
+  for (int s = s0; s < s1; ++s) {
+    const PlanWork w = plan_work(s, n_cfg, port_off, point_off, freq_off, npieces, simt_max_sys);
+    run[0] += w.a;
+    run[1] += w.u;
+    run[2] += w.f;
+    run[3] += w.v;
+  }
+  int64_t excl[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int64_t inc = plan_warp_incl(run[q], lane);
+    excl[q] = inc - run[q];
+    if (lane == 31) wsum[q][wp] = inc;
+  }
+  __syncthreads();
+  if (wp == 0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t v = wsum[q][lane];
+      wsum[q][lane] = plan_warp_incl(v, lane) - v;  // exclusive over the warps
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 4; ++q) excl[q] += wsum[q][wp];
+  for (int s = s0; s < s1; ++s) {
+    bop_off[s] = excl[0];
+    unit_off[s] = excl[1];
+    lu_off[s] = excl[2];
+    simt_off[s] = excl[3];
+    const PlanWork w = plan_work(s, n_cfg, port_off, point_off, freq_off, npieces, simt_max_sys);
+    excl[0] += w.a;
+    excl[1] += w.u;
+    excl[2] += w.f;
+    excl[3] += w.v;
+  }
+  if (t == kPlanThreads - 1) {  // its run ends at n_struct (or is empty past it)
+    bop_off[n_struct] = excl[0];
+    unit_off[n_struct] = excl[1];
+    lu_off[n_struct] = excl[2];
+    simt_off[n_struct] = excl[3];
+  }
 }
 
 cudaError_t launch_plan(const mts_problem* pb, int64_t n_cfg, int npieces, int64_t simt_max_sys,
                         int64_t* bop_off, int64_t* unit_off, int64_t* lu_off, int64_t* simt_off,
                         cudaStream_t st) {
-  plan_kernel<<<1, 32, 0, st>>>(pb->n_struct, n_cfg, pb->port_off, pb->point_off, pb->freq_off,
+  plan_kernel<<<1, kPlanThreads, 0, st>>>(pb->n_struct, n_cfg, pb->port_off, pb->point_off, pb->freq_off,
                                 npieces, simt_max_sys, bop_off, unit_off, lu_off, simt_off);
   note_launch();
   return cudaGetLastError();
