@@ -194,6 +194,22 @@ __global__ void __launch_bounds__(kSimtPts) superpose_simt_kernel(SuperposeArgs 
   const bool live = p < P;
   const T* hrow = static_cast<const T*>(a.H) + a.t.pn_off[s] + (live ? p : 0) * N;
   const bool vec = (N % VEC) == 0;
+  // offsets of the unit's systems in I and in B, one 64-bit division per system (not one per
+  // staged current and per stored value)
+  __shared__ int64_t s_ioff[kSimtSys], s_ooff[kSimtSys];
+  const int64_t fpo = a.t.fp_off[s];
+  if (t < kSimtSys) {
+    int64_t io = 0, oo = 0;
+    if (t < nsv) {
+      const int64_t sl = sys0 + t, b = sl / F;
+      const int f = (int)(sl - b * F);
+      io = 2 * (b * a.sumFN + a.t.fn_off[s] + (int64_t)f * N);
+      oo = b * a.sumFP + fpo + (int64_t)f * P;
+    }
+    s_ioff[t] = io;
+    s_ooff[t] = oo;
+  }
+  __syncthreads();
   T ax[kSimtSys], ay[kSimtSys];
 #pragma unroll
   for (int i = 0; i < kSimtSys; ++i) ax[i] = ay[i] = T(0);
@@ -222,9 +238,7 @@ __global__ void __launch_bounds__(kSimtPts) superpose_simt_kernel(SuperposeArgs 
       const int k = e / kSimtSys, i = e - k * kSimtSys;
       T re = T(0), im = T(0);
       if (i < nsv) {
-        const int64_t sl = sys0 + i, b = sl / F;
-        const int f = (int)(sl - b * F);
-        const double* Ip = a.I + 2 * (b * a.sumFN + a.t.fn_off[s] + (int64_t)f * N + k0 + k);
+        const double* Ip = a.I + s_ioff[i] + 2 * (k0 + k);
         re = (T)Ip[0];
         im = (T)Ip[1];
       }
@@ -238,16 +252,13 @@ __global__ void __launch_bounds__(kSimtPts) superpose_simt_kernel(SuperposeArgs 
   }
   if (live) {
     C2* out = static_cast<C2*>(a.B_out);
-    const int64_t fpo = a.t.fp_off[s];
 #pragma unroll
     for (int i = 0; i < kSimtSys; ++i)
       if (i < nsv) {
-        const int64_t sl = sys0 + i, b = sl / F;
-        const int f = (int)(sl - b * F);
         C2 v;
         v.x = ax[i];
         v.y = ay[i];
-        out[b * a.sumFP + fpo + (int64_t)f * P + p] = v;
+        out[s_ooff[i] + p] = v;
       }
   }
 }
