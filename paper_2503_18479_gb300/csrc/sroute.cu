@@ -373,6 +373,28 @@ __device__ void sr_solve_lu_h(int n, int n1, const V* a, V* x) {
 
 // objective term of one point and its field derivative (mode 0: (|b| - t)^2,
 // G = 2 (|b| - t) b/|b|, 0 at b = 0; mode 1: |b - t|^2, G = 2 (b - t))
+// Objective term alone (forward): the same FP64 arithmetic as sr_point_loss's value.
+__device__ inline double sr_point_value(int mode, double2 b, const double* t) {
+  if (mode == 0) {
+    const double r = hypot(b.x, b.y) - t[0];
+    return r * r;
+  }
+  const double ex = b.x - t[0], ey = b.y - t[1];
+  return ex * ex + ey * ey;
+}
+
+// Cotangent G of the term in FP32 (adjoint with FP32 factors, where the loss-point field it
+// differentiates is itself an FP32 sum), as the impedance route's FP32 kernels take it.
+__device__ inline double2 sr_point_grad_f(int mode, double2 b, const double* t) {
+  const float bx = (float)b.x, by = (float)b.y;
+  if (mode == 0) {
+    const float m = sqrtf(bx * bx + by * by);
+    const float s = m > 0.0f ? 2.0f * (m - (float)t[0]) / m : 0.0f;
+    return make_double2((double)(s * bx), (double)(s * by));
+  }
+  return make_double2(2.0 * (double)(bx - (float)t[0]), 2.0 * (double)(by - (float)t[1]));
+}
+
 __device__ inline double sr_point_loss(int mode, double2 b, const double* t, double2* G) {
   if (mode == 0) {
     const double m = hypot(b.x, b.y);
@@ -615,8 +637,7 @@ __global__ void __launch_bounds__(kSrThreads) sr_solve_kernel(SrArgs a) {
         bl.x *= a.loss_weight[ti];
         bl.y *= a.loss_weight[ti];
       }
-      double2 G;
-      acc += sr_point_loss(a.loss_mode, bl, a.target + ti * tw, &G);
+      acc += sr_point_value(a.loss_mode, bl, a.target + ti * tw);
     }
     acc = sr_block_sum(acc, red);
     if (tid == 0) a.loss_part[g] = acc;
@@ -723,7 +744,8 @@ __global__ void __launch_bounds__(kSrThreads) sr_adjoint_kernel(SrArgs a) {
           bl.y *= wl;
         }
         double2 G;
-        sr_point_loss(a.loss_mode, bl, a.target + ti * tw, &G);
+        if constexpr (kDF) G = sr_point_grad_f(a.loss_mode, bl, a.target + ti * tw);
+        else sr_point_loss(a.loss_mode, bl, a.target + ti * tw, &G);
         Gs[c * kSrLossChunk + (e % lc)] = make_double2(G.x * gl * wl, G.y * gl * wl);
       }
       __syncthreads();
