@@ -75,6 +75,44 @@ MUTANTS = {
     "reflection_derivative_factor": (
         "2.0 * Z0 / ((zl + Z0) * (zl + Z0))", "Z0 / ((zl + Z0) * (zl + Z0))", 0,
         "factor 2 of d Gamma / d Z dropped (Eq. 3 chain rule)"),
+    "basis_polygon_open": (
+        "int32_t w = (v + 1 < b) ? v + 1 : a;", "int32_t w = (v + 1 < b) ? v + 1 : v;", 0,
+        "closing segment of a loop left out of its field"),
+    "inductance_polygon_open": (
+        "int32_t ie = (i + 1 < loop_vtx_off[k + 1]) ? i + 1 : loop_vtx_off[k];",
+        "int32_t ie = (i + 1 < loop_vtx_off[k + 1]) ? i + 1 : i;", 0,
+        "closing segment of a loop left out of its inductances"),
+    "gauss_legendre_weight": (
+        "w[i] = 2.0 / ((1.0 - z * z) * dp * dp);", "w[i] = 1.0 / ((1.0 - z * z) * dp * dp);", 0,
+        "Gauss-Legendre weights off by a factor 2"),
+    "oblique_direction_cosine_dropped": (
+        "* cosang * 0.5 * (l1 / m) * acc", "* 0.5 * (l1 / m) * acc", 0,
+        "u1.u2 dropped from the oblique Neumann integral"),
+    "inner_integral_sign": (
+        "return log((R1 + a) * (R0 + t0) / rho2);", "return log((R1 + a) * (R0 - t0) / rho2);", 0,
+        "sign error in the rewritten inner integral of the oblique pair"),
+    "dloss_dr_sign": (
+        "gR[b * N + k] += -creal(mu[k] * x[k]);", "gR[b * N + k] += creal(mu[k] * x[k]);", 0,
+        "dloss/dR with the wrong sign"),
+    "dloss_dl_omega_dropped": (
+        "gL[b * N + k] += omega[f] * cimag(mu[k] * x[k]);", "gL[b * N + k] += cimag(mu[k] * x[k]);", 0,
+        "factor w of dA/dL dropped"),
+    "dloss_domega_capacitor_term_dropped": (
+        "gw[b * F + f] = (cimag(muMI) + diag) * nrm;", "gw[b * F + f] = cimag(muMI) * nrm;", 0,
+        "capacitor term of dA/dw dropped"),
+    "drive_cotangent_no_conjugate": (
+        "gV[(b * F + f) * N + k] = conj(mu[k]) * nrm;", "gV[(b * F + f) * N + k] = mu[k] * nrm;", 0,
+        "drive cotangent without the conjugate"),
+    "enhancement_offset_sign": (
+        "(offset ? b + offset[i] : b) * w", "(offset ? b - offset[i] : b) * w", 0,
+        "incident field subtracted instead of added (Sec. IV-B)"),
+    "drive_wave_amplitude": (
+        "csqrt(Z0 * P_in)", "csqrt(P_in / Z0)", 0,
+        "excitation wave sqrt(P / Z') instead of sqrt(Z' P) (Eq. 4)"),
+    "field_cotangent_gradient_sign": (
+        "grad_out[b * N + k] += cimag(mu[k] * x[k]) / (omega[f] * Cb[k] * Cb[k]);",
+        "grad_out[b * N + k] -= cimag(mu[k] * x[k]) / (omega[f] * Cb[k] * Cb[k]);", 1,
+        "dloss/dC of a field cotangent with the wrong sign"),
 }
 
 
