@@ -309,3 +309,32 @@ def test_system_status_validation(nv):
     cb, kb = fake_problem(nv, wl, n_struct=0)
     assert L.mts_system_status(ct.byref(cb), 2, nv.MTS_MIXED, ct.c_void_p(FAKE), ct.c_void_p(FAKE), None) == nv.MTS_EINVAL
     assert nv.mts_launch_count() == 0
+
+
+@pytest.mark.skipif(__import__("shutil").which("gcc") is None, reason="gcc compiles the probe")
+def test_binding_structs_match_the_header(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets that a C compiler
+    gives the struct of the same name in include/mts.h (a field name missing from the header
+    fails the compile): the argument blocks cross the boundary unchanged."""
+    import subprocess
+    from paper_2503_18479_gb300 import native
+    structs = {"mts_problem": native.MtsProblem, "mts_eval": native.MtsEval,
+               "mts_adam": native.MtsAdam, "mts_sparams": native.MtsSparams,
+               "mts_sroute_eval": native.MtsSrouteEval}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "mts.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "probe.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True, text=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in structs.items():
+        assert got[(cname, "sizeof")] == ct.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
