@@ -338,3 +338,48 @@ def test_binding_structs_match_the_header(tmp_path):
         assert got[(cname, "sizeof")] == ct.sizeof(py), cname
         for fname, _ in py._fields_:
             assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def _header_prototypes():
+    src = open(os.path.join(ROOT, "include", "mts.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    protos = {}
+    for ret, name, params in re.findall(r"([A-Za-z_][\w \*]*?)\s*\b(mts_[a-z_]+)\s*\(([^;{]*?)\)\s*;", src):
+        ps = [q.strip() for q in params.split(",")]
+        protos[name] = (ret.strip(), [] if ps == ["void"] or ps == [""] else ps)
+    return protos
+
+
+def _c_kind(decl: str) -> str:
+    """Argument class of a C declaration: ptr, i32, i64, u64 (size_t too) or f64."""
+    t = decl.replace("const ", "").split()[0]
+    if "*" in decl or t == "mts_stream":  # mts_stream is a pointer typedef
+        return "ptr"
+    return {"int32_t": "i32", "int": "i32", "mts_status": "i32", "mts_precision": "i32",
+            "mts_loss_mode": "i32", "mts_projection": "i32", "int64_t": "i64", "uint64_t": "u64",
+            "size_t": "u64", "double": "f64"}[t]
+
+
+def _ct_kind(t) -> str:
+    if t is ct.c_void_p or t is ct.c_char_p or isinstance(t, type(ct.POINTER(ct.c_int))):
+        return "ptr"
+    # ctypes aliases c_int32 to c_int and c_uint64 to c_size_t on LP64 platforms
+    return {ct.c_int32: "i32", ct.c_int: "i32", ct.c_int64: "i64", ct.c_uint64: "u64",
+            ct.c_size_t: "u64", ct.c_double: "f64"}[t]
+
+
+def test_binding_prototypes_match_the_header(nv):
+    """Every entry point the binding declares takes, in the header, the same number of
+    arguments with the same classes (pointer, 32- or 64-bit integer, size_t, double) in the
+    same order, and returns the same class."""
+    L = nv.lib()
+    protos = _header_prototypes()
+    assert set(protos) == set(declared_symbols())
+    for name, (ret, params) in protos.items():
+        f = getattr(L, name)
+        want = [_c_kind(q) for q in params]
+        got = [_ct_kind(t) for t in (f.argtypes or [])]
+        assert got == want, (name, got, want)
+        rk = "ptr" if "*" in ret else _c_kind(ret.split()[-1])
+        assert _ct_kind(f.restype) == rk, (name, f.restype, ret)
