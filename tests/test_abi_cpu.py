@@ -1,6 +1,7 @@
 """C ABI checks that need no GPU: the library builds, loads, exports every entry point that
-include/mts.h declares, and its host-side validation and size queries behave as documented.
-No call here reaches a CUDA launch."""
+include/mts.h declares, and its host-side validation and size queries behave as documented;
+the binding's structs, prototypes and constants agree with the header as a C compiler reads
+it. No call here reaches a CUDA launch."""
 import ctypes as ct
 import os
 import re
@@ -383,3 +384,26 @@ def test_binding_prototypes_match_the_header(nv):
         assert got == want, (name, got, want)
         rk = "ptr" if "*" in ret else _c_kind(ret.split()[-1])
         assert _ct_kind(f.restype) == rk, (name, f.restype, ret)
+
+
+@pytest.mark.skipif(__import__("shutil").which("gcc") is None, reason="gcc compiles the probe")
+def test_binding_constants_match_the_header(tmp_path):
+    """Every MTS_* constant of the binding (status codes, precisions, loss modes, projections)
+    has the value the header gives it."""
+    import subprocess
+    from paper_2503_18479_gb300 import native
+    names = sorted(n for n in vars(native) if re.fullmatch(r"MTS_[A-Z0-9_]+", n)
+                   and isinstance(getattr(native, n), int))
+    assert names
+    lines = ["#include <stdio.h>", '#include "mts.h"', "int main(void) {"]
+    lines += [f'  printf("{n} %lld\\n", (long long)({n}));' for n in names]
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "consts.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "consts"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True, text=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {l.split()[0]: int(l.split()[1]) for l in out if l.strip()}
+    for n in names:
+        assert got[n] == getattr(native, n), n
