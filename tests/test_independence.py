@@ -45,3 +45,29 @@ def test_oracle_imports_of_the_allowed_callers_are_local():
         for line in src.splitlines():
             if re.match(r"\s*(import|from)\s+oracle\b", line):
                 assert line.startswith((" ", "\t")), f"{name}: module-level oracle import: {line!r}"
+
+
+def test_product_path_fails_loudly_without_the_library(tmp_path):
+    """With libmts.so absent the binding raises ImportError at the first call (here: loading
+    the library, and building a Simulator), instead of falling back to any CPU code."""
+    import subprocess
+    import sys
+    code = (
+        "import sys\n"
+        f"sys.path.insert(0, {ROOT!r})\n"
+        "from paper_2503_18479_gb300 import native, workloads as W\n"
+        f"native.LIB_PATH = {str(tmp_path / 'absent' / 'libmts.so')!r}\n"
+        "for what in ('lib', 'simulator'):\n"
+        "    try:\n"
+        "        if what == 'lib':\n"
+        "            native.lib()\n"
+        "        else:\n"
+        "            from paper_2503_18479_gb300.simulator import Simulator\n"
+        "            Simulator(W.single_loop(seed=0, n_cfg=2, n_freq=2, grid=4), 'mixed', device='cpu')\n"
+        "        print(what, 'no error')\n"
+        "    except ImportError:\n"
+        "        print(what, 'ImportError')\n"
+    )
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.split("\n")[:2] == ["lib ImportError", "simulator ImportError"], r.stdout
