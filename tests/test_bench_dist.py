@@ -1,6 +1,7 @@
 """Host logic of bench.py for N > 1 ranks, on the CPU with two gloo ranks: the environment
 is read as torchrun sets it, the timing is the maximum over ranks, the value counts every
-rank's configurations, and the reference arm does its work on rank 0 only."""
+rank's configurations, and the reference arm does its work on rank 0 only; and the reference
+arm's JSON line (one bounded step of the FP64 oracle) carries the keys of the contract."""
 import os
 import socket
 import sys
@@ -61,3 +62,26 @@ def test_single_rank_defaults(monkeypatch):
     assert bench.dist_env() == (0, 1, 0)
     assert bench.max_over_ranks(3.5, 1, "cpu") == 3.5
     assert bench.whole_job_value(4096, 2, 1, 1000.0) == pytest.approx(8192.0)
+
+
+def test_reference_arm_line(tmp_path):
+    """`bench.py --impl reference` (the FP64 oracle on the host cores, one bounded step) prints
+    one JSON line with the arm's metric, unit and workload, its own cpu_baseline and an e2e
+    block without host-device copies."""
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "0"], capture_output=True, text=True,
+                       timeout=900, cwd=str(tmp_path))
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.strip().startswith("{")]
+    assert len(lines) == 1, r.stdout
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["higher_is_better"] is True and d["value"] > 0 and d["steps"] == 1
+    assert d["config"]["workload"] == bench.WORKLOAD and d["dtype"] == "f64"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
+    e = d["e2e"]
+    assert e["value"] == d["value"] and e["unit"] == d["unit"]
+    assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
