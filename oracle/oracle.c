@@ -153,8 +153,13 @@ void oracle_basis(int32_t n_loops, const int32_t* loop_vtx_off, const double* vx
  * internal inductance (skin depth far below the wire radius at these frequencies).
  * Pairs that are neither parallel nor perpendicular (oblique) and do not touch use the
  * Neumann integral by quadrature (oracle_segment_pair_quadrature).
- * Status: 0 ok, 1 an oblique pair that touches (shares an end point), 2 overlapping
- * collinear segments.
+ * Oblique pairs that share an end point O (the corners of a non-rectilinear polygon), with
+ * far end points P and Q, lengths l = |OP|, m = |OQ| and R = |PQ|: the Neumann double
+ * integral int_0^l int_0^m ds dt / |r1 - r2| of two rays from O at angle e, whose distance
+ * is sqrt(s^2 + t^2 - 2 s t cos e), integrates in closed form to
+ *   F = 2 [l atanh(m / (l + R)) + m atanh(l / (m + R))],
+ * so M = mu0/(4 pi) (u1.u2) F with u1, u2 the current directions (oracle_touching_pair).
+ * Status: 0 ok, 2 overlapping collinear segments.
  * ------------------------------------------------------------------------------------ */
 static double oracle_G(double u, double d) { return u * asinh(u / d) - sqrt(u * u + d * d); }
 static double oracle_G0(double u) {
@@ -265,8 +270,23 @@ double oracle_segment_pair_quadrature(const double r1s[3], const double r1e[3],
   return ORACLE_MU0 / (4.0 * ORACLE_PI) * cosang * 0.5 * (l1 / m) * acc;
 }
 
+/* Neumann integral of two straight filaments that share the end point O (see the block
+ * comment above): far end points P (of the first) and Q (of the second). Returns
+ * mu0/(4 pi) cosang F, cosang the cosine between the two current directions. */
+double oracle_touching_pair(const double O[3], const double P[3], const double Q[3],
+                            double cosang) {
+  double l = sqrt((P[0] - O[0]) * (P[0] - O[0]) + (P[1] - O[1]) * (P[1] - O[1]) +
+                  (P[2] - O[2]) * (P[2] - O[2]));
+  double m = sqrt((Q[0] - O[0]) * (Q[0] - O[0]) + (Q[1] - O[1]) * (Q[1] - O[1]) +
+                  (Q[2] - O[2]) * (Q[2] - O[2]));
+  double R = sqrt((P[0] - Q[0]) * (P[0] - Q[0]) + (P[1] - Q[1]) * (P[1] - Q[1]) +
+                  (P[2] - Q[2]) * (P[2] - Q[2]));
+  double F = 2.0 * (l * atanh(m / (l + R)) + m * atanh(l / (m + R)));
+  return ORACLE_MU0 / (4.0 * ORACLE_PI) * cosang * F;
+}
+
 /* Order of the rule for oblique pairs (enough for segments farther apart than a tenth of
- * their length; pairs that touch are reported instead). */
+ * their length; pairs that touch take oracle_touching_pair). */
 #define ORACLE_OBLIQUE_ORDER 16
 
 static double oracle_dist2(const double a[3], const double b[3]) {
@@ -296,10 +316,17 @@ int oracle_segment_pair_inductance(const double r1s[3], const double r1e[3],
   if (fabs(dot) <= tol) return 0; /* perpendicular */
   if (cross > tol) {              /* oblique: quadrature unless the segments touch */
     double e2 = 1e-24 * (l1 + l2) * (l1 + l2);
-    if (oracle_dist2(r1s, r2s) <= e2 || oracle_dist2(r1s, r2e) <= e2 ||
-        oracle_dist2(r1e, r2s) <= e2 || oracle_dist2(r1e, r2e) <= e2)
-      return 1; /* touching oblique pair (a polygon corner): not handled */
-    *out = oracle_segment_pair_quadrature(r1s, r1e, r2s, r2e, ORACLE_OBLIQUE_ORDER);
+    double cosang = dot / (l1 * l2);
+    if (oracle_dist2(r1s, r2s) <= e2)
+      *out = oracle_touching_pair(r1s, r1e, r2e, cosang);
+    else if (oracle_dist2(r1s, r2e) <= e2)
+      *out = oracle_touching_pair(r1s, r1e, r2s, cosang);
+    else if (oracle_dist2(r1e, r2s) <= e2)
+      *out = oracle_touching_pair(r1e, r1s, r2e, cosang);
+    else if (oracle_dist2(r1e, r2e) <= e2)
+      *out = oracle_touching_pair(r1e, r1s, r2s, cosang);
+    else
+      *out = oracle_segment_pair_quadrature(r1s, r1e, r2s, r2e, ORACLE_OBLIQUE_ORDER);
     return 0;
   }
   double u[3] = {d1[0] / l1, d1[1] / l1, d1[2] / l1};
@@ -315,7 +342,10 @@ int oracle_segment_pair_inductance(const double r1s[3], const double r1e[3],
   double b2 = (b_s < b_e) ? b_e : b_s;
   double v;
   if (dist <= 1e-12 * (l1 + l2)) {
-    if (b1 < a2 && a1 < b2) return 2; /* overlapping collinear filaments diverge */
+    /* overlapping collinear filaments diverge; spans that meet within rounding of their
+     * lengths (consecutive pieces of one straight side) are the touching case of G0 */
+    double ov = 1e-12 * (l1 + l2);
+    if (b1 < a2 - ov && a1 < b2 - ov) return 2;
     v = oracle_G0(a2 - b1) - oracle_G0(a1 - b1) - oracle_G0(a2 - b2) + oracle_G0(a1 - b2);
   } else {
     v = oracle_G(a2 - b1, dist) - oracle_G(a1 - b1, dist) - oracle_G(a2 - b2, dist) +

@@ -109,6 +109,14 @@ MUTANTS = {
     "drive_wave_amplitude": (
         "csqrt(Z0 * P_in)", "csqrt(P_in / Z0)", 0,
         "excitation wave sqrt(P / Z') instead of sqrt(Z' P) (Eq. 4)"),
+    "touching_pair_factor_two": (
+        "double F = 2.0 * (l * atanh(m / (l + R)) + m * atanh(l / (m + R)));",
+        "double F = (l * atanh(m / (l + R)) + m * atanh(l / (m + R)));", 0,
+        "factor 2 of the touching-filament Neumann integral dropped"),
+    "touching_pair_far_end_swapped": (
+        "*out = oracle_touching_pair(r1s, r1e, r2e, cosang);",
+        "*out = oracle_touching_pair(r1s, r1e, r2s, cosang);", 0,
+        "shared end point taken as a far end point of a touching pair"),
     "field_cotangent_gradient_sign": (
         "grad_out[b * N + k] += cimag(mu[k] * x[k]) / (omega[f] * Cb[k] * Cb[k]);",
         "grad_out[b * N + k] -= cimag(mu[k] * x[k]) / (omega[f] * Cb[k] * Cb[k]);", 1,

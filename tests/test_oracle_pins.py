@@ -159,8 +159,65 @@ def test_parallel_filaments_textbook():
     assert st == 0 and abs(m2 + m) < 1e-24
     st, m3 = oracle.segment_pair_inductance((0, 0, 0), (l, 0, 0), (0, d, 0), (0, d + l, 0), 1e-3)
     assert st == 0 and m3 == 0.0
-    st, _ = oracle.segment_pair_inductance((0, 0, 0), (l, 0, 0), (l, 0, 0), (l + l, l, 0), 1e-3)
-    assert st == 1  # oblique pairs that touch (a polygon corner) are reported, not guessed
+
+
+@pytest.mark.parametrize("ends", ["end-start", "end-end", "start-start", "start-end"])
+def test_touching_filaments_neumann(ends):
+    """Oblique filaments that share an end point (a polygon corner): the oracle's closed form
+    against the Neumann double integral mu0/(4 pi) int int dl1.dl2 / |r1 - r2| done by
+    scipy's 2-D adaptive quadrature (the integrand's 1/r corner singularity is integrable),
+    for every way the shared point can be an end of each segment, at acute and obtuse
+    angles; a right-angle corner gives exactly 0."""
+    integrate = pytest.importorskip("scipy.integrate")
+    O = np.array([0.01, 0.004, 0.0])
+    for P, Q in ((O + [0.02, 0.0, 0.0], O + [0.01, 0.015, 0.0]),
+                 (O + [0.012, 0.003, 0.0], O + [-0.02, 0.01, 0.004])):
+        a0, a1 = (P, O) if ends.startswith("end") else (O, P)
+        b0, b1 = (O, Q) if ends.endswith("start") else (Q, O)
+        d1, d2 = a1 - a0, b1 - b0
+        f = lambda t, u: 1.0 / np.linalg.norm(a0 + u * d1 - (b0 + t * d2))
+        v, _ = integrate.dblquad(f, 0, 1, 0, 1, epsabs=1e-13, epsrel=1e-11)
+        want = MU0 / (4 * np.pi) * float(d1 @ d2) * v
+        st, m = oracle.segment_pair_inductance(a0, a1, b0, b1, 1e-3)
+        assert st == 0 and abs(m / want - 1) < 1e-9, (m, want)
+    st, m = oracle.segment_pair_inductance(O + [0.02, 0, 0], O, O, O + [0, 0.03, 0], 1e-3)
+    assert st == 0 and m == 0.0
+
+
+def test_polygon_self_inductance_circle_limit():
+    """A regular n-gon's self inductance from its segments (self terms, collinear-free
+    corners by the touching closed form, the rest by quadrature) tends to the circular
+    loop's mu0 a (ln(8a/rw) - 2) (high-frequency form) as n grows: the gap shrinks as
+    1/n^2, and the Richardson extrapolation of n = 128 and 256 lands within 2e-5."""
+    a, rw = 0.05, 1e-4
+    circle = MU0 * a * (np.log(8 * a / rw) - 2)
+    Ls = []
+    for n in (64, 128, 256):
+        off, vx, vy, vz = _loop_arrays([W.circular_loop(a, n)])
+        st, M = oracle.inductance(off, vx, vy, vz, rw)
+        assert st == 0
+        Ls.append(M[0, 0])
+    gaps = [circle - L for L in Ls]
+    assert all(g > 0 for g in gaps)
+    assert 3.5 < gaps[0] / gaps[1] < 4.2 and 3.5 < gaps[1] / gaps[2] < 4.2
+    assert abs((4 * Ls[2] - Ls[1]) / 3 / circle - 1) < 2e-5
+
+
+def test_polygon_subdivision_invariance():
+    """Splitting every side of a regular octagon (wire radius well below the pieces) into
+    2, 3 or 4 collinear pieces leaves its self inductance unchanged: the touching corners,
+    the collinear pieces and the oblique pairs across corners (quadrature) add up to the
+    same Neumann integral."""
+    a, rw = 0.05, 1e-4
+    v = np.stack(W.circular_loop(a, 8), 1)
+    Ls = []
+    for sub in (1, 2, 3, 4):
+        pts = [p + (q - p) * s / sub for p, q in zip(v, np.roll(v, -1, 0)) for s in range(sub)]
+        P = np.array(pts)
+        st, M = oracle.inductance(np.array([0, len(P)], np.int32), P[:, 0], P[:, 1], P[:, 2], rw)
+        assert st == 0
+        Ls.append(M[0, 0])
+    assert max(abs(L / Ls[0] - 1) for L in Ls[1:]) < 1e-10, Ls
 
 
 def test_collinear_filaments_textbook():
