@@ -144,45 +144,3 @@ class RCReflection(torch.autograd.Function):
 def rc_reflection(R: Optional[torch.Tensor], C: torch.Tensor, omega: torch.Tensor, Z0: float = 50.0):
     return RCReflection.apply(R, C, omega, Z0)
 
-
-def _main(argv=None):
-    """Run the route's step (series-RC loads, forward with Bcomb and objective, adjoint,
-    dL/dC) on the synthetic 8x8-plus-drive workload: `python -m paper_2503_18479_gb300.sroute
-    --steps 2`; prints the status of the last step."""
-    import argparse
-
-    from . import workloads as W
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--steps", type=int, default=2)
-    ap.add_argument("--n-cfg", type=int, default=4096)
-    ap.add_argument("--precision", default="mixed")
-    args = ap.parse_args(argv)
-    wl = W.sroute_array(seed=0, n_cfg=args.n_cfg)
-    sr = SRoute(wl.S0, wl.field, wl.rows, wl.cols, wl.n1, sc_const=wl.sc_const,
-                loss_idx=wl.loss_idx, target=wl.target, precision=args.precision)
-    n, F, nS = wl.n_cfg, sr.F, sr.nS
-    dev = sr.device
-    R = torch.from_numpy(wl.R).to(dev)
-    C = torch.from_numpy(wl.C).to(dev)
-    om = torch.from_numpy(wl.omega).to(dev)
-    svar = torch.empty((n, F, nS, 2), dtype=torch.float64, device=dev)
-    ev = nv.SrouteEval(svar, sr.target, sr.loss_mode)
-    tape = sr.alloc_tape(n)
-    B = torch.empty((n, sr.n1, F, sr.P), dtype=sr.b_dtype, device=dev)
-    loss = torch.empty(n, dtype=torch.float64, device=dev)
-    gl = torch.ones(n, dtype=torch.float64, device=dev)
-    gs = torch.empty((n, F, nS, 2), dtype=torch.float64, device=dev)
-    gC = torch.empty((n, nS), dtype=torch.float64, device=dev)
-    for _ in range(args.steps):
-        nv.mts_rc_reflection(n, F, nS, om, R, C, wl.Z0, nS, 0, svar)
-        nv.mts_sroute_forward(sr.sp, sr.prec, sr.sbasis, ev, B_out=B, loss_out=loss, tape=tape)
-        nv.mts_sroute_backward(sr.sp, sr.prec, sr.sbasis, ev, tape, grad_loss=gl, grad_svar=gs)
-        nv.mts_rc_reflection_vjp(n, F, nS, om, R, C, wl.Z0, nS, 0, gs, grad_C=gC)
-    torch.cuda.synchronize(dev)
-    code, bad = sr.status(tape, n)
-    print(f"sroute_{n}: status {code}, flagged systems {bad}")
-    return 0 if code == 0 else 1
-
-
-if __name__ == "__main__":
-    raise SystemExit(_main())
