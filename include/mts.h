@@ -84,10 +84,13 @@ typedef enum {
  * Loop k is the closed polyline of vertices loop_vtx_off[k] .. loop_vtx_off[k+1]-1, the
  * last joined back to the first; its orientation fixes the sign of its current. Each
  * structure is coupled only within itself. Inductances come from the Neumann integral over
- * segment pairs: in closed form for parallel and perpendicular pairs, by quadrature
- * (composite 16-point Gauss-Legendre, inner integral exact) for oblique pairs that do not
- * touch. Oblique pairs that share an end point (the corners of a non-rectilinear polygon)
- * give MTS_EUNSUPPORTED from mts_basis_status, so such loops need L_self.
+ * segment pairs: in closed form for parallel and perpendicular pairs and for oblique
+ * pairs that share an end point (the corners of a non-rectilinear polygon: two rays from
+ * the corner, lengths l and m, far ends R apart, integrate to
+ * 2 [l atanh(m/(l+R)) + m atanh(l/(m+R))] times mu0/(4 pi) and the direction cosine), by
+ * quadrature (composite 16-point Gauss-Legendre, inner integral exact) for the other
+ * oblique pairs. So polygonal loops of any shape get L and M from their geometry; L_self,
+ * when given, overrides the diagonal.
  * Offset tables are given twice, identical: host copies (h_*) plan launches, device
  * copies are read by the kernels. Limits: 1 <= ports per structure <= 1024 (more give
  * MTS_EUNSUPPORTED from every entry point, before any launch). Systems of up to 64 ports
@@ -197,7 +200,7 @@ mts_status mts_basis_export(const mts_problem* pb, mts_precision prec, const voi
 
 /* Synchronises `stream`, then reports MTS_EINVAL if a component code in pcomp was not 0, 1
  * or 2, else MTS_EUNSUPPORTED if a segment pair needed for M could not be integrated (two
- * collinear segments overlapped, or oblique segments touched without L_self). */
+ * collinear segments overlapped by more than rounding). */
 mts_status mts_basis_status(const mts_problem* pb, mts_precision prec, const void* basis,
                             mts_stream stream);
 
@@ -297,16 +300,29 @@ mts_status mts_system_status(const mts_problem* pb, int64_t n_cfg, mts_precision
  *                or NULL (needs ev->target)
  * Returns MTS_EWORKSPACE, before any launch, when the work would need more than
  * MTS_STATIC_SCRATCH_BYTES (compare mts_tape_bytes(pb, n_cfg, prec)). Calls no device
- * allocator. The first call on each device looks up the array's device address with that
- * device current; make that first call before any stream capture. Every call on a device
- * shares the one array, so calls whose GPU work overlaps in time (other streams, other
- * threads) race: order them on one stream. The array keeps the last call's contents; each
+ * allocator. Every call looks up the array's device address in the current context; the
+ * first lookup in a context loads the library's device code, so make the first call on each
+ * device before any stream capture. Returns MTS_OK once the work is enqueued: systems that
+ * missed the refinement tolerance are reported by mts_solve_static_status, not here. Every
+ * call on a device shares the one array, so calls whose GPU work overlaps in time (other
+ * streams, other threads) race: order them on one stream. The array keeps the last call's contents; each
  * call clears what must start at zero and never reads a region it did not write.
  * --------------------------------------------------------------------------------- */
 #define MTS_STATIC_SCRATCH_BYTES (32u << 20)
 mts_status mts_solve_static(const mts_problem* pb, mts_precision prec, const void* basis,
                             const mts_eval* ev, double* I_out, double* loss_out,
                             double* dloss_dC_out, mts_stream stream);
+
+/* Synchronises `stream` and summarises the per-system status words of the last
+ * mts_solve_static call on this device, for the same (pb, n_cfg, prec): MTS_OK, MTS_ENOCONV
+ * if any system missed the refinement tolerance or met a zero pivot or a non-finite value
+ * (its results are written either way), or MTS_ECUDA. If n_bad is not NULL it receives the
+ * number of such systems. Like mts_solve_static it allocates nothing: it counts the words in
+ * the library's static array (the same reduction as mts_tape_status) and reads two words
+ * back. MTS_EINVAL / MTS_EWORKSPACE for arguments mts_solve_static would reject. The paper
+ * has no counterpart. */
+mts_status mts_solve_static_status(const mts_problem* pb, int64_t n_cfg, mts_precision prec,
+                                   int64_t* n_bad, mts_stream stream);
 
 /* ---------------------------------------------------------------------------------
  * Optimisation loop (paper Sec. III-C: the capacitances are fitted by gradient descent with

@@ -10,12 +10,11 @@
 // by every GPU that loads it until the process exits.
 //
 // The host never touches the array by name (in host code the name is only a stand-in for
-// the device symbol): its device address is looked up once per device with
-// cudaGetSymbolAddress and passed to the kernels.
+// the device symbol): its device address is looked up with cudaGetSymbolAddress, with the
+// device current, and passed to the kernels.
 #include <cuda_runtime.h>
 
 #include <cstring>
-#include <mutex>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -26,22 +25,16 @@ namespace mts {
 static __device__ __align__(256) unsigned char g_static_scratch[MTS_STATIC_SCRATCH_BYTES];
 
 namespace {
-constexpr int kMaxDevices = 64;
-std::mutex g_static_mu;
-void* g_static_ptr[kMaxDevices] = {nullptr};
-
-// Device address of the scratch array on the current device (looked up on first use).
+// Device address of the scratch array in the current context. Looked up on every call
+// (a table lookup once the module is loaded) rather than cached, so that a context that was
+// destroyed and re-created (cudaDeviceReset, a host framework resetting the device) never
+// leaves a stale address behind. The first lookup in a context loads the module, which is
+// why the first call on a device must come before any stream capture.
 mts_status static_scratch(void** out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MTS_ECUDA;
-  std::lock_guard<std::mutex> lk(g_static_mu);
-  if (g_static_ptr[dev] == nullptr) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess || p == nullptr) return MTS_ECUDA;
-    g_static_ptr[dev] = p;
-  }
-  *out = g_static_ptr[dev];
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  if (e != cudaSuccess || p == nullptr) return MTS_ECUDA;
+  *out = p;
   return MTS_OK;
 }
 }  // namespace
@@ -73,4 +66,18 @@ extern "C" mts_status mts_solve_static(const mts_problem* pb, mts_precision prec
                                   sizeof(double) * (size_t)ev->n_cfg * pb->n_ports,
                                   cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
   return e == cudaSuccess ? MTS_OK : MTS_ECUDA;
+}
+
+extern "C" mts_status mts_solve_static_status(const mts_problem* pb, int64_t n_cfg,
+                                              mts_precision prec, int64_t* n_bad,
+                                              mts_stream stream) {
+  // the per-system status words of the last mts_solve_static call live in the static
+  // array at the tape offsets of (pb, n_cfg, prec); mts_tape_status counts them
+  size_t need = mts_tape_bytes(pb, n_cfg, prec);
+  if (need == 0) return MTS_EINVAL;
+  if (need > (size_t)MTS_STATIC_SCRATCH_BYTES) return MTS_EWORKSPACE;
+  void* scratch = nullptr;
+  mts_status s = static_scratch(&scratch);
+  if (s != MTS_OK) return s;
+  return mts_tape_status(pb, n_cfg, prec, scratch, n_bad, stream);
 }

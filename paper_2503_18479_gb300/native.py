@@ -26,9 +26,9 @@ PRECISIONS = {"fp64": MTS_FP64, "mixed": MTS_MIXED, "bf16": MTS_BF16}
 EXPORTED = ["mts_status_string", "mts_version", "mts_launch_count", "mts_basis_bytes",
             "mts_build_basis", "mts_basis_export", "mts_basis_status", "mts_tape_bytes",
             "mts_solve", "mts_superpose", "mts_forward", "mts_backward", "mts_tape_status",
-            "mts_solve_static", "mts_adam_step", "mts_param_grad", "mts_sroute_basis_bytes",
-            "mts_sroute_build", "mts_sroute_tape_bytes", "mts_sroute_forward",
-            "mts_sroute_backward", "mts_sroute_status", "mts_rc_reflection",
+            "mts_solve_static", "mts_solve_static_status", "mts_adam_step", "mts_param_grad",
+            "mts_sroute_basis_bytes", "mts_sroute_build", "mts_sroute_tape_bytes",
+            "mts_sroute_forward", "mts_sroute_backward", "mts_sroute_status", "mts_rc_reflection",
             "mts_rc_reflection_vjp", "mts_system_status"]
 MTS_PROJ_NONE, MTS_PROJ_CLIP, MTS_PROJ_TANH = 0, 1, 2
 PROJECTIONS = {None: MTS_PROJ_NONE, "none": MTS_PROJ_NONE, "clip": MTS_PROJ_CLIP, "tanh": MTS_PROJ_TANH}
@@ -122,6 +122,8 @@ def lib():
             L.mts_backward.argtypes = [PP, ct.c_int, p, PE, p, sz, p, p, p, p]
             L.mts_solve_static.restype = ct.c_int
             L.mts_solve_static.argtypes = [PP, ct.c_int, p, PE, p, p, p, p]
+            L.mts_solve_static_status.restype = ct.c_int
+            L.mts_solve_static_status.argtypes = [PP, i64, ct.c_int, ct.POINTER(ct.c_int64), p]
             L.mts_param_grad.restype = ct.c_int
             L.mts_param_grad.argtypes = [PP, ct.c_int, p, PE, p, sz, p, p, p, p, p, p]
             L.mts_adam_step.restype = ct.c_int
@@ -352,6 +354,15 @@ def mts_solve_static(pb, prec, basis, ev: Eval, I_out=None, loss_out=None, dloss
     _check(lib().mts_solve_static(pb.ref, _prec(prec), _ptr(basis), ev.ref, _ptr(I_out),
                                   _ptr(loss_out), _ptr(dloss_dC_out), _stream(stream)),
            "mts_solve_static")
+
+
+def mts_solve_static_status(pb, n_cfg: int, prec, stream=None):
+    """(status code, number of flagged systems) of the last mts_solve_static call on this
+    device for the same problem, batch size and precision (synchronises the stream)."""
+    n_bad = ct.c_int64(0)
+    code = lib().mts_solve_static_status(pb.ref, int(n_cfg), _prec(prec), ct.byref(n_bad),
+                                         _stream(stream))
+    return int(code), int(n_bad.value)
 
 
 def alloc_bytes(nbytes: int, device="cuda") -> torch.Tensor:

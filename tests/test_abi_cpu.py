@@ -153,6 +153,39 @@ def test_workspace_and_alignment_checks(nv):
     assert nv.mts_launch_count() == 0
 
 
+def test_static_solve_argument_checks(nv):
+    """mts_solve_static and its status reader check their arguments before any CUDA call:
+    no evaluation, an invalid precision, a loss gradient without a target, and a batch whose
+    working state would not fit the static scratch."""
+    L = nv.lib()
+    wl = W.array_8x8(n_cfg=2, grid=8, planes=(0.02,))
+    c, keep = fake_problem(nv, wl)
+    ev = nv.MtsEval()
+    ev.n_cfg = 2
+    ev.C = ev.omega = ev.V = FAKE
+    ev.target = None
+    ev.loss_mode = 0
+    basis = ct.c_void_p(FAKE)
+    assert L.mts_solve_static(ct.byref(c), nv.MTS_MIXED, basis, None, None, None, None, None) == nv.MTS_EINVAL
+    assert L.mts_solve_static(ct.byref(c), 7, basis, ct.byref(ev), None, None, None, None) == nv.MTS_EINVAL
+    assert L.mts_solve_static(ct.byref(c), nv.MTS_MIXED, basis, ct.byref(ev), None, None,
+                              ct.c_void_p(FAKE), None) == nv.MTS_EINVAL
+    assert L.mts_solve_static(ct.byref(c), nv.MTS_MIXED, basis, ct.byref(ev), None,
+                              ct.c_void_p(FAKE), None, None) == nv.MTS_EINVAL
+    limit = 32 << 20
+    n_big = 1
+    while L.mts_tape_bytes(ct.byref(c), n_big, nv.MTS_MIXED) <= limit:
+        n_big *= 2
+    ev.n_cfg = n_big
+    assert L.mts_solve_static(ct.byref(c), nv.MTS_MIXED, basis, ct.byref(ev), None, None, None,
+                              None) == nv.MTS_EWORKSPACE
+    nb = ct.c_int64(-1)
+    assert L.mts_solve_static_status(ct.byref(c), n_big, nv.MTS_MIXED, ct.byref(nb), None) == nv.MTS_EWORKSPACE
+    assert L.mts_solve_static_status(ct.byref(c), -1, nv.MTS_MIXED, ct.byref(nb), None) == nv.MTS_EINVAL
+    assert L.mts_solve_static_status(ct.byref(c), 2, 9, ct.byref(nb), None) == nv.MTS_EINVAL
+    assert nv.mts_launch_count() == 0
+
+
 def _wide_workload(nx, ny, n_freq=1):
     loops = W.square_array(nx, ny, seg_per_side=1)
     pts = W.grid_plane(2, 0.1, 0.02)

@@ -71,3 +71,35 @@ def test_static_solve_rejects_work_beyond_the_scratch():
     with pytest.raises(nv.MtsError) as e:
         nv.mts_solve_static(sim.pb, sim.prec, sim.basis, sim.make_eval(C, True))
     assert e.value.code == nv.MTS_EWORKSPACE
+
+
+def test_static_solve_reports_unconverged_systems():
+    """A system too ill-conditioned for FP32 factors (an eigenvalue of A of about R = 1e-9
+    ohm, condition number about 3e10) cannot meet the refinement tolerance: after
+    mts_solve_static, mts_solve_static_status reports MTS_ENOCONV with exactly that system
+    counted, and a well-conditioned batch reports MTS_OK. The static path's status words are
+    the ones mts_solve would have written to a tape."""
+    import dataclasses
+    assert torch.cuda.is_available()
+    build_lib.build()
+    from helpers import small_rect, structure_basis
+    from paper_2503_18479_gb300 import native as nv
+    from paper_2503_18479_gb300.simulator import Simulator
+    wl = small_rect(8, 8, n_cfg=6)
+    st = dataclasses.replace(wl.structures[0], R=np.full(wl.structures[0].n_ports, 1e-9))
+    wl = dataclasses.replace(wl, structures=[st])
+    _, M = structure_basis(wl, 0)  # the oracle's inductances choose the planted input
+    w0 = float(st.omega[0])
+    C0 = 1.0 / (w0 * w0 * float(np.linalg.eigvalsh(M)[0]))
+    sim = Simulator(wl, "mixed")
+    n = wl.n_cfg
+    C = torch.from_numpy(wl.C).cuda()
+    nv.mts_solve_static(sim.pb, sim.prec, sim.basis, sim.make_eval(C, True))
+    assert nv.mts_solve_static_status(sim.pb, n, sim.prec) == (nv.MTS_OK, 0)
+    Cbad = C.clone()
+    Cbad[2, :] = C0
+    I = torch.empty((n, sim.sumFN), dtype=torch.complex128, device="cuda")
+    nv.mts_solve_static(sim.pb, sim.prec, sim.basis, sim.make_eval(Cbad, True), I)
+    code, n_bad = nv.mts_solve_static_status(sim.pb, n, sim.prec)
+    assert code == nv.MTS_ENOCONV and n_bad == 1, (code, n_bad)
+    assert torch.isfinite(torch.view_as_real(I)).all()  # results are written either way
