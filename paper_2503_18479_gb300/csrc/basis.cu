@@ -315,7 +315,11 @@ __global__ void __launch_bounds__(128) basis_fp32_kernel(
 //     form (ln((R1 + l2 - t0)/(R0 - t0)), cancelling factors rewritten through rho^2) and the
 //     outer one by a composite 16-point Gauss-Legendre rule on m = min(8, ceil(l1/d))
 //     equal panels, d the smallest end-point-to-segment distance.
-// Returns 0, or 1 (oblique pair that touches) / 2 (overlapping collinear pair) with value 0.
+//   oblique and sharing an end point O (a corner of a non-rectilinear polygon), far end
+//     points P, Q, lengths l = |OP|, m = |OQ|, R = |PQ|: two rays from O at angle e have
+//     distance sqrt(s^2 + t^2 - 2 s t cos e), whose double integral is
+//     F = 2 [l atanh(m / (l + R)) + m atanh(l / (m + R))]; M = mu0/(4 pi) (u1.u2) F.
+// Returns 0, or 2 (overlapping collinear pair) with value 0.
 // ---------------------------------------------------------------------------------------
 struct GaussRule16 {
   double x[16], w[16];
@@ -402,14 +406,18 @@ __device__ double pair_quadrature(double s1x, double s1y, double s1z, double e1x
   return kMu0Over4Pi * cosang * 0.5 * (l1 / m) * acc;
 }
 
-__device__ inline bool touches(double s1x, double s1y, double s1z, double e1x, double e1y,
-                               double e1z, double s2x, double s2y, double s2z, double e2x,
-                               double e2y, double e2z, double e2) {
-  auto d2 = [](double ax, double ay, double az, double bx, double by, double bz) {
-    return (ax - bx) * (ax - bx) + (ay - by) * (ay - by) + (az - bz) * (az - bz);
-  };
-  return d2(s1x, s1y, s1z, s2x, s2y, s2z) <= e2 || d2(s1x, s1y, s1z, e2x, e2y, e2z) <= e2 ||
-         d2(e1x, e1y, e1z, s2x, s2y, s2z) <= e2 || d2(e1x, e1y, e1z, e2x, e2y, e2z) <= e2;
+__device__ inline double dist3(double ax, double ay, double az, double bx, double by, double bz) {
+  return sqrt((ax - bx) * (ax - bx) + (ay - by) * (ay - by) + (az - bz) * (az - bz));
+}
+
+// Neumann integral of two filaments sharing the end point O (far end points P and Q),
+// cosang the cosine between the two current directions.
+__device__ inline double touching_pair(double ox, double oy, double oz, double px, double py,
+                                       double pz, double qx, double qy, double qz,
+                                       double cosang) {
+  const double l = dist3(px, py, pz, ox, oy, oz), m = dist3(qx, qy, qz, ox, oy, oz);
+  const double R = dist3(px, py, pz, qx, qy, qz);
+  return kMu0Over4Pi * cosang * 2.0 * (l * atanh(m / (l + R)) + m * atanh(l / (m + R)));
 }
 
 __device__ inline double Gpar(double u, double d) { return u * asinh(u / d) - sqrt(u * u + d * d); }
@@ -438,10 +446,21 @@ __device__ int pair_inductance(double s1x, double s1y, double s1z, double e1x, d
   double tol = 1e-12 * l1 * l2;
   if (fabs(dot) <= tol) return 0;
   if (cr > tol) {  // oblique
-    if (touches(s1x, s1y, s1z, e1x, e1y, e1z, s2x, s2y, s2z, e2x, e2y, e2z,
-                1e-24 * (l1 + l2) * (l1 + l2)))
-      return 1;
-    *out = pair_quadrature(s1x, s1y, s1z, e1x, e1y, e1z, s2x, s2y, s2z, e2x, e2y, e2z, g);
+    const double e2 = 1e-24 * (l1 + l2) * (l1 + l2);
+    const double c = dot / (l1 * l2);
+    auto d2 = [](double ax, double ay, double az, double bx, double by, double bz) {
+      return (ax - bx) * (ax - bx) + (ay - by) * (ay - by) + (az - bz) * (az - bz);
+    };
+    if (d2(s1x, s1y, s1z, s2x, s2y, s2z) <= e2)
+      *out = touching_pair(s1x, s1y, s1z, e1x, e1y, e1z, e2x, e2y, e2z, c);
+    else if (d2(s1x, s1y, s1z, e2x, e2y, e2z) <= e2)
+      *out = touching_pair(s1x, s1y, s1z, e1x, e1y, e1z, s2x, s2y, s2z, c);
+    else if (d2(e1x, e1y, e1z, s2x, s2y, s2z) <= e2)
+      *out = touching_pair(e1x, e1y, e1z, s1x, s1y, s1z, e2x, e2y, e2z, c);
+    else if (d2(e1x, e1y, e1z, e2x, e2y, e2z) <= e2)
+      *out = touching_pair(e1x, e1y, e1z, s1x, s1y, s1z, s2x, s2y, s2z, c);
+    else
+      *out = pair_quadrature(s1x, s1y, s1z, e1x, e1y, e1z, s2x, s2y, s2z, e2x, e2y, e2z, g);
     return 0;
   }
   double ux = d1x / l1, uy = d1y / l1, uz = d1z / l1;
@@ -454,7 +473,9 @@ __device__ int pair_inductance(double s1x, double s1y, double s1z, double e1x, d
   double a1 = 0.0, a2 = l1;
   double v;
   if (dist <= 1e-12 * (l1 + l2)) {
-    if (b1 < a2 && a1 < b2) return 2;
+    // spans that meet within rounding of their lengths are the touching case of G0
+    const double ov = 1e-12 * (l1 + l2);
+    if (b1 < a2 - ov && a1 < b2 - ov) return 2;
     v = Gcol(a2 - b1) - Gcol(a1 - b1) - Gcol(a2 - b2) + Gcol(a1 - b2);
   } else {
     v = Gpar(a2 - b1, dist) - Gpar(a1 - b1, dist) - Gpar(a2 - b2, dist) + Gpar(a1 - b2, dist);

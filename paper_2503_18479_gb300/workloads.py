@@ -306,10 +306,11 @@ def loop_sweep(n_init: int = 100, n_target: int = 100, grid: int = 32,
 
 def circle_array(nx: int = 3, ny: int = 3, seed: int = 0, n_cfg: int = 64, n_freq: int = 3,
                  radius: float = 0.025, pitch: float = 0.055, n_seg: int = 64,
-                 grid: int = 24) -> Workload:
+                 grid: int = 24, closed_form_L: bool = True) -> Workload:
     """An nx x ny array of circular loops (regular n_seg-gons of the given radius); the
-    mutual inductances couple oblique segment pairs, the self inductances take the
-    closed-form loop value."""
+    mutual inductances couple oblique segment pairs; the self inductances take the
+    closed-form loop value, or (closed_form_L=False) come from the polygon's own segment
+    pairs, corners included."""
     rng = np.random.Generator(np.random.PCG64(seed))
     rw = 0.001
     loops = [circular_loop(radius, n_seg, (i - (nx - 1) / 2.0) * pitch, (j - (ny - 1) / 2.0) * pitch)
@@ -319,7 +320,7 @@ def circle_array(nx: int = 3, ny: int = 3, seed: int = 0, n_cfg: int = 64, n_fre
     pts = _concat_points(grid_plane(grid, hx, 0.020, half_span_y=hy),
                          _cell_centre_points(nx, ny, pitch, 0.040))
     loss_idx = np.arange(grid * grid, grid * grid + nx * ny)
-    Ls = np.full(nx * ny, circular_loop_inductance(radius, rw))
+    Ls = np.full(nx * ny, circular_loop_inductance(radius, rw)) if closed_form_L else None
     st = _structure_from(loops, pts, omega, 0.1, loss_idx, L_self=Ls, label=f"circles_{nx}x{ny}")
     C = rng.uniform(20 * PF, 200 * PF, size=(n_cfg, nx * ny))
     target = rng.standard_normal(n_freq * nx * ny) * 1e-6

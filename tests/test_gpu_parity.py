@@ -50,6 +50,10 @@ _CASES = {
     "10x8": lambda: small_rect(10, 8, n_cfg=20, n_freq=2, grid=10, seed=4),
     # circular loops: mutual inductances from oblique segment pairs (quadrature)
     "circles": lambda: W.circle_array(3, 3, seed=6, n_cfg=40, n_freq=3, grid=12),
+    # circular loops whose self inductances come from their own segments: the polygon
+    # corners are oblique pairs that touch (closed form), no L_self
+    "circles_geometric_L": lambda: W.circle_array(2, 3, seed=7, n_cfg=24, n_freq=2, grid=10,
+                                                  closed_form_L=False),
     # Bx, By or Bz chosen per field point (objective points included), ragged structures
     "components": lambda: apply_target_rule(with_components(small_ragged(n_struct=6, seed=9), 10)),
 }
