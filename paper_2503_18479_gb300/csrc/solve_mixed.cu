@@ -5,30 +5,42 @@
 //
 // Register layout: row r lives in NB = NM/8 blocks of 8 columns; each block keeps the real
 // parts of its columns in 4 packed 64-bit pairs (columns 2m, 2m+1) and the imaginary parts
-// in another 4, so that the row update runs on the packed FP32x2 pipe over adjacent
-// columns (re' = re - l.x ux + l.y uy, im' = im - l.x uy - l.y ux: four fma.rn.f32x2 per
-// column pair) and the pivot row is published with 128-bit stores. Rows are never moved;
-// the pivot of step k is the row with the largest |a_rk| among rows not chosen yet (one
-// redux.sync.max per warp on the magnitude with the row index in the low bits), and its
-// step is recorded in `pivstep`.
+// in another 4, so that updates run on the packed FP32x2 pipe over adjacent columns
+// (re' = re + n.x ux - n.y uy, im' = im + n.x uy + n.y ux: four fma.rn.f32x2 per column
+// pair). Rows are never moved: the pivot of step k is the row with the largest |a_rk|
+// among rows not chosen yet (one redux.sync.max per warp on the magnitude with the row
+// index in the low bits), and the step at which a row was chosen is its `pivstep`.
 //
-// LU in panels of 8 columns: the 8 steps of a panel are unrolled with static register
-// indices; the panel loop is a runtime loop, and after each panel the blocks rotate by one
-// (block b <- block b+1, the finished panel to the end), so the active panel is always
-// block 0 and the code stays one panel long. NB rotations restore the original order.
+// LU in panels of 8 columns with delayed updates. The active panel is always register
+// block 0 (after each panel the blocks rotate by one; NB rotations restore the order).
+// Inside a panel the 8 pivot steps update block 0 only (rank-1 on 8 columns), so a step
+// publishes 8 columns of its pivot row. At the panel end, with L_bb and U_bb the panel's
+// unit-lower and upper diagonal blocks in pivot order:
+//   W_b = L_bb^-1 and V_b = U_bb^-1 (one column per thread, 16 threads);
+//   every row solves lt L_bb = l for its panel multipliers l (rows chosen in this panel
+//     use their multipliers left of their own pivot, rows chosen earlier use none), so
+//     lt = l W_b;
+//   the panel's pivot rows publish their trailing columns as they were before the panel,
+//     and every row adds -lt times them: unchosen rows get A_22 - L_21 U_12, and the pivot
+//     rows get U_12 = W_b A_12 itself (their lt is e_ii - W_b[ii]);
+//   block 0 keeps -lt (unchosen rows: the block-L multipliers L_rb W_b of the forward
+//     sweep), V_b's row ii (the panel's pivot row ii), or its U entries (earlier rows).
 //
-// Triangular solves in 8x8 blocks (pivot order): the diagonal blocks of L and U are
-// inverted once (W = L_bb^-1, V = U_bb^-1, all blocks in parallel, 8 group barriers), and
-// the off-diagonal factor rows are premultiplied and negated in place (-l W, -u V). A forward
-// block step is then y_b = W_b c_b for the block's pivot rows and c_r += (-l~_r) c_b for
-// later rows, both from the raw c_b values, with one barrier; the backward step likewise
-// with V and -u~. The block steps are branch-free (predicated), so a warp never runs both
-// sides of a row-role test.
+// Solves with P A = L U in blocks of 8 (pivot order), L = Lt D, D = diag(L_bb):
+//   forward: yt_b = c_b - sum_{a<b} (L_ba W_a) yt_a, one barrier per block: the block's
+//     pivot rows publish their value, every row adds its block-b coefficients times it
+//     (rows past their own block add garbage to a value they no longer use);
+//   z_b = W_b yt_b for all blocks at once;
+//   backward: x_b = V_b (z_b - sum_{c>b} U_bc x_c), two barriers per block (publish the
+//     block's partial values, the pivot rows apply their V row, publish x_b, earlier rows
+//     subtract U_rb x_b).
+// No step masks a coefficient: each row's block b holds exactly what its role in block b
+// needs.
 //
 // Refinement: x_0 = LU \ rhs; the first residual r_1 = rhs - A x_0 is evaluated in
-// double-float arithmetic (M = hi + lo, x = hi + lo, error-free products and sums on the
-// FP32x2 pipe); later residuals are updated incrementally, r_{k+1} = r_k - A d_k, in FP32,
-// since d_k is already small. One solve call site serves every right-hand side.
+// double-float arithmetic (M = hi + lo, x_0 in FP32, error-free products and sums on the
+// FP32x2 pipe); later residuals are updated incrementally, r_{k+1} = r_k - A d_k, in FP32.
+// The stop test uses max|d_k| (folded into the permutation barrier of each solve).
 //
 // Objective and adjoint (Eq. 1, 7-9): b_l = H_loss I, loss = sum e(b_l, t_l),
 // u = H_loss^T conj(G), A mu = u (A^T = A), dloss/dC_k = Im(mu_k I_k)/(w C_k^2).
@@ -75,24 +87,29 @@ __device__ __forceinline__ u64 fmul2(u64 a, u64 b) {
 }
 
 template <int NM>
-struct SmemV3 {
+struct SmemV4 {
   static constexpr int NB = NM / 8;
-  static constexpr int NW = NM > 32 ? NM / 32 : 1;  // candidate buffers (warps per group)
-  float prow_re[2][NW][NM];    // pivot-row candidates, real parts, [parity][warp][col]
-  float prow_im[2][NW][NM];    // imaginary parts
-  float2 Wb[NB][8][8];         // inverses of the diagonal blocks of L (unit lower)
-  float2 Vb[NB][8][8];         // and of U (upper)
-  ulonglong2 xhl[NM];          // x split: ((re_hi, im_hi), (re_lo, im_lo))
-  double2 x64[NM];
-  float2 Gs[NM];               // conj(G) of a chunk of loss points
-  float2 bp[2][8];
-  float2 bq[2][8];
-  float2 xs[NM];
+  static constexpr int NW = NM > 32 ? NM / 32 : 1;      // warps per group
+  static constexpr int NT = NM > 8 ? NM - 8 : 8;        // trailing columns of the first panel
+  __align__(16) float prow[2][NW][16];   // in-panel pivot-row candidates: block 0, re then im
+  __align__(16) float dre[8][8];         // the panel's pivot rows (pivot order): L_bb below
+  __align__(16) float dim[8][8];         // the diagonal, U_bb on and above it
+  __align__(16) float vre[8][8];         // V_b = U_bb^-1 of the current panel
+  __align__(16) float vim[8][8];
+  __align__(16) float wre[NB][8][8];     // W_b = L_bb^-1 of every block
+  __align__(16) float wim[NB][8][8];
+  __align__(16) float tre[8][NT];        // trailing columns of the panel's pivot rows
+  __align__(16) float tim[8][NT];
+  __align__(16) float sre[2][8];         // block values published in the sweeps
+  __align__(16) float sim[2][8];
+  __align__(16) float yre[NM];           // forward-sweep values by pivot position
+  __align__(16) float yim[NM];
+  __align__(16) float2 xc[NM];           // unknowns by column (FP32), permutation buffer
+  __align__(16) float2 Gs[NM];           // conj(G) of a chunk of loss points
   double red[NW];
   float redf[NW];
-  float ckey[2][NW];
-  int cidx[2][NW];
   unsigned ukey[2][NW];
+  unsigned umax[NW];
 };
 
 template <int NM>
@@ -102,7 +119,7 @@ __device__ __forceinline__ void gsync() {
 }
 
 template <int NM>
-__device__ inline float gmax(float v, SmemV3<NM>& sm, int r) {
+__device__ inline float gmax(float v, SmemV4<NM>& sm, int r) {
   if constexpr (NM <= 32) {
     for (int off = NM >> 1; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off, NM));
     return v;
@@ -113,13 +130,13 @@ __device__ inline float gmax(float v, SmemV3<NM>& sm, int r) {
     __syncthreads();
     float m = sm.redf[0];
 #pragma unroll
-    for (int q = 1; q < SmemV3<NM>::NW; ++q) m = fmaxf(m, sm.redf[q]);
+    for (int q = 1; q < SmemV4<NM>::NW; ++q) m = fmaxf(m, sm.redf[q]);
     return m;
   }
 }
 
 template <int NM>
-__device__ inline double gsum(double v, SmemV3<NM>& sm, int r) {
+__device__ inline double gsum(double v, SmemV4<NM>& sm, int r) {
   if constexpr (NM <= 32) {
     for (int off = NM >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off, NM);
     return v;
@@ -130,16 +147,11 @@ __device__ inline double gsum(double v, SmemV3<NM>& sm, int r) {
     __syncthreads();
     double s = 0.0;
 #pragma unroll
-    for (int q = 0; q < SmemV3<NM>::NW; ++q) s += sm.red[q];
+    for (int q = 0; q < SmemV4<NM>::NW; ++q) s += sm.red[q];
     return s;
   }
 }
 
-// c += a * b (complex, FP32)
-__device__ __forceinline__ void cma(float2& c, float2 a, float2 b) {
-  c.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x));
-  c.y = fmaf(a.x, b.y, fmaf(a.y, b.x, c.y));
-}
 __device__ __forceinline__ float2 crecip(float2 a) {
   // hardware approximate reciprocal (one instruction, <= 1 ulp): the factors are FP32 and
   // refinement on double-float residuals removes their rounding; it shortens the per-step
@@ -150,6 +162,11 @@ __device__ __forceinline__ float2 crecip(float2 a) {
 }
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// c -= a * b (complex, FP32)
+__device__ __forceinline__ void cms(float2& c, float2 a, float2 b) {
+  c.x = fmaf(-a.x, b.x, fmaf(a.y, b.y, c.x));
+  c.y = fmaf(-a.x, b.y, fmaf(-a.y, b.x, c.y));
 }
 
 // Objective term of one loss point in FP32 and its cotangent G = de/dRe b + j de/dIm b
@@ -186,62 +203,77 @@ __device__ __forceinline__ void set_elem(u64* re4, u64* im4, int j, float2 v) {
   }
 }
 
+// sum_j a_j v_j over one register block (a: 4 re pairs, 4 im pairs) and 8 complex values
+// stored as re[8], im[8] (16-byte aligned)
+__device__ __forceinline__ float2 bdot(const u64* re4, const u64* im4, const float* vre, const float* vim) {
+  const ulonglong2 r0 = reinterpret_cast<const ulonglong2*>(vre)[0];
+  const ulonglong2 r1 = reinterpret_cast<const ulonglong2*>(vre)[1];
+  const ulonglong2 i0 = reinterpret_cast<const ulonglong2*>(vim)[0];
+  const ulonglong2 i1 = reinterpret_cast<const ulonglong2*>(vim)[1];
+  const u64 VR[4] = {r0.x, r0.y, r1.x, r1.y}, VI[4] = {i0.x, i0.y, i1.x, i1.y};
+  u64 A = 0ull, B = 0ull, C = 0ull, D = 0ull;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    A = ffma2(re4[m], VR[m], A);
+    B = ffma2(im4[m], VI[m], B);
+    C = ffma2(re4[m], VI[m], C);
+    D = ffma2(im4[m], VR[m], D);
+  }
+  const float2 a = up(A), b = up(B), c = up(C), d = up(D);
+  return make_float2((a.x + a.y) - (b.x + b.y), (c.x + c.y) + (d.x + d.y));
+}
+
 template <int NM>
-__global__ void __launch_bounds__(NM >= 64 ? NM : 128, NM >= 64 ? 5 : 1) solve_mixed_v3(SolveArgs a, int64_t n_sys) {
+__global__ void __launch_bounds__(NM >= 64 ? NM : 128, NM >= 64 ? 6 : (NM == 32 ? 3 : 4))
+solve_mixed_v4(SolveArgs a, int64_t n_sys) {
   constexpr int NB = NM / 8;
   constexpr int CT = NM >= 64 ? NM : 128;
   constexpr int G = CT / NM;
   extern __shared__ __align__(16) unsigned char dsm[];
   const int grp = threadIdx.x / NM, r = threadIdx.x % NM;
-  SmemV3<NM>& sm = reinterpret_cast<SmemV3<NM>*>(dsm)[grp];
+  SmemV4<NM>& sm = reinterpret_cast<SmemV4<NM>*>(dsm)[grp];
 
   const int64_t li = (int64_t)blockIdx.x * G + grp;
   const bool in_range = li < n_sys;
   const int64_t sys = in_range ? launch_sys(a, li) : 0;
-  SysInfo si = sys_info(a, sys);
-  const bool valid = in_range && si.N <= NM;  // larger systems: solve_large.cu
-  if (!valid) si.N = 0;
-  const int N = si.N;
-  const double w = si.w;
-  const float w32 = (float)w;
-  const bool real_row = r < N;
-  const bool bwd = a.rhs_in != nullptr;
-  const double Cr = real_row ? a.C[si.b * a.n_ports + si.k0 + r] : 1.0;
-  cd Dr = {0.0, 0.0};
-  if (real_row) Dr = {a.R[si.k0 + r], -1.0 / (w * Cr)};
-  // M = hi + lo of this structure, read through L1 (shared by every system of the structure)
-  const int64_t mo = a.t.nn_off[si.s];
-  const float* __restrict__ Mh = a.M32hi + mo;
-  const float* __restrict__ Ml = a.M32lo + mo;
-
-  // ---- row r of A (FP32), identity rows for padding ----
-  // The diagonal entry needs FP64 (w (M_rr hi + lo) + Im D_r, then rounded): it is computed
-  // once per thread here, not inside the unrolled column loop, where each column's branch
-  // would run its FP64 instructions for the one lane with c == r (this part's FP64 rate is
-  // 1/62 of FP32).
-  float dre = 1.0f, dim = 0.0f;
-  if (real_row) {
-    dre = (float)Dr.x;
-    dim = (float)(w * ((double)__ldg(Mh + r * N + r) + (double)__ldg(Ml + r * N + r)) + Dr.y);
-  }
   u64 ReP[NB][4], ImP[NB][4];
-#pragma unroll
-  for (int b = 0; b < NB; ++b)
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      float re2[2], im2[2];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int c = 8 * b + 2 * m + h;
-        const float mm = (real_row && c < N) ? w32 * __ldg(Mh + c * N + r) : 0.0f;  // M symmetric
-        re2[h] = (c == r) ? dre : 0.0f;
-        im2[h] = (c == r) ? dim : mm;
-      }
-      ReP[b][m] = pk(re2[0], re2[1]);
-      ImP[b][m] = pk(im2[0], im2[1]);
+  {
+    // ---- row r of A (FP32), identity rows for padding. The per-system values used here are
+    // derived again after the LU, so that none of them stays live across it. ----
+    SysInfo si = sys_info(a, sys);
+    const int N = (in_range && si.N <= NM) ? si.N : 0;
+    const double w = si.w;
+    const float w32 = (float)w;
+    const bool real_row = r < N;
+    const float* __restrict__ Mh = a.M32hi + a.t.nn_off[si.s];
+    const float* __restrict__ Ml = a.M32lo + a.t.nn_off[si.s];
+    // The diagonal entry needs FP64 (w (M_rr hi + lo) - 1/(w C_r), then rounded): it is
+    // computed once per thread here, not inside the unrolled column loop, where each
+    // column's branch would run its FP64 instructions for the one lane with c == r.
+    float dre = 1.0f, dimv = 0.0f;
+    if (real_row) {
+      const double Cr = a.C[si.b * a.n_ports + si.k0 + r];
+      dre = (float)a.R[si.k0 + r];
+      dimv = (float)(w * ((double)__ldg(Mh + r * N + r) + (double)__ldg(Ml + r * N + r)) - 1.0 / (w * Cr));
     }
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        float re2[2], im2[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int c = 8 * b + 2 * m + h;
+          const float mm = (real_row && c < N) ? w32 * __ldg(Mh + c * N + r) : 0.0f;  // M symmetric
+          re2[h] = (c == r) ? dre : 0.0f;
+          im2[h] = (c == r) ? dimv : mm;
+        }
+        ReP[b][m] = pk(re2[0], re2[1]);
+        ImP[b][m] = pk(im2[0], im2[1]);
+      }
+  }
 
-  // ---- LU with partial pivoting, panels of 8 columns ----
+  // ---- LU with partial pivoting, panels of 8 columns, delayed trailing updates ----
   int pivstep = NM;
 #pragma unroll 1
   for (int kb = 0; kb < NB; ++kb) {
@@ -251,37 +283,32 @@ __global__ void __launch_bounds__(NM >= 64 ? NM : 128, NM >= 64 ? 5 : 1) solve_m
       const int k = 8 * kb + kk;
       const int par = kk & 1;
       const float2 cur = elem(ReP[0], ImP[0], kk);
+      const bool unpiv = pivstep == NM;
       int p, src = 0;
       if constexpr (NM >= 32) {
-        // magnitude bits with the row index in the low 6 bits (ties -> smaller row)
+        // magnitude bits, a "not chosen yet" bit and the row index in the low 7 bits
+        // (ties -> smaller row); chosen rows have key 0
         const float mag = cur.x * cur.x + cur.y * cur.y;
-        const unsigned key = (pivstep < NM) ? 0u : ((__float_as_uint(mag) & ~63u) | (unsigned)(63 - r));
+        const unsigned key = unpiv ? ((__float_as_uint(mag) & ~127u) | 64u | (unsigned)(63 - r)) : 0u;
         unsigned wmax;
         asm volatile("redux.sync.max.u32 %0, %1, 0xffffffff;" : "=r"(wmax) : "r"(key));
         const int cand = 63 - (int)(wmax & 63u);
-        const int wv = r >> 5;
         if constexpr (NM == 32) {
           p = cand;
         } else {
+          const int wv = r >> 5;
           if ((r & 31) == 0) sm.ukey[par][wv] = wmax;
-          if (r == cand) {  // this warp's candidate publishes its row speculatively
-#pragma unroll
-            for (int b = 0; b < NB; ++b) {
-              if (b >= nact) break;  // finished panels sit at the end: skip them by a jump
-              {
-                ulonglong2* dr = reinterpret_cast<ulonglong2*>(&sm.prow_re[par][wv][8 * b]);
-                ulonglong2* di = reinterpret_cast<ulonglong2*>(&sm.prow_im[par][wv][8 * b]);
-                dr[0] = make_ulonglong2(ReP[b][0], ReP[b][1]);
-                dr[1] = make_ulonglong2(ReP[b][2], ReP[b][3]);
-                di[0] = make_ulonglong2(ImP[b][0], ImP[b][1]);
-                di[1] = make_ulonglong2(ImP[b][2], ImP[b][3]);
-              }
-            }
+          if (r == cand) {  // this warp's candidate publishes its panel block speculatively
+            ulonglong2* d = reinterpret_cast<ulonglong2*>(sm.prow[par][wv]);
+            d[0] = make_ulonglong2(ReP[0][0], ReP[0][1]);
+            d[1] = make_ulonglong2(ReP[0][2], ReP[0][3]);
+            d[2] = make_ulonglong2(ImP[0][0], ImP[0][1]);
+            d[3] = make_ulonglong2(ImP[0][2], ImP[0][3]);
           }
           __syncthreads();
           unsigned best = sm.ukey[par][0];
 #pragma unroll
-          for (int q = 1; q < SmemV3<NM>::NW; ++q) {
+          for (int q = 1; q < SmemV4<NM>::NW; ++q) {
             const unsigned uq = sm.ukey[par][q];
             if (uq > best) {
               best = uq;
@@ -291,60 +318,162 @@ __global__ void __launch_bounds__(NM >= 64 ? NM : 128, NM >= 64 ? 5 : 1) solve_m
           p = 63 - (int)(best & 63u);
         }
       } else {
-        float key = (pivstep < NM) ? -1.0f : cur.x * cur.x + cur.y * cur.y;
+        // chosen rows rank -1, the others by magnitude (a NaN magnitude ranks as 0, so
+        // that the pick is always a row not chosen yet)
+        float key = unpiv ? fmaxf(cur.x * cur.x + cur.y * cur.y, 0.0f) : -1.0f;
         int idx = r;
         argmax_shfl(key, idx, NM);
         p = idx;
       }
       if constexpr (NM <= 32) {
         if (r == p) {
-#pragma unroll
-          for (int b = 0; b < NB; ++b)
-            if (b < nact) {
-              ulonglong2* dr = reinterpret_cast<ulonglong2*>(&sm.prow_re[par][0][8 * b]);
-              ulonglong2* di = reinterpret_cast<ulonglong2*>(&sm.prow_im[par][0][8 * b]);
-              dr[0] = make_ulonglong2(ReP[b][0], ReP[b][1]);
-              dr[1] = make_ulonglong2(ReP[b][2], ReP[b][3]);
-              di[0] = make_ulonglong2(ImP[b][0], ImP[b][1]);
-              di[1] = make_ulonglong2(ImP[b][2], ImP[b][3]);
-            }
+          ulonglong2* d = reinterpret_cast<ulonglong2*>(sm.prow[par][0]);
+          d[0] = make_ulonglong2(ReP[0][0], ReP[0][1]);
+          d[1] = make_ulonglong2(ReP[0][2], ReP[0][3]);
+          d[2] = make_ulonglong2(ImP[0][0], ImP[0][1]);
+          d[3] = make_ulonglong2(ImP[0][2], ImP[0][3]);
         }
         __syncwarp();
       }
-      if (r == p) pivstep = k;
-      if (pivstep > k) {
-        const float* ur = sm.prow_re[par][src];
-        const float* ui = sm.prow_im[par][src];
-        const float2 l = cmulf(cur, crecip(make_float2(ur[kk], ui[kk])));
+      if (r == p) {
+        pivstep = k;
+        // the pivot row of step kk (pivot order) for the panel's diagonal blocks
+        ulonglong2* dr = reinterpret_cast<ulonglong2*>(sm.dre[kk]);
+        ulonglong2* di = reinterpret_cast<ulonglong2*>(sm.dim[kk]);
+        dr[0] = make_ulonglong2(ReP[0][0], ReP[0][1]);
+        dr[1] = make_ulonglong2(ReP[0][2], ReP[0][3]);
+        di[0] = make_ulonglong2(ImP[0][0], ImP[0][1]);
+        di[1] = make_ulonglong2(ImP[0][2], ImP[0][3]);
+      }
+      if (pivstep > k) {  // rows not chosen yet: rank-1 update of the panel block
+        const float* ur = sm.prow[par][src];
+        const float2 l = cmulf(cur, crecip(make_float2(ur[kk], ur[8 + kk])));
         const u64 NLx = pk(-l.x, -l.x), Ly = pk(l.y, l.y), NLy = pk(-l.y, -l.y);
         const u64* urp = reinterpret_cast<const u64*>(ur);
-        const u64* uip = reinterpret_cast<const u64*>(ui);
+        const u64* uip = reinterpret_cast<const u64*>(ur + 8);
 #pragma unroll
-        for (int m = (kk + 1) / 2; m < 4; ++m) {  // panel pairs right of column kk
+        for (int m = (kk + 1) / 2; m < 4; ++m) {  // pairs right of column kk
           const u64 UX = urp[m], UY = uip[m];
           ReP[0][m] = ffma2(Ly, UY, ffma2(NLx, UX, ReP[0][m]));
           ImP[0][m] = ffma2(NLy, UX, ffma2(NLx, UY, ImP[0][m]));
         }
         set_elem(ReP[0], ImP[0], kk, l);
+      }
+    }
+
+    // ---- panel end ----
+    gsync<NM>();  // every step's pivot row recorded in dre/dim
+    const bool fin = pivstep < 8 * kb;            // chosen in an earlier panel
+    const bool pan = !fin && pivstep < 8 * kb + 8;  // chosen in this panel
+    const int ii = pan ? pivstep - 8 * kb : 0;
+    // V_b = U_bb^-1 (threads 0..7, column r) and W_b = L_bb^-1 (threads 8..15, column r - 8;
+    // both by the 8 threads of an 8-thread group)
+    if (r < 8) {
+      const int c = r;
+      float2 v[8];
+#pragma unroll
+      for (int i = 7; i >= 0; --i) {
+        float2 acc = make_float2(i == c ? 1.0f : 0.0f, 0.0f);
+#pragma unroll
+        for (int m = i + 1; m < 8; ++m) cms(acc, make_float2(sm.dre[i][m], sm.dim[i][m]), v[m]);
+        const float2 vi = cmulf(acc, crecip(make_float2(sm.dre[i][i], sm.dim[i][i])));
+        v[i] = (i > c) ? make_float2(0.0f, 0.0f) : vi;
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        sm.vre[i][c] = v[i].x;
+        sm.vim[i][c] = v[i].y;
+      }
+    }
+    if ((NM == 8 && r < 8) || (NM > 8 && r >= 8 && r < 16)) {
+      const int c = r & 7;
+      float2 v[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        float2 acc = make_float2(i == c ? 1.0f : 0.0f, 0.0f);
+#pragma unroll
+        for (int m = 0; m < i; ++m) cms(acc, make_float2(sm.dre[i][m], sm.dim[i][m]), v[m]);
+        v[i] = (i < c) ? make_float2(0.0f, 0.0f) : acc;
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        sm.wre[kb][i][c] = v[i].x;
+        sm.wim[kb][i][c] = v[i].y;
+      }
+    }
+    // lt L_bb = l (masked multipliers), from the last column to the first; block 0 then
+    // holds n = -lt (rows chosen earlier keep their U entries and use n = 0)
+    {
+      float2 lt[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const bool use = !fin && (!pan || j < ii);
+        lt[j] = use ? elem(ReP[0], ImP[0], j) : make_float2(0.0f, 0.0f);
+      }
+#pragma unroll
+      for (int j = 6; j >= 0; --j)
+#pragma unroll
+        for (int m = j + 1; m < 8; ++m) cms(lt[j], lt[m], make_float2(sm.dre[m][j], sm.dim[m][j]));
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        ReP[0][m] = fin ? ReP[0][m] : pk(-lt[2 * m].x, -lt[2 * m + 1].x);
+        ImP[0][m] = fin ? ImP[0][m] : pk(-lt[2 * m].y, -lt[2 * m + 1].y);
+      }
+    }
+    gsync<NM>();  // V_b, W_b in place; dre/dim read by everyone
+    if constexpr (NB > 1) {
+      if (nact > 1) {
+        // the panel's pivot rows publish their trailing blocks as they were before the panel
+        if (pan) {
+#pragma unroll
+          for (int b = 1; b < NB; ++b) {
+            if (b >= nact) break;
+            ulonglong2* dr = reinterpret_cast<ulonglong2*>(&sm.tre[ii][8 * (b - 1)]);
+            ulonglong2* di = reinterpret_cast<ulonglong2*>(&sm.tim[ii][8 * (b - 1)]);
+            dr[0] = make_ulonglong2(ReP[b][0], ReP[b][1]);
+            dr[1] = make_ulonglong2(ReP[b][2], ReP[b][3]);
+            di[0] = make_ulonglong2(ImP[b][0], ImP[b][1]);
+            di[1] = make_ulonglong2(ImP[b][2], ImP[b][3]);
+          }
+        }
+        gsync<NM>();  // trailing blocks published
+        // A_r,trail += n A_piv,trail (rows chosen earlier: n = 0)
 #pragma unroll
         for (int b = 1; b < NB; ++b) {
-          if (b >= nact) break;  // finished panels sit at the end: skip them by a jump
-          {
-            const ulonglong2 x0 = reinterpret_cast<const ulonglong2*>(ur)[2 * b];
-            const ulonglong2 x1 = reinterpret_cast<const ulonglong2*>(ur)[2 * b + 1];
-            const ulonglong2 y0 = reinterpret_cast<const ulonglong2*>(ui)[2 * b];
-            const ulonglong2 y1 = reinterpret_cast<const ulonglong2*>(ui)[2 * b + 1];
-            const u64 UX[4] = {x0.x, x0.y, x1.x, x1.y}, UY[4] = {y0.x, y0.y, y1.x, y1.y};
+          if (b >= nact) break;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const float2 nj = fin ? make_float2(0.0f, 0.0f) : elem(ReP[0], ImP[0], j);
+            const u64 NR = pk(nj.x, nj.x), NI = pk(nj.y, nj.y), NIn = pk(-nj.y, -nj.y);
+            const ulonglong2 t0 = reinterpret_cast<const ulonglong2*>(&sm.tre[j][8 * (b - 1)])[0];
+            const ulonglong2 t1 = reinterpret_cast<const ulonglong2*>(&sm.tre[j][8 * (b - 1)])[1];
+            const ulonglong2 s0 = reinterpret_cast<const ulonglong2*>(&sm.tim[j][8 * (b - 1)])[0];
+            const ulonglong2 s1 = reinterpret_cast<const ulonglong2*>(&sm.tim[j][8 * (b - 1)])[1];
+            const u64 TR[4] = {t0.x, t0.y, t1.x, t1.y}, TI[4] = {s0.x, s0.y, s1.x, s1.y};
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
-              ReP[b][m] = ffma2(Ly, UY[m], ffma2(NLx, UX[m], ReP[b][m]));
-              ImP[b][m] = ffma2(NLy, UX[m], ffma2(NLx, UY[m], ImP[b][m]));
+              ReP[b][m] = ffma2(NIn, TI[m], ffma2(NR, TR[m], ReP[b][m]));
+              ImP[b][m] = ffma2(NI, TR[m], ffma2(NR, TI[m], ImP[b][m]));
             }
           }
         }
       }
     }
-    if constexpr (NB > 1) {  // rotate: the finished panel goes to the end
+    // block 0 of this panel's pivot rows: V_b's row ii
+    {
+      const ulonglong2 v0 = reinterpret_cast<const ulonglong2*>(sm.vre[ii])[0];
+      const ulonglong2 v1 = reinterpret_cast<const ulonglong2*>(sm.vre[ii])[1];
+      const ulonglong2 u0 = reinterpret_cast<const ulonglong2*>(sm.vim[ii])[0];
+      const ulonglong2 u1 = reinterpret_cast<const ulonglong2*>(sm.vim[ii])[1];
+      const u64 VR[4] = {v0.x, v0.y, v1.x, v1.y}, VI[4] = {u0.x, u0.y, u1.x, u1.y};
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        ReP[0][m] = pan ? VR[m] : ReP[0][m];
+        ImP[0][m] = pan ? VI[m] : ImP[0][m];
+      }
+    }
+    if constexpr (NB > 1) {
+      // rotate: the finished panel goes to the end
       u64 tr[4], ti[4];
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
@@ -366,144 +495,112 @@ __global__ void __launch_bounds__(NM >= 64 ? NM : 128, NM >= 64 ? 5 : 1) solve_m
     }
   }
 
-  // ---- inverses of the 8x8 diagonal blocks (pivot order), all blocks at once ----
   const int Mb = pivstep >> 3, ii = pivstep & 7;
-  float2 dg[8];
-#pragma unroll
-  for (int j = 0; j < 8; ++j) dg[j] = make_float2(0.0f, 0.0f);
-#pragma unroll
-  for (int b = 0; b < NB; ++b)
-    if (b == Mb)
-#pragma unroll
-      for (int j = 0; j < 8; ++j) dg[j] = elem(ReP[b], ImP[b], j);
-#pragma unroll
-  for (int s = 0; s < 8; ++s) {
-    if (ii == s) {  // W_s = e_s - sum_{m<s} L[s][m] W_m
-#pragma unroll
-      for (int j = 0; j < s; ++j) {
-        float2 acc = make_float2(0.0f, 0.0f);
-#pragma unroll
-        for (int m = j; m < s; ++m) cma(acc, dg[m], sm.Wb[Mb][m][j]);
-        sm.Wb[Mb][s][j] = make_float2(-acc.x, -acc.y);
-      }
-      sm.Wb[Mb][s][s] = make_float2(1.0f, 0.0f);
-#pragma unroll
-      for (int j = s + 1; j < 8; ++j) sm.Wb[Mb][s][j] = make_float2(0.0f, 0.0f);
-    }
-    if (ii == 7 - s) {  // V_i = (e_i - sum_{m>i} U[i][m] V_m) / U[i][i], i = 7 - s
-      const int i = 7 - s;
-      const float2 dinv = crecip(dg[i]);
-#pragma unroll
-      for (int j = 0; j < i; ++j) sm.Vb[Mb][i][j] = make_float2(0.0f, 0.0f);
-      sm.Vb[Mb][i][i] = dinv;
-#pragma unroll
-      for (int j = i + 1; j < 8; ++j) {
-        float2 acc = make_float2(0.0f, 0.0f);
-#pragma unroll
-        for (int m = i + 1; m <= j; ++m) cma(acc, dg[m], sm.Vb[Mb][m][j]);
-        const float2 v = cmulf(acc, dinv);
-        sm.Vb[Mb][i][j] = make_float2(-v.x, -v.y);
-      }
-    }
-    gsync<NM>();
-  }
-  // diagonal block <- W (strictly lower) and V (upper); off-diagonal blocks premultiplied
-  // and negated in place: -(l W_b) for multipliers (columns in increasing order: entry j
-  // reads columns >= j only), -(u V_b) for U entries (decreasing order: reads <= j only)
-#pragma unroll
-  for (int b = 0; b < NB; ++b) {
-    if (b == Mb) {
-#pragma unroll
-      for (int j = 0; j < 8; ++j) set_elem(ReP[b], ImP[b], j, (j < ii) ? sm.Wb[b][ii][j] : sm.Vb[b][ii][j]);
-    } else if (b < Mb) {
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        float2 acc = elem(ReP[b], ImP[b], j);  // W_b[j][j] = 1
-#pragma unroll
-        for (int m = j + 1; m < 8; ++m) cma(acc, elem(ReP[b], ImP[b], m), sm.Wb[b][m][j]);
-        set_elem(ReP[b], ImP[b], j, make_float2(-acc.x, -acc.y));
-      }
-    } else {
-#pragma unroll
-      for (int j = 7; j >= 0; --j) {
-        float2 acc = make_float2(0.0f, 0.0f);
-#pragma unroll
-        for (int m = 0; m <= j; ++m) cma(acc, elem(ReP[b], ImP[b], m), sm.Vb[b][m][j]);
-        set_elem(ReP[b], ImP[b], j, make_float2(-acc.x, -acc.y));
-      }
-    }
-  }
 
-  // ---- block triangular solve (branch-free): returns the unknown x_r ----
-  auto lu_solve = [&](float2 rhs) -> float2 {
+  // ---- the per-system values again (reloaded rather than kept through the LU) ----
+  asm volatile("" ::: "memory");
+  SysInfo si = sys_info(a, sys);
+  const bool valid = in_range && si.N <= NM;  // larger systems: solve_large.cu
+  if (!valid) si.N = 0;
+  const int N = si.N;
+  const double w = si.w;
+  const float w32 = (float)w;
+  const bool real_row = r < N;
+  const bool bwd = a.rhs_in != nullptr;
+  cd Dr = {0.0, 0.0};
+  if (real_row) Dr = {a.R[si.k0 + r], -1.0 / (w * a.C[si.b * a.n_ports + si.k0 + r])};
+  const int64_t mo = a.t.nn_off[si.s];
+  const float* __restrict__ Mh = a.M32hi + mo;
+  const float* __restrict__ Ml = a.M32lo + mo;
+
+  // ---- solve A x = c with the blocked factors; returns the unknown of column pivstep ----
+  auto lu_solve = [&](float2 c) -> float2 {
+    float2 acc = c, yt = c;
 #pragma unroll
     for (int kb = 0; kb < NB; ++kb) {
-      if (Mb == kb) sm.bp[kb & 1][ii] = rhs;
-      gsync<NM>();
-      const bool piv = Mb == kb, later = Mb > kb;
-      float2 acc1 = make_float2(0.0f, 0.0f);
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        // the mask is applied to the freshly loaded value, so that no masked copy of the
-        // (loop-invariant) coefficients is kept in registers
-        const bool use = later || (piv && j < ii);
-        const float2 v = sm.bp[kb & 1][j];
-        cma((j & 1) ? acc1 : rhs, elem(ReP[kb], ImP[kb], j), use ? v : make_float2(0.0f, 0.0f));
+      const int buf = kb & 1;
+      if (Mb == kb) {
+        sm.sre[buf][ii] = acc.x;
+        sm.sim[buf][ii] = acc.y;
+        yt = acc;
       }
-      rhs.x += acc1.x;
-      rhs.y += acc1.y;
+      gsync<NM>();
+      const float2 t = bdot(ReP[kb], ImP[kb], sm.sre[buf], sm.sim[buf]);
+      acc.x += t.x;
+      acc.y += t.y;
     }
+    sm.yre[pivstep] = yt.x;
+    sm.yim[pivstep] = yt.y;
+    gsync<NM>();
+    acc = bdot(reinterpret_cast<const u64*>(sm.wre[Mb][ii]), reinterpret_cast<const u64*>(sm.wim[Mb][ii]),
+               &sm.yre[8 * Mb], &sm.yim[8 * Mb]);  // z = W yt (W rows via the same product)
+    float2 x = make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int kb = NB - 1; kb >= 0; --kb) {
-      if (Mb == kb) sm.bq[kb & 1][ii] = rhs;
-      gsync<NM>();
-      const bool piv = Mb == kb, earlier = Mb < kb;
-      float2 acc = piv ? make_float2(0.0f, 0.0f) : rhs;
-      float2 acc1 = make_float2(0.0f, 0.0f);
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const bool use = earlier || (piv && j >= ii);
-        const float2 v = sm.bq[kb & 1][j];
-        cma((j & 1) ? acc1 : acc, elem(ReP[kb], ImP[kb], j), use ? v : make_float2(0.0f, 0.0f));
+      if (Mb == kb) {
+        sm.sre[0][ii] = acc.x;
+        sm.sim[0][ii] = acc.y;
       }
-      rhs = make_float2(acc.x + acc1.x, acc.y + acc1.y);
+      gsync<NM>();
+      const float2 t = bdot(ReP[kb], ImP[kb], sm.sre[0], sm.sim[0]);
+      if (Mb == kb) {
+        x = t;
+        sm.sre[1][ii] = t.x;
+        sm.sim[1][ii] = t.y;
+      }
+      gsync<NM>();
+      const float2 t2 = bdot(ReP[kb], ImP[kb], sm.sre[1], sm.sim[1]);
+      acc.x -= t2.x;
+      acc.y -= t2.y;
     }
-    sm.xs[pivstep] = rhs;
-    gsync<NM>();
-    const float2 out = sm.xs[r];
-    gsync<NM>();
-    return out;
+    return x;
   };
 
-  // publish the FP64 iterate of this thread's unknown and its double-float split
-  auto publish = [&](cd x) {
-    sm.x64[r] = make_double2(x.x, x.y);
-    const float rh = (float)x.x, ih = (float)x.y;
-    sm.xhl[r] = make_ulonglong2(pk(rh, ih), pk((float)(x.x - (double)rh), (float)(x.y - (double)ih)));
-    gsync<NM>();
+  // solve, put the unknowns in column order (xc) and reduce max |re| + |im| over the
+  // group in the same exchange
+  auto solve_perm = [&](float2 c, float* dmax) -> float2 {
+    const float2 x = lu_solve(c);
+    sm.xc[pivstep] = x;
+    float m = fabsf(x.x) + fabsf(x.y);
+    if constexpr (NM >= 64) {
+      unsigned u;
+      asm volatile("redux.sync.max.u32 %0, %1, 0xffffffff;" : "=r"(u) : "r"(__float_as_uint(m)));
+      if ((r & 31) == 0) sm.umax[r >> 5] = u;
+      __syncthreads();
+      unsigned best = sm.umax[0];
+#pragma unroll
+      for (int q = 1; q < SmemV4<NM>::NW; ++q) best = max(best, sm.umax[q]);
+      m = __uint_as_float(best);
+    } else {
+      __syncwarp();
+      for (int off = NM >> 1; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off, NM));
+    }
+    *dmax = m;
+    return sm.xc[r];
   };
 
-  // accurate residual of row r: rhs_r - sum_j A_rj x_j, sum_j M_rj x_j in double-float
+  // accurate residual of row r with the FP32 iterate in xc: rhs_r - sum_j A_rj x_j, the
+  // sum over M_rj x_j in double-float (M = hi + lo exactly, x exact in FP32)
   auto residual = [&](cd rhs) -> cd {
-    const double2 xr = sm.x64[r];
-    if (!real_row) return {rhs.x - xr.x, rhs.y - xr.y};
+    const float2 xr = sm.xc[r];
+    if (!real_row) return {rhs.x - (double)xr.x, rhs.y - (double)xr.y};
     u64 S[2] = {0ull, 0ull}, Lo[2] = {0ull, 0ull};  // (re, im) high and low parts, 2 chains
     const u64 neg1 = pk(-1.0f, -1.0f);
+    const u64* xv = reinterpret_cast<const u64*>(sm.xc);
     for (int j0 = 0; j0 < N; j0 += 2) {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int j = j0 + h;
         if (j < N) {
-          const float2 m = make_float2(__ldg(Mh + j * N + r), __ldg(Ml + j * N + r));
-          const ulonglong2 xj = sm.xhl[j];
-          const u64 A = pk(m.x, m.x), Al = pk(m.y, m.y);
-          const u64 p = fmul2(A, xj.x);
-          u64 e = ffma2(A, xj.x, fmul2(p, neg1));
-          e = ffma2(A, xj.y, e);
-          e = ffma2(Al, xj.x, e);
-          const u64 t = fadd2(S[h], p);
+          const float mh = __ldg(Mh + j * N + r), ml = __ldg(Ml + j * N + r);
+          const u64 xj = xv[j];
+          const u64 A = pk(mh, mh);
+          const u64 pr = fmul2(A, xj);
+          u64 e = ffma2(A, xj, fmul2(pr, neg1));
+          e = ffma2(pk(ml, ml), xj, e);
+          const u64 t = fadd2(S[h], pr);
           const u64 z = fsub2(t, S[h]);
-          const u64 err = fadd2(fsub2(S[h], fsub2(t, z)), fsub2(p, z));
+          const u64 err = fadd2(fsub2(S[h], fsub2(t, z)), fsub2(pr, z));
           S[h] = t;
           Lo[h] = fadd2(Lo[h], fadd2(err, e));
         }
@@ -512,26 +609,25 @@ __global__ void __launch_bounds__(NM >= 64 ? NM : 128, NM >= 64 ? 5 : 1) solve_m
     const float2 s0 = up(S[0]), s1 = up(S[1]), l0 = up(Lo[0]), l1 = up(Lo[1]);
     const double Sr = ((double)s0.x + (double)l0.x) + ((double)s1.x + (double)l1.x);
     const double Si = ((double)s0.y + (double)l0.y) + ((double)s1.y + (double)l1.y);
-    const double ax = Dr.x * xr.x - Dr.y * xr.y;
-    const double ay = Dr.x * xr.y + Dr.y * xr.x;
+    const double ax = Dr.x * (double)xr.x - Dr.y * (double)xr.y;
+    const double ay = Dr.x * (double)xr.y + Dr.y * (double)xr.x;
     return {rhs.x - ax + w * Si, rhs.y - ay - w * Sr};
   };
 
-  // r -= A d for the correction d just solved (in sm.xs), FP32
+  // r -= A d for the correction d in xc (FP32)
   auto residual_update = [&](cd res, float2 dr) -> cd {
     if (!real_row) return {res.x - dr.x, res.y - dr.y};
     u64 S0 = 0ull, S1 = 0ull;
+    const u64* xv = reinterpret_cast<const u64*>(sm.xc);
     int j = 0;
     for (; j + 1 < N; j += 2) {
       const float m0 = __ldg(Mh + j * N + r), m1 = __ldg(Mh + (j + 1) * N + r);
-      const float2 d0 = sm.xs[j], d1 = sm.xs[j + 1];
-      S0 = ffma2(pk(m0, m0), pk(d0.x, d0.y), S0);
-      S1 = ffma2(pk(m1, m1), pk(d1.x, d1.y), S1);
+      S0 = ffma2(pk(m0, m0), xv[j], S0);
+      S1 = ffma2(pk(m1, m1), xv[j + 1], S1);
     }
     if (j < N) {
       const float m0 = __ldg(Mh + j * N + r);
-      const float2 d0 = sm.xs[j];
-      S0 = ffma2(pk(m0, m0), pk(d0.x, d0.y), S0);
+      S0 = ffma2(pk(m0, m0), xv[j], S0);
     }
     const float2 s = make_float2(up(S0).x + up(S1).x, up(S0).y + up(S1).y);
     const float dx = (float)Dr.x, dy = (float)Dr.y;
@@ -570,19 +666,20 @@ __global__ void __launch_bounds__(NM >= 64 ? NM : 128, NM >= 64 ? 5 : 1) solve_m
     }
     cd xk = {0.0, 0.0};
     cd res = rhs64;
-    float dprev = 0.0f;
+    float dprev = 0.0f, xm0 = 0.0f;
     bool conv = max_it == 0;
 #pragma unroll 1
     for (int it = 0;; ++it) {
-      const float2 d = lu_solve(make_float2((float)res.x, (float)res.y));
+      float dm;
+      const float2 d = solve_perm(make_float2((float)res.x, (float)res.y), &dm);
       xk.x += (double)d.x;
       xk.y += (double)d.y;
-      const float dm = gmax<NM>(fabsf(d.x) + fabsf(d.y), sm, r);
       bool stop = it >= max_it;
-      if (it > 0) {
-        const float xm = gmax<NM>((float)(fabs(xk.x) + fabs(xk.y)), sm, r);
+      if (it == 0) {
+        xm0 = dm;
+      } else {
         const float est = dm * fminf(1.0f, dm / fmaxf(dprev, 1e-30f));
-        conv = conv || (est <= tol * xm);
+        conv = conv || (est <= tol * xm0);
         stop = stop || conv || !(dm <= 0.5f * dprev);
       }
       dprev = dm;
@@ -591,12 +688,7 @@ __global__ void __launch_bounds__(NM >= 64 ? NM : 128, NM >= 64 ? 5 : 1) solve_m
       } else {
         if (stop) break;
       }
-      if (it == 0) {
-        publish(xk);
-        res = residual(rhs64);
-      } else {
-        res = residual_update(res, d);
-      }
+      res = (it == 0) ? residual(rhs64) : residual_update(res, d);
     }
     conv_all = conv_all && conv;
     bad = bad || (real_row && !(isfinite(xk.x) && isfinite(xk.y)));
@@ -643,8 +735,9 @@ __global__ void __launch_bounds__(NM >= 64 ? NM : 128, NM >= 64 ? 5 : 1) solve_m
         }
       }
       if (has_obj) {
-        // objective at the loss points (FP32 sums of FP32 H rows, FP64 per-point terms)
-        publish(x);
+        // objective at the loss points (FP32 sums of FP32 H rows, FP32 per-point terms)
+        sm.xc[r] = make_float2((float)x.x, (float)x.y);
+        gsync<NM>();
         const int L = a.loss_off[si.s + 1] - a.loss_off[si.s];
         const float* Hl = a.Hl32 + a.t.ln_off[si.s];
         const float* HlT = a.HlT32 + a.t.ln_off[si.s];  // [k][l]: lanes l read consecutively
@@ -652,6 +745,8 @@ __global__ void __launch_bounds__(NM >= 64 ? NM : 128, NM >= 64 ? 5 : 1) solve_m
         const double* tb = a.target + (a.target_per_cfg ? si.b * a.sumFL * tw : 0) +
                            (a.t.fl_off[si.s] + (int64_t)si.f * L) * tw;
         const int64_t wo = a.t.fl_off[si.s] + (int64_t)si.f * L;  // weight / offset base
+        const u64* xv = reinterpret_cast<const u64*>(sm.xc);
+        const u64* gv = reinterpret_cast<const u64*>(sm.Gs);
         double lsum = 0.0;
         u64 U = 0ull;
         for (int c0 = 0; c0 < a.max_loss; c0 += NM) {
@@ -662,12 +757,12 @@ __global__ void __launch_bounds__(NM >= 64 ? NM : 128, NM >= 64 ? 5 : 1) solve_m
             int k = 0;
             for (; k + 1 < N; k += 2) {
               const float h0 = HlT[(int64_t)k * L + l], h1 = HlT[(int64_t)(k + 1) * L + l];
-              b0 = ffma2(pk(h0, h0), sm.xhl[k].x, b0);
-              b1 = ffma2(pk(h1, h1), sm.xhl[k + 1].x, b1);
+              b0 = ffma2(pk(h0, h0), xv[k], b0);
+              b1 = ffma2(pk(h1, h1), xv[k + 1], b1);
             }
             if (k < N) {
               const float h0 = HlT[(int64_t)k * L + l];
-              b0 = ffma2(pk(h0, h0), sm.xhl[k].x, b0);
+              b0 = ffma2(pk(h0, h0), xv[k], b0);
             }
             float2 bl = make_float2(up(b0).x + up(b1).x, up(b0).y + up(b1).y);
             float wl = 1.0f;
@@ -690,8 +785,7 @@ __global__ void __launch_bounds__(NM >= 64 ? NM : 128, NM >= 64 ? 5 : 1) solve_m
             const int lc = max(0, min(NM, L - c0));
             for (int q = 0; q < lc; ++q) {
               const float h = Hl[(int64_t)(c0 + q) * N + r];
-              const float2 g = sm.Gs[q];
-              U = ffma2(pk(h, h), pk(g.x, g.y), U);
+              U = ffma2(pk(h, h), gv[q], U);
             }
           }
           gsync<NM>();
@@ -718,24 +812,24 @@ __global__ void __launch_bounds__(NM >= 64 ? NM : 128, NM >= 64 ? 5 : 1) solve_m
 }
 
 template <int NM>
-static cudaError_t launch_v3(const SolveArgs& a, int64_t n_sys, cudaStream_t st) {
+static cudaError_t launch_v4(const SolveArgs& a, int64_t n_sys, cudaStream_t st) {
   constexpr int CT = NM >= 64 ? NM : 128;
   constexpr int G = CT / NM;
-  const size_t smem = sizeof(SmemV3<NM>) * G;
-  cudaError_t e = cudaFuncSetAttribute(solve_mixed_v3<NM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const size_t smem = sizeof(SmemV4<NM>) * G;
+  cudaError_t e = cudaFuncSetAttribute(solve_mixed_v4<NM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   const unsigned grid = (unsigned)((n_sys + G - 1) / G);
-  solve_mixed_v3<NM><<<grid, CT, smem, st>>>(a, n_sys);
+  solve_mixed_v4<NM><<<grid, CT, smem, st>>>(a, n_sys);
   note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_solve_mixed(const SolveArgs& a, int64_t n_sys, int max_ports, cudaStream_t st) {
-  if (max_ports <= 8) return launch_v3<8>(a, n_sys, st);
-  if (max_ports <= 16) return launch_v3<16>(a, n_sys, st);
-  if (max_ports <= 32) return launch_v3<32>(a, n_sys, st);
-  if (max_ports <= 64) return launch_v3<64>(a, n_sys, st);
+  if (max_ports <= 8) return launch_v4<8>(a, n_sys, st);
+  if (max_ports <= 16) return launch_v4<16>(a, n_sys, st);
+  if (max_ports <= 32) return launch_v4<32>(a, n_sys, st);
+  if (max_ports <= 64) return launch_v4<64>(a, n_sys, st);
   return cudaErrorNotSupported;
 }
 
