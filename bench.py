@@ -42,8 +42,34 @@ WORKLOAD = ("array_8x8: 8x8 square loops (side 50 mm, pitch 55 mm, 16 segments/s
 # proportional to the configurations); see profiles/.
 TRAFFIC = {"superpose_tc.cu": {"sha256_12": "07c09890dea6", "bytes": 4 * (33.925376e6 + 476.838144e6)},
            "solve_mixed.cu": {"sha256_12": "ec9cb3ec34c8", "bytes": 4 * (1.00224e6 + 0)}}
-# FP32 peak from unit counts and clocks: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def fp32_peak():
+    """FP32 FMA throughput of this GPU for the ALU rooflines: measured by the probe program
+    built beside libmts.so (packed fma.rn.f32x2 chains, best of five launches), else derived
+    from the device's SM count and clock (128 FP32 lanes x 2 flops per SM and cycle)."""
+    import torch
+    from paper_2503_18479_gb300.build_lib import PEAK_PROBE
+    try:
+        r = subprocess.run([PEAK_PROBE], capture_output=True, text=True, timeout=120)
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+        return {"tflops": float(d["ffma2_tflops"]), "ffma_tflops": float(d["ffma_tflops"]),
+                "fp64_tflops": float(d["dfma_tflops"]),
+                "source": "measured: fp32_peak probe (packed fma.rn.f32x2 chains, 8 x 256-thread "
+                          f"CTAs per SM, best of 5), {d['sms']} SMs at {d['clock_mhz']:.0f} MHz"}
+    except Exception as e:  # derived from the device properties
+        props = torch.cuda.get_device_properties(torch.cuda.current_device())
+        sms = props.multi_processor_count
+        mhz = float(subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"],
+                                   capture_output=True, text=True).stdout.split()[0])
+        return {"tflops": sms * 128 * 2 * mhz * 1e6 / 1e12, "fp64_tflops": sms * 2 * 2 * mhz * 1e6 / 1e12,
+                "source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flops x {mhz:.0f} MHz "
+                          f"(probe unavailable: {type(e).__name__})"}
+
+
+def lu_flops(N: int) -> int:
+    """Real flops of one complex LU factorisation, 8N^3/3."""
+    return (8 * N ** 3) // 3
 
 
 def solve_flops_per_system(N: int, L: int) -> int:
@@ -70,9 +96,10 @@ def parse():
     ap.add_argument("--no-fp64-path", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--n-cfg", type=int, default=N_CFG, help="configurations per GPU (profiling runs)")
-    ap.add_argument("--other-workloads", default="loop,line,fit,fit8x8,sroute",
+    ap.add_argument("--other-workloads", default="loop,line,ragged,32x32,fit,fit8x8,sroute",
                     help="comma list of extra workloads timed after the headline (loop, line, "
-                         "ragged, 32x32; empty for none); reported under other_workloads")
+                         "ragged, 32x32, fit, fit8x8, sroute; empty for none); reported under "
+                         "other_workloads")
     return ap.parse_args()
 
 
@@ -181,6 +208,7 @@ def run_ours(args, rank, world, local):
     build()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
+    peak32 = fp32_peak()
     if world > 1:
         tdist.init_process_group("nccl", device_id=dev)
     wl = W.array_8x8(seed=rank, n_cfg=args.n_cfg)
@@ -326,13 +354,45 @@ def run_ours(args, rank, world, local):
     st0 = wl.structures[0]
     flops = n_cfg * solve_flops_per_system(st0.n_ports, st0.n_loss)
     tf = flops / (solve_ms / 1e3) / 1e12
-    roof_solve = {"kernel": "solve_mixed_v3<64>" if prec != "fp64" else "solve_fp64_kernel<64>",
-                  "bound": "alu", "achieved": tf, "peak": FP32_PEAK_TFLOPS,
-                  "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz", "unit": "TFLOP/s",
-                  "frac": tf / FP32_PEAK_TFLOPS, "traffic": traffic_of("solve_mixed.cu"),
+    alu_peak = peak32["tflops"] if prec != "fp64" else peak32["fp64_tflops"]
+    roof_solve = {"kernel": "solve_mixed_v4<64>" if prec != "fp64" else "solve_fp64_kernel<64>",
+                  "bound": "alu", "achieved": tf, "peak": alu_peak,
+                  "peak_source": peak32["source"] + (" (FP64 chains)" if prec == "fp64" else ""),
+                  "unit": "TFLOP/s", "frac": tf / alu_peak, "traffic": traffic_of("solve_mixed.cu"),
                   "algorithmic_flops_per_launch": flops, "avg_launch_ms": solve_ms,
                   "note": "duration includes the plan and reduce launches of mts_solve (~2 %)"}
     dominant, secondary = (roof_solve, roof_gemm) if solve_ms >= gemm_ms else (roof_gemm, roof_solve)
+
+    # ---- backward with a full-field cotangent grad_B (dL/dRe B + j dL/dIm B for every
+    # configuration and point): u = H^T conj(grad_B), mu = A^-1 u, dloss/dC
+    backward_field = None
+    if rank == 0:
+        gB = torch.randn((n_cfg, sim.sumFP), dtype=sim.b_dtype, device=dev)
+        gC2 = torch.empty_like(grad_C)
+        nv.mts_backward(sim.pb, sim.prec, sim.basis, ev, tape, gB, gl, gC2)
+        torch.cuda.synchronize()
+        kb = 5
+        msb = 0.0
+        for _ in range(kb):
+            flush.fill_(1)
+            b0 = torch.cuda.Event(enable_timing=True)
+            b1 = torch.cuda.Event(enable_timing=True)
+            b0.record(st)
+            nv.mts_backward(sim.pb, sim.prec, sim.basis, ev, tape, gB, gl, gC2)
+            b1.record(st)
+            b1.synchronize()
+            msb += b0.elapsed_time(b1)
+        msb /= kb
+        gb_bytes = gB.numel() * gB.element_size()
+        backward_field = {"ms": msb, "grad_B_bytes": gb_bytes,
+                          "grad_B_read_GBs": gb_bytes / (msb / 1e3) / 1e9,
+                          "hbm_frac_of_call": gb_bytes / (msb / 1e3) / 1e9 / hbm_peak,
+                          "steps": kb,
+                          "note": "one mts_backward call with a full-field cotangent (random, "
+                                  "complex64) and the loss cotangent: u = H^T conj(grad_B) over all "
+                                  "points, the adjoint solve of every system, dloss/dC"}
+        del gB, gC2
+        torch.cuda.empty_cache()
 
     # ---- FP64 GPU path on the same workload (context for the mixed-precision speed-up)
     fp64_path = None
@@ -364,6 +424,8 @@ def run_ours(args, rank, world, local):
         del B64, sim64
         torch.cuda.empty_cache()
 
+    stash = {}
+    setup = basis_setup(sim, wl, dev, peak32) if rank == 0 else None
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": max_ms / K, "higher_is_better": True,
@@ -397,20 +459,80 @@ def run_ours(args, rank, world, local):
         "wall_s_timed_loop": t_wall,
         "status": {"code": code, "systems_flagged": n_bad},
         "fp64_path": fp64_path,
-        "other_workloads": other_workloads(args, dev, prec) if rank == 0 else None,
+        "fp32_peak": peak32,
+        "backward_field": backward_field,
+        "basis_setup": setup,
+        "other_workloads": other_workloads(args, dev, prec, peak32, stash) if rank == 0 else None,
     }
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"], out["accuracy"] = cpu_baseline_and_accuracy(wl, sim, C, B, loss, grad_C, gl, tape, ev)
+        if "32x32" in stash and out.get("other_workloads"):
+            out["other_workloads"]["32x32"]["accuracy_per_path"] = path_errors_32x32(stash["32x32"])
     if world > 1:
         tdist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out))
 
 
-def other_workloads(args, dev, prec):
+# Algorithmic flops of one segment-point pair of the Biot-Savart basis (closed form of the
+# segment's Bz: R2 = R1 + d 3, (R1 x d)_z 3, |R1|^2 and |R2|^2 10, R1.R2 5, two square roots
+# 2, n1 n2 (n1 n2 + R1.R2) 3, (n1 + n2) / den 2, times the cross product 1, accumulate 1;
+# a square root or a division counts as one flop)
+BASIS_FLOPS_PER_PAIR = 30
+
+
+def basis_setup(sim, wl, dev, peak):
+    """Time mts_build_basis for the workload (CUDA events; the basis is rebuilt in place)
+    and split it into the Biot-Savart basis H and the partial inductances M by rebuilding a
+    copy of the problem with one field point per structure (M only)."""
+    import dataclasses
+
+    import torch
+
+    from paper_2503_18479_gb300 import native as nv
+
+    def timed_build(s):
+        nv.mts_build_basis(s.pb, s.prec, s.basis)
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record()
+        nv.mts_build_basis(s.pb, s.prec, s.basis)
+        a1.record()
+        a1.synchronize()
+        return a0.elapsed_time(a1)
+
+    from paper_2503_18479_gb300.simulator import Simulator
+    t_all = timed_build(sim)
+    one = [dataclasses.replace(st, px=st.px[:1], py=st.py[:1], pz=st.pz[:1], loss_idx=st.loss_idx[:0],
+                               pcomp=None if getattr(st, "pcomp", None) is None else st.pcomp[:1])
+           for st in wl.structures]
+    wl1 = dataclasses.replace(wl, structures=one, target=None, target_rule=None)
+    sim1 = Simulator(wl1, "mixed", device=dev)
+    t_m = timed_build(sim1)
+    del sim1
+    torch.cuda.empty_cache()
+    seg = [len(st.vx) for st in wl.structures]
+    pairs_h = sum(st.n_points * S for st, S in zip(wl.structures, seg))
+    pairs_m = sum(S * (S + 1) // 2 for S in seg)  # loop pairs k <= l, every segment pair
+    t_h = max(t_all - t_m, 1e-6)
+    tf = pairs_h * BASIS_FLOPS_PER_PAIR / (t_h / 1e3) / 1e12
+    return {"ms": t_all, "ms_field_basis_H": t_h, "ms_inductances_M": t_m,
+            "segment_point_pairs": pairs_h, "segment_pairs": pairs_m,
+            "H_pairs_per_s": pairs_h / (t_h / 1e3), "M_pairs_per_s": pairs_m / (t_m / 1e3),
+            "H_roofline": {"bound": "alu", "achieved": tf, "peak": peak["tflops"], "unit": "TFLOP/s",
+                           "frac": tf / peak["tflops"],
+                           "flops_per_pair": BASIS_FLOPS_PER_PAIR,
+                           "note": "FP32 closed form per segment-point pair; FP64 near-field terms and "
+                                   "the near-field test are not counted"},
+            "note": "M time from a rebuild with one field point per structure; H = total - M"}
+
+
+def other_workloads(args, dev, prec, peak, stash):
     """The same step (solve + objective + adjoint, superposition, gradient) on the other
     synthetic workloads: configs/s, systems/s and field points/s at one GPU, CUDA events
-    over a few steps with the L2 flushed between them."""
+    over a few steps with the L2 flushed between them, the split between the solve call and
+    the superposition call, the LU's share of the FP32 peak, and the basis setup time."""
     import torch
 
     from paper_2503_18479_gb300 import native as nv
@@ -449,6 +571,7 @@ def other_workloads(args, dev, prec):
         if wl.target is None:  # timing only: a zero target costs the same work
             wl.target = np.zeros(sum(s.n_freq * s.n_loss for s in wl.structures))
         sim = Simulator(wl, prec, device=dev)
+        setup = basis_setup(sim, wl, dev, peak) if name in ("32x32",) else None
         n = wl.n_cfg
         C = torch.from_numpy(wl.C).to(dev)
         ev = sim.make_eval(C, True)
@@ -457,11 +580,20 @@ def other_workloads(args, dev, prec):
         loss = torch.empty((n, sim.n_struct), dtype=torch.float64, device=dev)
         g = torch.empty((n, sim.n_ports), dtype=torch.float64, device=dev)
         gl = torch.ones((n, sim.n_struct), dtype=torch.float64, device=dev)
+        marks = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
 
-        def step():
+        def step(m=None):
+            if m:
+                m[0].record(st)
             nv.mts_solve(sim.pb, sim.prec, sim.basis, ev, None, loss, tape)
+            if m:
+                m[1].record(st)
             nv.mts_superpose(sim.pb, sim.prec, sim.basis, ev, tape, B)
+            if m:
+                m[2].record(st)
             nv.mts_backward(sim.pb, sim.prec, sim.basis, ev, tape, None, gl, g)
+            if m:
+                m[3].record(st)
 
         for _ in range(3):
             flush.fill_(1)
@@ -469,25 +601,65 @@ def other_workloads(args, dev, prec):
         torch.cuda.synchronize()
         code, bad = sim.status(tape, n)
         K = 10
-        ms = 0.0
+        ms = ms_solve = ms_sup = 0.0
         for _ in range(K):
             flush.fill_(1)
-            a0 = torch.cuda.Event(enable_timing=True)
-            a1 = torch.cuda.Event(enable_timing=True)
-            a0.record(st)
-            step()
-            a1.record(st)
-            a1.synchronize()
-            ms += a0.elapsed_time(a1)
-        ms /= K
+            step(marks)
+            marks[3].synchronize()
+            ms += marks[0].elapsed_time(marks[3])
+            ms_solve += marks[0].elapsed_time(marks[1])
+            ms_sup += marks[1].elapsed_time(marks[2])
+        ms, ms_solve, ms_sup = ms / K, ms_solve / K, ms_sup / K
         n_sys = n * sum(s.n_freq for s in wl.structures)
-        res[name] = {"workload": desc, "precision": prec, "ms_per_step": ms,
-                     "configs_per_s": n / (ms / 1e3), "systems_per_s": n_sys / (ms / 1e3),
-                     "field_points_per_s": n * sim.sumFP / (ms / 1e3), "steps": K,
-                     "status": {"code": code, "systems_flagged": bad}}
+        lu = n * sum(s.n_freq * lu_flops(s.n_ports) for s in wl.structures)
+        lu_tf = lu / (ms_solve / 1e3) / 1e12
+        bytes_b = n * sim.sumFP * (16 if prec == "fp64" else 8)
+        mac = 8 * n * sum(s.n_freq * s.n_points * s.n_ports for s in wl.structures)  # complex B = H I
+        r = {"workload": desc, "precision": prec, "ms_per_step": ms,
+             "configs_per_s": n / (ms / 1e3), "systems_per_s": n_sys / (ms / 1e3),
+             "field_points_per_s": n * sim.sumFP / (ms / 1e3), "steps": K,
+             "breakdown_ms": {"solve_loss_adjoint": ms_solve, "superpose": ms_sup,
+                              "backward": ms - ms_solve - ms_sup},
+             "solve_roofline": {"bound": "alu", "achieved": lu_tf, "peak": peak["tflops"], "unit": "TFLOP/s",
+                                "frac": lu_tf / peak["tflops"], "algorithmic_flops": lu,
+                                "note": "LU flops 8N^3/3 only, over the whole mts_solve call (refinement, "
+                                        "objective and adjoint not counted)"},
+             "superpose": {"B_bytes": bytes_b, "achieved_GBs": bytes_b / (ms_sup / 1e3) / 1e9,
+                           "achieved_TFLOPs_real": 2 * mac / 8 / (ms_sup / 1e3) / 1e12},
+             "status": {"code": code, "systems_flagged": bad}}
+        if setup:
+            r["basis_setup"] = setup
+        res[name] = r
+        if name == "32x32":
+            stash["32x32"] = path_samples(wl, sim, C, B, dev, prec)
         del sim, B, tape
         torch.cuda.empty_cache()
     return res
+
+
+def path_samples(wl, sim, C, B, dev, prec, n_cfg=2, n_pts=4096, seed=11):
+    """B of the first n_cfg configurations at n_pts sampled field points from every
+    precision path (MTS_MIXED and MTS_BF16 on the tensor cores, MTS_FP64) for the per-path
+    error against the oracle; the timed step's own precision comes from its output."""
+    import torch
+
+    from paper_2503_18479_gb300.simulator import Simulator
+    st = wl.structures[0]
+    rng = np.random.Generator(np.random.PCG64(seed))
+    idx = np.sort(rng.choice(st.n_points, size=min(n_pts, st.n_points), replace=False))
+    it = torch.from_numpy(idx).to(dev)
+    out = {"idx": idx, "C": wl.C[:n_cfg], prec: B[:n_cfg][:, it].cpu().numpy()}
+    for p in ("mixed", "bf16", "fp64"):
+        if p in out:
+            continue
+        s = Simulator(wl, p, device=dev)
+        if p != "fp64":  # a few configurations: force the tensor-core superposition path
+            s.tuning["simt_max_sys"] = -1
+        o = s.forward(C[:n_cfg], want_B=True, want_loss=False)
+        out[p] = o["B"][:, it].cpu().numpy()
+        del s, o
+        torch.cuda.empty_cache()
+    return out
 
 
 def sroute_bench(desc, dev, prec, flush, K=10):
@@ -648,7 +820,8 @@ def cpu_baseline_and_accuracy(wl, sim, C, B, loss, grad_C, gl, tape, ev):
     cores = oracle.num_threads()
     base = {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n} of the 4096 configurations, forward (full field at all {wl.n_points} points) "
-                      f"+ loss + adjoint gradient, FP64, {cores} OpenMP threads; basis setup untimed"}
+                      f"+ loss + adjoint gradient, FP64, {cores} OpenMP threads; basis setup untimed",
+            "single_thread": oracle_single_thread()}
     # accuracy of the GPU path (last timed step) on the same configurations
     torch.cuda.synchronize()
     Bg = B[:n].cpu().numpy().reshape(n, 1, -1)
@@ -659,6 +832,58 @@ def cpu_baseline_and_accuracy(wl, sim, C, B, loss, grad_C, gl, tape, ev):
     acc = {"sample_configs": n, "B_rel_l2": rel(Bg, ref["B"]), "loss_rel_l2": rel(lg, ref["loss"]),
            "grad_rel_l2": rel(gg, g), "grad_cosine": float(ga @ gb / (np.linalg.norm(ga) * np.linalg.norm(gb)))}
     return base, acc
+
+
+def path_errors_32x32(smp):
+    """Relative L2 error of B from each precision path against the FP64 oracle on the
+    sampled configurations and field points of the 32x32 array (the oracle's own basis and
+    inductances of the full geometry)."""
+    import oracle
+    from paper_2503_18479_gb300 import workloads as W
+    wl = W.array_32x32(seed=0)
+    st = wl.structures[0]
+    idx = smp["idx"]
+    t0 = time.perf_counter()
+    H = oracle.basis(st.loop_vtx_off, st.vx, st.vy, st.vz, st.px[idx], st.py[idx], st.pz[idx], wl.wire_radius)
+    _, M = oracle.inductance(st.loop_vtx_off, st.vx, st.vy, st.vz, wl.wire_radius)
+    ref = oracle.forward(H, M, st.R, smp["C"], st.omega, st.V)["B"].reshape(len(smp["C"]), -1)
+    rel = lambda a, b: float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+    out = {p: rel(smp[p].reshape(ref.shape), ref) for p in ("fp64", "mixed", "bf16")}
+    out.update({"sample": f"{len(smp['C'])} configurations x {len(idx)} random field points of "
+                          f"{st.n_points}; oracle basis and inductances of the full geometry",
+                "oracle_s": time.perf_counter() - t0,
+                "bounds": {"fp64": 1e-10, "mixed": 1e-6, "bf16": 1e-2}})
+    return out
+
+
+def oracle_single_thread(n=16):
+    """configs/s of the oracle restricted to one thread (OMP_NUM_THREADS=1, a child
+    process) on the first n configurations of the 8x8 workload: forward (full field) + loss
+    + adjoint gradient, basis setup untimed."""
+    code = (
+        "import json, sys, time, numpy as np\n"
+        f"sys.path.insert(0, {ROOT!r})\n"
+        "import oracle\n"
+        "from paper_2503_18479_gb300 import workloads as W\n"
+        "wl = W.array_8x8(seed=0, n_cfg=%d)\n"
+        "st = wl.structures[0]\n"
+        "H = oracle.basis(st.loop_vtx_off, st.vx, st.vy, st.vz, st.px, st.py, st.pz, wl.wire_radius)\n"
+        "_, M = oracle.inductance(st.loop_vtx_off, st.vx, st.vy, st.vz, wl.wire_radius)\n"
+        "t = wl.structure_target(0)\n"
+        "t0 = time.perf_counter()\n"
+        "oracle.forward(H, M, st.R, wl.C, st.omega, st.V, st.loss_idx, t)\n"
+        "oracle.gradient(H, M, st.R, wl.C, st.omega, st.V, st.loss_idx, t)\n"
+        "dt = time.perf_counter() - t0\n"
+        "print(json.dumps({'value': wl.n_cfg / dt, 'threads': oracle.num_threads()}))\n") % n
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+    try:
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception:
+        return {"value": None, "error": r.stderr[-300:]}
+    return {"value": d["value"], "unit": UNIT, "cores": d["threads"],
+            "sample": f"{n} configurations, forward (full field) + loss + adjoint gradient, FP64, "
+                      "one thread"}
 
 
 # ---------------------------------------------------------------------------------------

@@ -64,9 +64,27 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
         os.replace(tmp, LIB)
+    _build_peak_probe(force)
     if verbose:
         print(f"built {LIB}")
     return LIB
+
+
+PEAK_PROBE = os.path.join(LIBDIR, "fp32_peak")
+
+
+def _build_peak_probe(force: bool) -> str:
+    """The FP32 throughput probe (csrc/fp32_peak.cu) that bench.py runs for the measured
+    denominator of its ALU rooflines; a standalone program, not part of libmts.so."""
+    src = os.path.join(CSRC, "fp32_peak.cu")
+    if not force and os.path.exists(PEAK_PROBE) and os.path.getmtime(PEAK_PROBE) >= os.path.getmtime(src):
+        return PEAK_PROBE
+    tmp = PEAK_PROBE + f".tmp{os.getpid()}"
+    r = subprocess.run([nvcc(), *ARCH, "-O3", "-o", tmp, src], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for fp32_peak.cu:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, PEAK_PROBE)
+    return PEAK_PROBE
 
 
 if __name__ == "__main__":
