@@ -5,6 +5,12 @@
 // x = x0 + x1 + x2 (bf16 pieces, exact for FP32 data) the product keeps the six piece
 // pairs of order >= 2^-16 (x0y0, x0y1, x1y0, x0y2, x1y1, x2y0) accumulated in FP32 in
 // tensor memory: relative error ~2^-24 per product (MTS_MIXED). MTS_BF16 uses x0 y0 only.
+// When K spans more than kSumChunks 64-wide chunks (MTS_MIXED, more than 128 ports), each
+// group of kSumChunks chunks goes to a fresh accumulator and the epilogue adds the group
+// partials into a running double-float sum (hi + lo, Knuth's TwoSum) held in two more TMEM
+// regions: the FP32 accumulator then grows only to the magnitude of one group's partial sum
+// instead of the running sum over the whole K range (measured on the 1024-port array:
+// 2.4e-6 relative error with one accumulator, 2e-7 with one per chunk).
 //
 // Persistent kernel, one CTA per SM, 192 threads:
 //   warp 0      producer: cp.async.bulk copies of the pre-swizzled 16 KB operand tiles
@@ -23,6 +29,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "tc_common.cuh"
 
 namespace mts {
 
@@ -30,129 +37,9 @@ namespace tc {
 
 constexpr int kThreads = 192;
 constexpr uint32_t kTileBytes = kTileP * kChunkK * 2;  // 16 KB (also kTileN x 64 x 2)
-constexpr uint32_t kTmemCols = 256;
-constexpr uint64_t kWaitNs = 2000000000ull;  // bound of every mbarrier wait: 2 s
-
-__device__ inline uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ inline void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ inline void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ inline void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ inline bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ inline uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Bounded wait (kWaitNs of wall time); returns false and records `code` in *err on timeout.
-__device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity, int32_t* err, int code) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  while (true) {
-#pragma unroll 1
-    for (int i = 0; i < 256; ++i)  // the timer is read once per 256 polls
-      if (mbar_try_wait(bar, parity)) return true;
-    if (global_ns() - t0 > kWaitNs) {
-      atomicCAS(err, 0, code);
-      return false;
-    }
-  }
-}
-
-__device__ inline void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ inline void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ inline void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
-__device__ inline uint64_t make_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);  // start address
-  d |= (uint64_t)1u << 16;                  // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024u >> 4) << 32;        // stride byte offset: 8 rows x 128 B
-  d |= (uint64_t)1u << 46;                  // descriptor version (sm_100 family)
-  d |= (uint64_t)2u << 61;                  // layout: 128-byte swizzle
-  return d;
-}
-
-// Instruction descriptor: kind::f16, A = B = bf16, D = f32, both K-major, M = 128, N = 128.
-constexpr uint32_t kIdesc = (1u << 4)            // D format f32
-                            | (1u << 7)          // A bf16
-                            | (1u << 10)         // B bf16
-                            | ((128u >> 3) << 17)  // N
-                            | ((128u >> 4) << 24); // M
-
-__device__ inline void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accum)
-      : "memory");
-}
-
-__device__ inline void mma_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-
-__device__ inline void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t* r = reinterpret_cast<uint32_t*>(v);
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-        "=r"(r[31])
-      : "r"(taddr));
-}
-
-__device__ inline void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-__device__ inline void st_cs_f2(float2* p, float x, float y) {
-  asm volatile("st.global.cs.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(x), "f"(y) : "memory");
-}
+constexpr uint32_t kTmemCols = 512;  // two 128-column accumulators + running sum hi, lo
+constexpr uint32_t kHiCol = 256, kLoCol = 384;
+constexpr int kSumChunks = 2;  // K chunks per accumulator when the running sum is used
 
 struct Unit {
   int s, N, F, nkc;
@@ -302,40 +189,52 @@ __global__ void __launch_bounds__(kThreads, 1) superpose_tc_kernel(SuperposeArgs
       bool ok = true;
       for (int64_t u = u_begin; u < u_end && ok; ++u) {
         Unit x = unit_info(a, u);
-        if (!mbar_wait(&tempty[acc], aphase ^ 1u, err, 2)) break;
-        tc_fence_after();
-        const uint32_t d_tmem = tmem_base + (uint32_t)acc * 128u;
-        for (int kc = 0; kc < x.nkc; ++kc) {
-          if (!mbar_wait(&full[stage], phase, err, 3)) {
+        // K chunks per accumulator hand-off: all of them, or kSumChunks with the running sum
+        const int group = (NPIECE == 3 && x.nkc > kSumChunks) ? kSumChunks : x.nkc;
+        for (int k0 = 0; k0 < x.nkc && ok; k0 += group) {
+          if (!mbar_wait(&tempty[acc], aphase ^ 1u, err, 2)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t sA = smem_u32(stages + stage * kStageBytes);
-          const uint32_t sB = sA + NPIECE * kTileBytes;
+          const uint32_t d_tmem = tmem_base + (uint32_t)acc * 128u;
+          const int k1 = min(k0 + group, x.nkc);
+          for (int kc = k0; kc < k1; ++kc) {
+            if (!mbar_wait(&full[stage], phase, err, 3)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sA = smem_u32(stages + stage * kStageBytes);
+            const uint32_t sB = sA + NPIECE * kTileBytes;
+            // K-steps of 16 that hold data (the tail of the last chunk is zero in both
+            // operands: its all-zero steps are not issued)
+            const int ksteps = min(kChunkK / 16, (x.N - kc * kChunkK + 15) / 16);
 #pragma unroll
-          for (int pp = 0; pp < NPAIR; ++pp) {
-            const int qa = NPIECE == 3 ? pa[pp] : 0, qb = NPIECE == 3 ? pb[pp] : 0;
-            const uint64_t da = make_desc(sA + qa * kTileBytes);
-            const uint64_t db = make_desc(sB + qb * kTileBytes);
+            for (int pp = 0; pp < NPAIR; ++pp) {
+              const int qa = NPIECE == 3 ? pa[pp] : 0, qb = NPIECE == 3 ? pb[pp] : 0;
+              const uint64_t da = make_desc(sA + qa * kTileBytes);
+              const uint64_t db = make_desc(sB + qb * kTileBytes);
 #pragma unroll
-            for (int kk = 0; kk < kChunkK / 16; ++kk) {
-              // advance 16 elements (32 bytes) along K inside the swizzle atom
-              mma_bf16(d_tmem, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2),
-                       (kc > 0 || pp > 0 || kk > 0) ? 1u : 0u);
+              for (int kk = 0; kk < kChunkK / 16; ++kk) {
+                // advance 16 elements (32 bytes) along K inside the swizzle atom
+                if (kk < ksteps)
+                  mma_bf16(d_tmem, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2),
+                           (kc > k0 || pp > 0 || kk > 0) ? 1u : 0u);
+              }
+            }
+            mma_commit(&empty[stage]);
+            if (++stage == NSTAGE) {
+              stage = 0;
+              phase ^= 1u;
             }
           }
-          mma_commit(&empty[stage]);
-          if (++stage == NSTAGE) {
-            stage = 0;
-            phase ^= 1u;
+          if (!ok) break;
+          mma_commit(&tfull[acc]);
+          if (++acc == 2) {
+            acc = 0;
+            aphase ^= 1u;
           }
-        }
-        if (!ok) break;
-        mma_commit(&tfull[acc]);
-        if (++acc == 2) {
-          acc = 0;
-          aphase ^= 1u;
         }
       }
       // every MMA issued by this thread has finished before TMEM is released
@@ -348,8 +247,76 @@ __global__ void __launch_bounds__(kThreads, 1) superpose_tc_kernel(SuperposeArgs
     int acc = 0;
     uint32_t aphase = 0;
     float2* Bout = static_cast<float2*>(a.B_out);
-    for (int64_t u = u_begin; u < u_end; ++u) {
+    bool alive = true;
+    for (int64_t u = u_begin; u < u_end && alive; ++u) {
       Unit x = unit_info(a, u);
+      const int64_t p = x.pt * kTileP + quarter * 32 + lane;
+      const int64_t nsys = a.n_cfg * x.F;
+      const int64_t sys0 = x.nt * (kTileN / 2);
+      const int64_t fpo = a.uni.on ? 0 : a.t.fp_off[x.s];
+      if (NPIECE == 3 && x.nkc > kSumChunks) {
+        // one partial per group of kSumChunks K chunks, added into the running sum (hi, lo)
+        const uint32_t lrow = (uint32_t)(quarter * 32) << 16;
+        for (int kc = 0; kc < x.nkc; kc += kSumChunks) {
+          int ok = (lane == 0) ? (int)mbar_wait(&tfull[acc], aphase, err, 4) : 1;
+          ok = __shfl_sync(0xffffffffu, ok, 0);
+          if (!ok) {
+            alive = false;
+            break;
+          }
+          mbar_wait(&tfull[acc], aphase, err, 4);
+          tc_fence_after();
+          const bool last = kc + kSumChunks >= x.nkc;
+#pragma unroll 1
+          for (int c = 0; c < 4; ++c) {
+            float pv[32], hi[32], lo[32];
+            tmem_ld32(tmem_base + lrow + (uint32_t)acc * 128u + c * 32, pv);
+            if (kc > 0) {
+              tmem_ld32(tmem_base + lrow + kHiCol + c * 32, hi);
+              tmem_ld32(tmem_base + lrow + kLoCol + c * 32, lo);
+            }
+            tmem_wait_ld();
+            if (kc == 0) {
+#pragma unroll
+              for (int i = 0; i < 32; ++i) {
+                hi[i] = pv[i];
+                lo[i] = 0.0f;
+              }
+            } else {
+#pragma unroll
+              for (int i = 0; i < 32; ++i) two_sum_acc(hi[i], lo[i], pv[i]);
+            }
+            if (!last) {
+              tmem_st32(tmem_base + lrow + kHiCol + c * 32, hi);
+              tmem_st32(tmem_base + lrow + kLoCol + c * 32, lo);
+            } else if (p < x.P) {
+              // columns 32c .. 32c + 31: systems sys0 + 16c .. + 15
+              int64_t sy = sys0 + 16 * c;
+              int64_t b = sy / x.F;
+              int f = (int)(sy - b * x.F);
+#pragma unroll
+              for (int i = 0; i < 16; ++i) {
+                if (sy + i < nsys) {
+                  float2* dst = Bout + (b * a.sumFP + fpo + (int64_t)f * x.P + p);
+                  st_cs_f2(dst, __fadd_rn(hi[2 * i], lo[2 * i]), __fadd_rn(hi[2 * i + 1], lo[2 * i + 1]));
+                }
+                if (++f == x.F) {
+                  f = 0;
+                  ++b;
+                }
+              }
+            }
+          }
+          tmem_wait_st();
+          tc_fence_before();
+          mbar_arrive(&tempty[acc]);
+          if (++acc == 2) {
+            acc = 0;
+            aphase ^= 1u;
+          }
+        }
+        continue;
+      }
       // lane 0 does the bounded wait; the outcome is made warp-uniform before the
       // warp-collective tcgen05.ld
       int ok = (lane == 0) ? (int)mbar_wait(&tfull[acc], aphase, err, 4) : 1;
@@ -368,11 +335,7 @@ __global__ void __launch_bounds__(kThreads, 1) superpose_tc_kernel(SuperposeArgs
         acc = 0;
         aphase ^= 1u;
       }
-      const int64_t p = x.pt * kTileP + quarter * 32 + lane;
       if (p < x.P) {
-        const int64_t nsys = a.n_cfg * x.F;
-        const int64_t sys0 = x.nt * (kTileN / 2);
-        const int64_t fpo = a.uni.on ? 0 : a.t.fp_off[x.s];
         if (x.F == 1 && sys0 + kTileN / 2 <= nsys) {
           // full tile, one frequency: system i of the tile is row sys0 + i of the output
           float2* dst = Bout + (sys0 * a.sumFP + fpo + p);
