@@ -246,7 +246,11 @@ mts_status mts_forward(const mts_problem* pb, mts_precision prec, const void* ba
  *                                                   as B_out; torch convention
  *                                                   dL/dRe B + j dL/dIm B)
  * Either input may be NULL (both NULL gives zeros). `ev` must be the forward's. The
- * field-cotangent term re-solves A mu = H^T conj(grad_B) per system. */
+ * field-cotangent term re-solves A mu = H^T conj(grad_B) per system. For one-structure
+ * MTS_MIXED / MTS_BF16 problems on the tensor-core superposition path, u = H^T conj(grad_B)
+ * runs on the tensor cores with the split-bf16 basis operand (grad_B rounded to three bf16
+ * pieces, FP32 partial sums over K ranges of points, the partials summed in FP64); otherwise
+ * one FP32 sum per point block on the SIMT cores. */
 mts_status mts_backward(const mts_problem* pb, mts_precision prec, const void* basis,
                         const mts_eval* ev, void* tape, size_t tape_bytes,
                         const void* grad_B, const double* grad_loss, double* grad_C,

@@ -20,8 +20,8 @@ LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libmts.so")
 SOURCES = ["abi.cu", "basis.cu", "solve.cu", "solve_mixed.cu", "solve_large.cu", "superpose.cu", "superpose_tc.cu",
            "backward.cu",
-           "static_solve.cu", "optim.cu", "sroute.cu"]
-HEADERS = ["common.cuh", "kernels.h", "solve_common.cuh"]
+           "static_solve.cu", "optim.cu", "sroute.cu", "field_adjoint_tc.cu"]
+HEADERS = ["common.cuh", "kernels.h", "solve_common.cuh", "tc_common.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

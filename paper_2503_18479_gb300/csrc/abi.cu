@@ -134,8 +134,16 @@ TapeLayout tape_layout(const mts_problem* pb, int64_t n_cfg, mts_precision prec)
   t.Bop = o; o += align256(2 * (size_t)bop_elems(pb, n_cfg, n_pieces(prec), nullptr));
   t.lu = o; o += align256((prec == MTS_FP64 ? 16 : 8) * nc * (size_t)ps.sumLU);
   t.mu_loss = o; o += align256(16 * nc * ps.sumFN);
+  t.fa_part = o; o += align256(fa_part_bytes(pb, n_cfg, prec));
   t.total = o;
   return t;
+}
+
+size_t fa_part_bytes(const mts_problem* pb, int64_t n_cfg, mts_precision prec) {
+  if (pb->n_struct != 1 || prec == MTS_FP64 || n_cfg <= 0) return 0;
+  const int64_t N = pb->h_port_off[1], F = pb->h_freq_off[1];
+  const int64_t nmt = (n_cfg * F + 63) / 64;
+  return sizeof(float) * (size_t)kFaMaxSplit * (size_t)round_up(N, 64) * (size_t)(128 * nmt);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -489,7 +497,45 @@ mts_status mts_backward(const mts_problem* pb, mts_precision prec, const void* b
     fa.H = static_cast<const char*>(basis) + bl.H;
     fa.grad_B = grad_B;
     fa.u = reinterpret_cast<double*>(T + tl.mu);
-    e = launch_field_adjoint_rhs(fa, prec, ps.max_ports, st);
+    const int64_t F0 = pb->h_freq_off[1];
+    if (pb->n_struct == 1 && prec != MTS_FP64 && pb->n_points > 0 &&
+        use_tensor_path(n_pieces(prec), ev->n_cfg, F0, simt_threshold(ev))) {
+      // tensor cores: the basis operand image doubles as the MN-major H operand
+      FaTcArgs t;
+      std::memset(&t, 0, sizeof(t));
+      t.F = (int)F0;
+      t.N = pb->h_port_off[1];
+      t.P = pb->h_point_off[1];
+      t.nsys = ev->n_cfg * F0;
+      t.sumFP = ps.sumFP;
+      t.fpo = 0;
+      t.nkc = (t.N + kChunkK - 1) / kChunkK;
+      t.nptile = (t.P + kTileP - 1) / kTileP;
+      t.nsteps = (int)((t.P + 63) / 64);
+      t.nmt = (t.nsys + 63) / 64;
+      t.npad = round_up(t.N, 64);
+      t.rows_pad = 128 * t.nmt;
+      static int sms = 0;
+      if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+          sms = 1;
+      }
+      // K splits: about four work units per SM, at most kFaMaxSplit and one per K step
+      int64_t ns = (4 * (int64_t)sms + t.nmt * t.nkc - 1) / (t.nmt * t.nkc);
+      ns = ns < 1 ? 1 : (ns > kFaMaxSplit ? kFaMaxSplit : ns);
+      if (ns > t.nsteps) ns = t.nsteps;
+      t.nsplit = (int)ns;
+      t.units = t.nmt * t.nkc * t.nsplit;
+      t.Aop = reinterpret_cast<const __nv_bfloat16*>(static_cast<const char*>(basis) + bl.Aop);
+      t.gB = static_cast<const float2*>(grad_B);
+      t.part = reinterpret_cast<float*>(T + tl.fa_part);
+      t.err = reinterpret_cast<int32_t*>(T + tl.err);
+      e = launch_field_adjoint_tc(t, prec, fa.u, ps.sumFN, 0, st);
+    } else {
+      e = launch_field_adjoint_rhs(fa, prec, ps.max_ports, st);
+    }
     if (e != cudaSuccess) return MTS_ECUDA;
     SolveArgs a = solve_args(pb, prec, basis, ev, tape, ps);
     a.rhs_in = reinterpret_cast<const double*>(T + tl.mu);

@@ -35,6 +35,9 @@
 //   mu_loss    FP64 complex [n_cfg][sum F N]    adjoint solution of the objective
 //   lu         complex FP32 (FP64 for MTS_FP64) [n_cfg][sum_{N_s > 64} F_s N_s^2]: LU
 //              factors of the systems too large for the register-resident solve
+//   fa_part    FP32 [kFaMaxSplit][N rounded to 64][128 ceil(n_cfg F / 64)]: K-split
+//              partials of the tensor-core field adjoint (one-structure MTS_MIXED/MTS_BF16
+//              problems; empty otherwise)
 #pragma once
 #include <cstddef>
 #include <cstdint>
@@ -111,7 +114,7 @@ struct TableLayout {
 
 struct TapeLayout {
   size_t I = 0, loss_part = 0, grad_part = 0, dldc = 0, lossv = 0, status = 0, mu = 0,
-         gfield = 0, plan = 0, err = 0, Bop = 0, lu = 0, mu_loss = 0, total = 0;
+         gfield = 0, plan = 0, err = 0, Bop = 0, lu = 0, mu_loss = 0, fa_part = 0, total = 0;
 };
 
 // Per-call plan tables inside the tape (arrays of n_struct+1 int64).

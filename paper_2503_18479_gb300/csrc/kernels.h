@@ -155,6 +155,29 @@ struct FieldAdjArgs {
 cudaError_t launch_field_adjoint_rhs(const FieldAdjArgs& a, mts_precision prec, int max_ports,
                                      cudaStream_t st);
 
+// u = H^T conj(grad_B) on the tensor cores for a one-structure problem on the tensor path
+// (field_adjoint_tc.cu): work units of 64 systems x 64 ports x one of nsplit K ranges, FP32
+// partial per split in the tape (`part`, [nsplit][npad][rows_pad]), summed in FP64 into u.
+constexpr int kFaMaxSplit = 16;
+struct FaTcArgs {
+  int64_t nsys;      // systems n_cfg F
+  int64_t P;         // field points
+  int64_t sumFP, fpo;  // row stride of grad_B and the structure's offset in a row
+  int F, N, nkc, nsteps, nsplit;
+  int64_t nptile;    // point tiles (128) of the basis operand image
+  int64_t nmt;       // row tiles of 64 systems
+  int64_t units;     // nmt * nkc * nsplit
+  int64_t npad;      // ports rounded up to 64
+  int64_t rows_pad;  // 128 * nmt
+  const __nv_bfloat16* Aop;  // the structure's basis operand image (bf16 pieces of H)
+  const float2* gB;          // grad_B, complex64 [n_cfg][sumFP]
+  float* part;               // K-split partials (tape)
+  int32_t* err;              // bounded-wait error word (tape)
+};
+size_t fa_part_bytes(const mts_problem* pb, int64_t n_cfg, mts_precision prec);
+cudaError_t launch_field_adjoint_tc(FaTcArgs a, mts_precision prec, double* u, int64_t sumFN,
+                                    int64_t fno, cudaStream_t st);
+
 cudaError_t launch_grad_combine(int64_t n_cfg, int n_struct, int n_ports,
                                 const int32_t* port_off, const double* grad_loss,
                                 const double* dldc, const double* gfield, double* grad_C,
