@@ -366,8 +366,9 @@ solve_mixed_v4(SolveArgs a, int64_t n_sys) {
     const bool fin = pivstep < 8 * kb;            // chosen in an earlier panel
     const bool pan = !fin && pivstep < 8 * kb + 8;  // chosen in this panel
     const int ii = pan ? pivstep - 8 * kb : 0;
-    // V_b = U_bb^-1 (threads 0..7, column r) and W_b = L_bb^-1 (threads 8..15, column r - 8;
-    // both by the 8 threads of an 8-thread group)
+    // V_b = U_bb^-1 (threads 0..7, column r) and W_b = L_bb^-1 (threads 32..39 for 64-row
+    // groups, so that the two serial inversions run on different warps; threads 8..15 for
+    // 16 and 32 rows; both by the 8 threads of an 8-thread group)
     if (r < 8) {
       const int c = r;
       float2 v[8];
@@ -385,7 +386,8 @@ solve_mixed_v4(SolveArgs a, int64_t n_sys) {
         sm.vim[i][c] = v[i].y;
       }
     }
-    if ((NM == 8 && r < 8) || (NM > 8 && r >= 8 && r < 16)) {
+    constexpr int WOFF = NM >= 64 ? 32 : 8;
+    if ((NM == 8 && r < 8) || (NM > 8 && r >= WOFF && r < WOFF + 8)) {
       const int c = r & 7;
       float2 v[8];
 #pragma unroll
