@@ -148,8 +148,9 @@ typedef struct mts_problem {
  *                 frequencies are at most this, else on the tensor cores (MTS_MIXED,
  *                 MTS_BF16); 0 selects 16, a negative value puts every structure on the
  *                 tensor cores. Memory does not depend on it.
- *   large_threads threads per system of the blocked solve for N > 64: 128 or 256; 0 selects
- *                 128 for N <= 128 and 256 above. Other values give MTS_EINVAL.
+ *   large_threads threads per system of the blocked solve for N > 64: 128, 256 or 512 (512
+ *                 runs as 256 for MTS_FP64); 0 selects 128 for N <= 128, 256 for N <= 256
+ *                 and 512 above. Other values give MTS_EINVAL.
  * Enhancement objective (Sec. IV-B: beta = |B_MTS| / |B_ref|, the field with the structure
  * over that of a reference run without it): with loss_weight w and loss_offset o (layout of
  * the target without its configuration blocks; either may be NULL) the objective term of a

@@ -135,6 +135,7 @@ TapeLayout tape_layout(const mts_problem* pb, int64_t n_cfg, mts_precision prec)
   t.lu = o; o += align256((prec == MTS_FP64 ? 16 : 8) * nc * (size_t)ps.sumLU);
   t.mu_loss = o; o += align256(16 * nc * ps.sumFN);
   t.fa_part = o; o += align256(fa_part_bytes(pb, n_cfg, prec));
+  t.lu_ord = o; o += align256(4 * nc * ps.sumFN);
   t.total = o;
   return t;
 }
@@ -187,7 +188,8 @@ static int64_t simt_threshold(const mts_eval* ev) {
 
 static mts_status validate_eval(const mts_problem* pb, const mts_eval* ev) {
   if (!ev) return MTS_EINVAL;
-  if (ev->large_threads != 0 && ev->large_threads != 128 && ev->large_threads != 256)
+  if (ev->large_threads != 0 && ev->large_threads != 128 && ev->large_threads != 256 &&
+      ev->large_threads != 512)
     return MTS_EINVAL;
   if (ev->n_cfg < 0) return MTS_EINVAL;
   if (ev->n_cfg > 0 && !ev->C) return MTS_EINVAL;
@@ -257,6 +259,7 @@ static SolveArgs solve_args(const mts_problem* pb, mts_precision prec, const voi
   a.bop_off = reinterpret_cast<const int64_t*>(T + tl.plan + pl.bop_off);
   a.lu_off = reinterpret_cast<const int64_t*>(T + tl.plan + pl.lu_off);
   a.lu = T + tl.lu;
+  a.lu_order = reinterpret_cast<int32_t*>(T + tl.lu_ord);
   a.mu_out = reinterpret_cast<double*>(T + tl.mu_loss);
   a.max_loss = max_loss_points(pb);
   a.large_threads = ev->large_threads;

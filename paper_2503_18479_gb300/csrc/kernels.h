@@ -43,12 +43,14 @@ struct SolveArgs {
   const int64_t* lu_off;   // per-structure element base of the factor scratch (plan table;
                            // [n_struct] = elements per configuration)
   void* lu;                // factor scratch of the large-system kernel
+  int32_t* lu_order;       // pivot order of each large system (forward writes; a backward
+                           // call with rhs_in reuses it and the factors; NULL: refactor)
   double* mu_out;          // adjoint solution mu of the objective (forward with a target)
   // systems of one launch: all (glist == nullptr: system = launch index), or the
   // configurations x the gcount frequencies glist[0 .. gcount-1] of one port class
   const int32_t* glist;
   int64_t gcount;
-  int large_threads;  // 0: 128 for N <= 128, else 256
+  int large_threads;  // 0: 128 for N <= 128, 256 for N <= 256, else 512
   int npieces;
   int max_loss;  // max loss points of one structure (uniform trip count for group loops)
   // backward (field cotangent) mode: solve A mu = rhs_in and write grad terms only

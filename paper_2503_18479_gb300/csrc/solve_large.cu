@@ -34,7 +34,7 @@
 
 namespace mts {
 
-constexpr int kLargeMaxWarps = 8;  // CTAs of 128 (N <= 128) or 256 threads
+constexpr int kLargeMaxWarps = 16;  // CTAs of 128, 256 or 512 threads
 
 template <typename R>
 struct Cx {
@@ -224,172 +224,197 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
   const int F = a.freq_off[si.s + 1] - a.freq_off[si.s];
   Cx<R>* A = scratch + si.b * a.lu_off[a.n_struct] + a.lu_off[si.s] + (int64_t)si.f * N * N;
 
-  // ---- assemble A (Eq. 2, 11), four independent loads of M in flight per thread ----
-  const int NN = N * N;
-  if constexpr (kF) {
-    // off-diagonal (and the diagonal's placeholder) in FP32 from the FP32 part of M
-    const float w32 = (float)w;
-    const float* __restrict__ M32 = a.M32hi + a.t.nn_off[si.s];
-    for (int e0 = 0; e0 < NN; e0 += 4 * T) {
-      float mv[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int e = e0 + q * T + tid;
-        mv[q] = e < NN ? M32[e] : 0.0f;
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int e = e0 + q * T + tid;
-        if (e < NN) A[e] = {(R)0, (R)(w32 * mv[q])};
-      }
-    }
+  const int64_t ioff = si.b * a.sumFN + a.t.fn_off[si.s] + (int64_t)si.f * N;
+  // A backward call reuses the factors and the pivot order the forward left in the tape
+  // (the order is checked to be a permutation; otherwise A is assembled and factored again).
+  bool need_lu = true;
+  if (bwd && a.lu_order != nullptr) {
+    for (int r = tid; r < N; r += T) pivstep[r] = N;
     __syncthreads();
-    // the diagonal once per row in FP64: R_r + j (w M_rr - 1/(w C_r))
-    for (int r = tid; r < N; r += T)
-      A[(int64_t)r * N + r] = {(R)Rk[r], (R)(w * M[(int64_t)r * N + r] - 1.0 / (w * Cb[r]))};
-  } else
-  for (int e0 = 0; e0 < NN; e0 += 4 * T) {
-    double mv[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = e0 + q * T + tid;
-      mv[q] = e < NN ? M[e] : 0.0;
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = e0 + q * T + tid;
-      if (e < NN) {
-        const int r = e / N, j = e - r * N;
-        double im = w * mv[q], re = 0.0;
-        if (j == r) {
-          re = Rk[r];
-          im -= 1.0 / (w * Cb[r]);
-        }
-        A[e] = {(R)re, (R)im};
-      }
-    }
-  }
-  for (int r = tid; r < N; r += T) pivstep[r] = N;
-  __syncthreads();
-
-  // ---- blocked LU with partial pivoting ----
-  for (int c0 = 0; c0 < N; c0 += NB) {
-    const int nb = min(NB, N - c0);
-    for (int e = tid; e < N * NB; e += T) {
-      const int r = e / NB, j = e - r * NB;
-      Cx<R> v = {0, 0};
-      if (j < nb && pivstep[r] == N) v = A[(int64_t)r * N + c0 + j];
-      pan[j * NP + r] = v;
-    }
-    __syncthreads();
-    for (int kk = 0; kk < nb; ++kk) {
-      int p;
-      if constexpr (kF) {
-        float best = -1.0f;
-        int bi = N;
-        for (int r = tid; r < N; r += T)
-          if (pivstep[r] == N) {
-            const Cx<R> v = pan[kk * NP + r];
-            float m = v.x * v.x + v.y * v.y;
-            if (!(m >= 0.0f)) m = 0.0f;  // NaN: still a candidate, so a row is always chosen
-            if (m > best) {
-              best = m;
-              bi = r;
-            }
-          }
-        p = block_argmax_f<W>(best, bi, red);
+    int bad = 0;
+    for (int k = tid; k < N; k += T) {
+      const int p = a.lu_order[ioff + k];
+      if ((unsigned)p < (unsigned)N) {
+        order[k] = p;
+        pivstep[p] = k;
       } else {
-        double best = -1.0;
-        int bi = N;
-        for (int r = tid; r < N; r += T)
-          if (pivstep[r] == N) {
-            const Cx<R> v = pan[kk * NP + r];
-            double m = (double)v.x * v.x + (double)v.y * v.y;
-            if (!(m >= 0.0)) m = 0.0;  // NaN: still a candidate, so a row is always chosen
-            if (m > best) {
-              best = m;
-              bi = r;
-            }
-          }
-        p = block_argmax<W>(best, bi, red);
+        bad = 1;
       }
-      const Cx<R> piv = pan[kk * NP + p];
-      for (int r = tid; r < N; r += T)
-        if (pivstep[r] == N && r != p) {
-          const Cx<R> l = cx_div(pan[kk * NP + r], piv);
-          pan[kk * NP + r] = l;
-          for (int j = kk + 1; j < nb; ++j) cx_fnma(pan[j * NP + r], l, pan[j * NP + p]);
-        }
-      __syncthreads();
-      if (tid == 0) {
-        pivstep[p] = c0 + kk;
-        order[c0 + kk] = p;
-      }
-      __syncthreads();
-    }
-    // panel back to the matrix (rows chosen in this panel or later)
-    for (int e = tid; e < N * NB; e += T) {
-      const int r = e / NB, j = e - r * NB;
-      if (j < nb && pivstep[r] >= c0) A[(int64_t)r * N + c0 + j] = pan[j * NP + r];
     }
     __syncthreads();
-    // trailing columns, CW at a time
-    for (int j0 = c0 + nb; j0 < N; j0 += CW) {
-      if (tid < CW) {
-        const int j = j0 + tid;
-        Cx<R> uu[NB];
+    for (int r = tid; r < N; r += T) bad |= pivstep[r] == N;
+    need_lu = __syncthreads_or(bad) != 0;
+  }
+  if (need_lu) {
+    // ---- assemble A (Eq. 2, 11), four independent loads of M in flight per thread ----
+    const int NN = N * N;
+    if constexpr (kF) {
+      // off-diagonal (and the diagonal's placeholder) in FP32 from the FP32 part of M
+      const float w32 = (float)w;
+      const float* __restrict__ M32 = a.M32hi + a.t.nn_off[si.s];
+      for (int e0 = 0; e0 < NN; e0 += 4 * T) {
+        float mv[4];
 #pragma unroll
-        for (int i = 0; i < NB; ++i) {
-          Cx<R> v = {0, 0};
-          if (i < nb && j < N) {
-            const int pi = order[c0 + i];
-            v = A[(int64_t)pi * N + j];
+        for (int q = 0; q < 4; ++q) {
+          const int e = e0 + q * T + tid;
+          mv[q] = e < NN ? M32[e] : 0.0f;
+        }
 #pragma unroll
-            for (int m = 0; m < i; ++m) cx_fnma(v, pan[m * NP + pi], uu[m]);
-            A[(int64_t)pi * N + j] = v;
-          }
-          uu[i] = v;
-          u12[i * CW + tid] = v;
+        for (int q = 0; q < 4; ++q) {
+          const int e = e0 + q * T + tid;
+          if (e < NN) A[e] = {(R)0, (R)(w32 * mv[q])};
         }
       }
       __syncthreads();
-      {
-        const int col = tid % CW, rg = tid / CW;
-        const int j = j0 + col;
-        Cx<R> uu[NB];
+      // the diagonal once per row in FP64: R_r + j (w M_rr - 1/(w C_r))
+      for (int r = tid; r < N; r += T)
+        A[(int64_t)r * N + r] = {(R)Rk[r], (R)(w * M[(int64_t)r * N + r] - 1.0 / (w * Cb[r]))};
+    } else
+    for (int e0 = 0; e0 < NN; e0 += 4 * T) {
+      double mv[4];
 #pragma unroll
-        for (int m = 0; m < NB; ++m) uu[m] = u12[m * CW + col];
-        if (j < N) {
-          constexpr int RF = 8;  // rows in flight: independent loads per thread
-          int r = rg;
-          for (; r + (RF - 1) * RG < N; r += RF * RG) {
-            bool act[RF];
-            Cx<R> v[RF];
+      for (int q = 0; q < 4; ++q) {
+        const int e = e0 + q * T + tid;
+        mv[q] = e < NN ? M[e] : 0.0;
+      }
 #pragma unroll
-            for (int q = 0; q < RF; ++q) {
-              act[q] = pivstep[r + q * RG] == N;
-              v[q] = act[q] ? A[(int64_t)(r + q * RG) * N + j] : Cx<R>{0, 0};
+      for (int q = 0; q < 4; ++q) {
+        const int e = e0 + q * T + tid;
+        if (e < NN) {
+          const int r = e / N, j = e - r * N;
+          double im = w * mv[q], re = 0.0;
+          if (j == r) {
+            re = Rk[r];
+            im -= 1.0 / (w * Cb[r]);
+          }
+          A[e] = {(R)re, (R)im};
+        }
+      }
+    }
+    for (int r = tid; r < N; r += T) pivstep[r] = N;
+    __syncthreads();
+
+    // ---- blocked LU with partial pivoting ----
+    for (int c0 = 0; c0 < N; c0 += NB) {
+      const int nb = min(NB, N - c0);
+      for (int e = tid; e < N * NB; e += T) {
+        const int r = e / NB, j = e - r * NB;
+        Cx<R> v = {0, 0};
+        if (j < nb && pivstep[r] == N) v = A[(int64_t)r * N + c0 + j];
+        pan[j * NP + r] = v;
+      }
+      __syncthreads();
+      for (int kk = 0; kk < nb; ++kk) {
+        int p;
+        if constexpr (kF) {
+          float best = -1.0f;
+          int bi = N;
+          for (int r = tid; r < N; r += T)
+            if (pivstep[r] == N) {
+              const Cx<R> v = pan[kk * NP + r];
+              float m = v.x * v.x + v.y * v.y;
+              if (!(m >= 0.0f)) m = 0.0f;  // NaN: still a candidate, so a row is always chosen
+              if (m > best) {
+                best = m;
+                bi = r;
+              }
             }
+          p = block_argmax_f<W>(best, bi, red);
+        } else {
+          double best = -1.0;
+          int bi = N;
+          for (int r = tid; r < N; r += T)
+            if (pivstep[r] == N) {
+              const Cx<R> v = pan[kk * NP + r];
+              double m = (double)v.x * v.x + (double)v.y * v.y;
+              if (!(m >= 0.0)) m = 0.0;  // NaN: still a candidate, so a row is always chosen
+              if (m > best) {
+                best = m;
+                bi = r;
+              }
+            }
+          p = block_argmax<W>(best, bi, red);
+        }
+        const Cx<R> piv = pan[kk * NP + p];
+        for (int r = tid; r < N; r += T)
+          if (pivstep[r] == N && r != p) {
+            const Cx<R> l = cx_div(pan[kk * NP + r], piv);
+            pan[kk * NP + r] = l;
+            for (int j = kk + 1; j < nb; ++j) cx_fnma(pan[j * NP + r], l, pan[j * NP + p]);
+          }
+        __syncthreads();
+        if (tid == 0) {
+          pivstep[p] = c0 + kk;
+          order[c0 + kk] = p;
+        }
+        __syncthreads();
+      }
+      // panel back to the matrix (rows chosen in this panel or later)
+      for (int e = tid; e < N * NB; e += T) {
+        const int r = e / NB, j = e - r * NB;
+        if (j < nb && pivstep[r] >= c0) A[(int64_t)r * N + c0 + j] = pan[j * NP + r];
+      }
+      __syncthreads();
+      // trailing columns, CW at a time
+      for (int j0 = c0 + nb; j0 < N; j0 += CW) {
+        if (tid < CW) {
+          const int j = j0 + tid;
+          Cx<R> uu[NB];
 #pragma unroll
-            for (int q = 0; q < RF; ++q)
-              if (act[q]) {
+          for (int i = 0; i < NB; ++i) {
+            Cx<R> v = {0, 0};
+            if (i < nb && j < N) {
+              const int pi = order[c0 + i];
+              v = A[(int64_t)pi * N + j];
 #pragma unroll
-                for (int m = 0; m < NB; ++m) cx_fnma(v[q], pan[m * NP + r + q * RG], uu[m]);
-                A[(int64_t)(r + q * RG) * N + j] = v[q];
+              for (int m = 0; m < i; ++m) cx_fnma(v, pan[m * NP + pi], uu[m]);
+              A[(int64_t)pi * N + j] = v;
+            }
+            uu[i] = v;
+            u12[i * CW + tid] = v;
+          }
+        }
+        __syncthreads();
+        {
+          const int col = tid % CW, rg = tid / CW;
+          const int j = j0 + col;
+          Cx<R> uu[NB];
+#pragma unroll
+          for (int m = 0; m < NB; ++m) uu[m] = u12[m * CW + col];
+          if (j < N) {
+            constexpr int RF = 8;  // rows in flight: independent loads per thread
+            int r = rg;
+            for (; r + (RF - 1) * RG < N; r += RF * RG) {
+              bool act[RF];
+              Cx<R> v[RF];
+#pragma unroll
+              for (int q = 0; q < RF; ++q) {
+                act[q] = pivstep[r + q * RG] == N;
+                v[q] = act[q] ? A[(int64_t)(r + q * RG) * N + j] : Cx<R>{0, 0};
+              }
+#pragma unroll
+              for (int q = 0; q < RF; ++q)
+                if (act[q]) {
+#pragma unroll
+                  for (int m = 0; m < NB; ++m) cx_fnma(v[q], pan[m * NP + r + q * RG], uu[m]);
+                  A[(int64_t)(r + q * RG) * N + j] = v[q];
+                }
+            }
+            for (; r < N; r += RG)
+              if (pivstep[r] == N) {
+                Cx<R> v = A[(int64_t)r * N + j];
+#pragma unroll
+                for (int m = 0; m < NB; ++m) cx_fnma(v, pan[m * NP + r], uu[m]);
+                A[(int64_t)r * N + j] = v;
               }
           }
-          for (; r < N; r += RG)
-            if (pivstep[r] == N) {
-              Cx<R> v = A[(int64_t)r * N + j];
-#pragma unroll
-              for (int m = 0; m < NB; ++m) cx_fnma(v, pan[m * NP + r], uu[m]);
-              A[(int64_t)r * N + j] = v;
-            }
         }
+        __syncthreads();
       }
-      __syncthreads();
     }
-  }
+    if (!bwd && a.lu_order != nullptr)
+      for (int k = tid; k < N; k += T) a.lu_order[ioff + k] = order[k];
+  }  // need_lu
 
   // ---- solve A x = rhs (FP64 rhs in shared memory) into wv (by row) with the factors;
   // the unknown of column k ends in wv[order[k]] ----
@@ -530,7 +555,6 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
     return conv;
   };
 
-  const int64_t ioff = si.b * a.sumFN + a.t.fn_off[si.s] + (int64_t)si.f * N;
   bool conv_all = true;
   if (!bwd) {
     for (int r = tid; r < N; r += T) {
@@ -705,7 +729,7 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
 }
 
 // CTA size for a class whose largest system has max_ports ports
-static int large_threads(int max_ports) { return max_ports <= 128 ? 128 : 256; }
+static int large_threads(int max_ports) { return max_ports <= 128 ? 128 : (max_ports <= 256 ? 256 : 512); }
 
 size_t large_solve_smem(mts_precision prec, int max_ports) {
   return prec == MTS_FP64 ? LargeSmem<double>(max_ports).bytes : LargeSmem<float>(max_ports).bytes;
@@ -727,12 +751,13 @@ static cudaError_t launch_large(const SolveArgs& a, int64_t n_sys, int min_ports
 cudaError_t launch_solve_large(const SolveArgs& a, mts_precision prec, int64_t n_sys, int min_ports,
                                int max_ports, void* scratch, cudaStream_t st) {
   if (n_sys == 0) return cudaSuccess;
-  const bool small = (a.large_threads ? a.large_threads : large_threads(max_ports)) == 128;
-  if (prec == MTS_FP64)
-    return small ? launch_large<double, 128>(a, n_sys, min_ports, max_ports, scratch, st)
-                 : launch_large<double, 256>(a, n_sys, min_ports, max_ports, scratch, st);
-  return small ? launch_large<float, 128>(a, n_sys, min_ports, max_ports, scratch, st)
-               : launch_large<float, 256>(a, n_sys, min_ports, max_ports, scratch, st);
+  const int T = a.large_threads ? a.large_threads : large_threads(max_ports);
+  if (prec == MTS_FP64)  // FP64 factors: at most 256 threads (the register budget of 512 is too small)
+    return T == 128 ? launch_large<double, 128>(a, n_sys, min_ports, max_ports, scratch, st)
+                    : launch_large<double, 256>(a, n_sys, min_ports, max_ports, scratch, st);
+  if (T == 128) return launch_large<float, 128>(a, n_sys, min_ports, max_ports, scratch, st);
+  if (T == 256) return launch_large<float, 256>(a, n_sys, min_ports, max_ports, scratch, st);
+  return launch_large<float, 512>(a, n_sys, min_ports, max_ports, scratch, st);
 }
 
 }  // namespace mts

@@ -2,7 +2,7 @@
 Simulator on a given batch for each candidate schedule and keeps the fastest in
 `sim.tuning` (passed to every later call through mts_eval). The candidates choose, per
 structure, the tensor-core or the SIMT superposition (the threshold on configurations x
-frequencies) and the CTA size of the blocked solve for N > 64 (128 or 256 threads per
+frequencies) and the CTA size of the blocked solve for N > 64 (128, 256 or 512 threads per
 system). Every schedule computes the same result to rounding; only time differs."""
 from __future__ import annotations
 
@@ -14,7 +14,7 @@ from . import native as nv
 from .simulator import Simulator
 
 SIMT_CHOICES = (-1, 4, 16, 64, 1 << 30)  # -1: every structure on the tensor cores
-LARGE_CHOICES = (128, 256)
+LARGE_CHOICES = (128, 256, 512)
 
 
 def _time_step(sim: Simulator, C: torch.Tensor, tuning: dict, reps: int, flush: torch.Tensor):

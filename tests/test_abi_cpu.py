@@ -249,7 +249,7 @@ def test_adam_step_validation(nv):
 
 
 def test_schedule_fields_are_validated(nv):
-    """large_threads must be 0, 128 or 256; the schedule does not change the tape size."""
+    """large_threads must be 0, 128, 256 or 512; the schedule does not change the tape size."""
     L = nv.lib()
     wl = W.array_8x8(n_cfg=2, grid=4, planes=(0.02,))
     c, keep = fake_problem(nv, wl)

@@ -49,14 +49,15 @@ def test_large_solve_cta_sizes_agree(prec):
     wl = small_rect(10, 8, n_cfg=6, n_freq=2, grid=8, seed=9)
     sim = Simulator(wl, prec)
     outs = []
-    for lt in (128, 256):
+    for lt in (128, 256, 512):
         sim.tuning = {"simt_max_sys": 0, "large_threads": lt}
         C = torch.from_numpy(wl.C).cuda().requires_grad_(True)
         B, loss = sim(C)
         loss.sum().backward()
         outs.append((B.detach(), loss.detach(), C.grad.clone()))
-    for a, b in zip(outs[0], outs[1]):
-        assert rel(a.cpu().numpy(), b.cpu().numpy()) < 1e-13
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert rel(a.cpu().numpy(), b.cpu().numpy()) < 1e-13
 
 
 def test_autotune_picks_a_candidate_and_keeps_results():
