@@ -14,14 +14,19 @@
 // products, MTS_BF16 uses one pair.
 //
 // Work units: (64-system row tile) x (64-port chunk) x (K split). Persistent kernel, one CTA
-// per SM, 448 threads:
+// per SM, 480 threads:
 //   warp 0      producer: cp.async.bulk of the H half-tiles (64 points x 64 ports per
 //               piece) into a ring of stages, mbarrier transaction counts
 //   warp 1      TMEM allocation (128 columns: two 64-column FP32 accumulators); lane 0
 //               issues tcgen05.mma (M = 128, N = 64, K = 16, kind::f16, bf16 inputs, B
 //               MN-major) and hands an accumulator to the epilogue every kDrain K steps
-//   warps 2..5  converters: load 64 systems x 64 points of grad_B (coalesced), write the
-//               conj pieces in the K-major swizzled image, fence the async proxy, arrive
+//   warps 2..5  converters: read 64 systems x 64 points of grad_B from the raw ring, write
+//               the conj pieces in the K-major swizzled image, fence the async proxy, arrive
+//   warp 14     raw producer: cp.async.bulk of each system's 64 points (512 bytes) into a
+//               ring of raw grad_B stages (row pitch 528 bytes, so that the converters'
+//               16-byte reads of eight consecutive rows fall in distinct banks); rows whose
+//               address is not 16-byte aligned, and an odd last point, are read by the
+//               converters from global memory instead
 //   warps 6..13 epilogue: tcgen05.ld of the accumulator into FP64 running sums (one TMEM
 //               lane = one row, 32 of the 64 columns per thread: two warps per lane
 //               quarter), at the unit's end the FP32 partial of its K split to the tape
@@ -40,13 +45,15 @@ namespace fa {
 
 using namespace tc;
 
-constexpr int kThreads = 448;
+constexpr int kThreads = 480;
 constexpr int kEpiThreads = 256;  // warps 6..13
 constexpr int kStepPts = 64;                            // points per K step
 constexpr uint32_t kAPiece = 128u * kStepPts * 2u;      // 16 KB: 128 rows x 64 points
 constexpr uint32_t kBPiece = (uint32_t)kStepPts * 64u * 2u;  // 8 KB: 64 points x 64 ports
 constexpr uint32_t kTmemCols = 128;                     // two 64-column accumulators
 constexpr int kDrain = 4;                               // K steps per accumulator hand-off
+constexpr uint32_t kRawPitch = 528;                     // bytes per system row of a raw stage
+constexpr uint32_t kRawStage = 64u * kRawPitch;          // 64 systems x 64 points of grad_B
 
 // Instruction descriptor: kind::f16, A = B = bf16, D = f32, A K-major, B MN-major,
 // M = 128, N = 64.
@@ -68,7 +75,8 @@ __device__ inline void fence_async_smem() {
 
 template <int NPIECE>
 struct Cfg {
-  static constexpr int NSTAGE = NPIECE == 3 ? 3 : 4;
+  static constexpr int NSTAGE = NPIECE == 3 ? 2 : 4;  // operand stages (pieces of both)
+  static constexpr int RAW = NPIECE == 3 ? 2 : 3;     // raw grad_B stages
   static constexpr uint32_t kStage = (uint32_t)NPIECE * (kAPiece + kBPiece);
 };
 
@@ -105,6 +113,7 @@ __device__ inline uint4 bf16_chunk(const float* x, float* rem) {
 template <int NPIECE>
 __global__ void __launch_bounds__(kThreads, 1) field_adjoint_tc_kernel(FaTcArgs a) {
   constexpr int NSTAGE = Cfg<NPIECE>::NSTAGE;
+  constexpr int RAW = Cfg<NPIECE>::RAW;
   constexpr uint32_t kStage = Cfg<NPIECE>::kStage;
   constexpr int NPAIR = NPIECE == 3 ? 6 : 1;
   constexpr int pa[6] = {2, 1, 0, 1, 0, 0};  // piece pairs (A = grad_B, B = H), small first
@@ -113,14 +122,17 @@ __global__ void __launch_bounds__(kThreads, 1) field_adjoint_tc_kernel(FaTcArgs 
   extern __shared__ __align__(1024) unsigned char smem_dyn[];
   uintptr_t sbase = (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023);
   unsigned char* stages = reinterpret_cast<unsigned char*>(sbase);  // [stage][A pieces, B pieces]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(stages + NSTAGE * kStage);
+  unsigned char* raws = stages + NSTAGE * kStage;  // [RAW][64 rows, pitch kRawPitch]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(raws + RAW * kRawStage);
   uint64_t* bfull = bars;               // [NSTAGE] H copies landed
   uint64_t* afull = bars + NSTAGE;      // [NSTAGE] grad_B pieces written (128 arrivals)
   uint64_t* empty = bars + 2 * NSTAGE;  // [NSTAGE] MMAs of the stage done
   uint64_t* tfull = bars + 3 * NSTAGE;  // [2]
   uint64_t* tempty = tfull + 2;         // [2] (128 arrivals)
   uint64_t* mdone = tempty + 2;         // [1]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mdone + 1);
+  uint64_t* rfull = mdone + 1;          // [RAW] raw copies landed
+  uint64_t* rempty = rfull + RAW;       // [RAW] raw stage read (128 arrivals)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(rempty + RAW);
   int32_t* err = a.err;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -139,6 +151,10 @@ __global__ void __launch_bounds__(kThreads, 1) field_adjoint_tc_kernel(FaTcArgs 
       mbar_init(&tempty[i], kEpiThreads);
     }
     mbar_init(mdone, 1);
+    for (int i = 0; i < RAW; ++i) {
+      mbar_init(&rfull[i], 1);
+      mbar_init(&rempty[i], 128);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -249,11 +265,13 @@ __global__ void __launch_bounds__(kThreads, 1) field_adjoint_tc_kernel(FaTcArgs 
       mbar_wait(mdone, 0, err, 16);
     }
   } else if (warp < 6) {
-    // ---------------- converters: grad_B -> conj bf16 pieces ----------------
-    const int tid = threadIdx.x - 64;  // 0..127
-    const int il = tid >> 1, h = tid & 1;  // system of the tile, half of the 64 points
-    int stage = 0;
-    uint32_t phase = 0;
+    // ---------------- converters: raw grad_B -> conj bf16 pieces ----------------
+    const int tid = threadIdx.x - 64;        // 0..127
+    const int il = tid & 63, h = tid >> 6;   // system of the tile, half of the 64 points
+    const int cfirst = (il >> 2) & 1;        // component written first: eight consecutive
+                                             // rows then cover all eight 16-byte slots
+    int stage = 0, rs = 0;
+    uint32_t phase = 0, rph = 0;
     bool ok = true;
     for (int64_t u = u_begin; u < u_end && ok; ++u) {
       const UnitPos q = unit_pos(a, u);
@@ -262,27 +280,48 @@ __global__ void __launch_bounds__(kThreads, 1) field_adjoint_tc_kernel(FaTcArgs 
       const int64_t b = vs ? sys / a.F : 0;
       const int64_t f = vs ? sys - b * a.F : 0;
       const float2* src = a.gB + b * a.sumFP + a.fpo + f * a.P;
+      const bool bulk = vs && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0);
       for (int t = q.t0; t < q.t1; ++t) {
-        if (!mbar_wait(&empty[stage], phase ^ 1u, err, 17)) {
+        if (!mbar_wait(&rfull[rs], rph, err, 19) || !mbar_wait(&empty[stage], phase ^ 1u, err, 17)) {
           ok = false;
           break;
         }
+        const unsigned char* row = raws + rs * kRawStage + il * kRawPitch;
         unsigned char* sA = stages + stage * kStage;
-        const int64_t p0 = (int64_t)t * kStepPts + 32 * h;
+        const int64_t p0 = (int64_t)t * kStepPts;
+        const int np = (int)min((int64_t)kStepPts, a.P - p0);
+        const int npe = bulk ? (np & ~1) : 0;  // points of this row in the raw stage
 #pragma unroll 1
         for (int c8 = 0; c8 < 4; ++c8) {
+          const int e0 = 32 * h + 8 * c8;
           float re[8], im[8];
+          if (e0 + 8 <= npe) {
+            const float4* s4 = reinterpret_cast<const float4*>(row + 8 * e0);
 #pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const int64_t p = p0 + 8 * c8 + e;
-            float2 g = make_float2(0.0f, 0.0f);
-            if (vs && p < a.P) g = __ldg(src + p);
-            re[e] = g.x;
-            im[e] = -g.y;  // conj
+            for (int i = 0; i < 4; ++i) {
+              const float4 v = s4[i];
+              re[2 * i] = v.x;
+              im[2 * i] = -v.y;  // conj
+              re[2 * i + 1] = v.z;
+              im[2 * i + 1] = -v.w;
+            }
+          } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const int p = e0 + e;
+              float2 g = make_float2(0.0f, 0.0f);
+              if (p < npe)
+                g = reinterpret_cast<const float2*>(row)[p];
+              else if (vs && p < np)
+                g = __ldg(src + p0 + p);
+              re[e] = g.x;
+              im[e] = -g.y;
+            }
           }
           const int j = 4 * h + c8;  // 16-byte chunk of the 128-byte row
 #pragma unroll
-          for (int c = 0; c < 2; ++c) {
+          for (int cc = 0; cc < 2; ++cc) {
+            const int c = cc ^ cfirst;
             const uint32_t R = 2u * il + c;
             const uint32_t off = R * 128u + ((((uint32_t)j ^ (R & 7u)) & 7u) << 4);
             float x[8], r1[8];
@@ -298,14 +337,76 @@ __global__ void __launch_bounds__(kThreads, 1) field_adjoint_tc_kernel(FaTcArgs 
         }
         fence_async_smem();  // generic-proxy writes become visible to the tensor core
         mbar_arrive(&afull[stage]);
+        mbar_arrive(&rempty[rs]);
         if (++stage == NSTAGE) {
           stage = 0;
           phase ^= 1u;
         }
+        if (++rs == RAW) {
+          rs = 0;
+          rph ^= 1u;
+        }
       }
     }
+  } else if (warp == 14) {
+    // ---------------- raw producer: 64 points of each system row per K step ----------------
+    int rs = 0;
+    uint32_t rph = 0;
+    uint32_t last_phase[RAW];
+    bool used[RAW];
+    for (int i = 0; i < RAW; ++i) {
+      used[i] = false;
+      last_phase[i] = 0;
+    }
+    bool ok = true;
+    for (int64_t u = u_begin; u < u_end && ok; ++u) {
+      const UnitPos q = unit_pos(a, u);
+      const float2* src[2];
+      bool bulk[2];
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int64_t sys = q.mt * 64 + lane + 32 * hh;
+        const bool vs = sys < a.nsys;
+        const int64_t b = vs ? sys / a.F : 0;
+        const int64_t f = vs ? sys - b * a.F : 0;
+        src[hh] = a.gB + b * a.sumFP + a.fpo + f * a.P;
+        bulk[hh] = vs && ((reinterpret_cast<uintptr_t>(src[hh]) & 15u) == 0);
+      }
+      const uint32_t nbulk = __popc(__ballot_sync(0xffffffffu, bulk[0])) +
+                             __popc(__ballot_sync(0xffffffffu, bulk[1]));
+      for (int t = q.t0; t < q.t1; ++t) {
+        int okw = (lane == 0) ? (int)mbar_wait(&rempty[rs], rph ^ 1u, err, 20) : 1;
+        okw = __shfl_sync(0xffffffffu, okw, 0);
+        if (!okw) {
+          ok = false;
+          break;
+        }
+        const int64_t p0 = (int64_t)t * kStepPts;
+        const int np = (int)min((int64_t)kStepPts, a.P - p0);
+        const uint32_t bytes = 8u * (uint32_t)(np & ~1);  // a multiple of 16
+        if (lane == 0) mbar_arrive_expect_tx(&rfull[rs], nbulk * bytes);
+        __syncwarp();
+        if (bytes > 0) {
+#pragma unroll
+          for (int hh = 0; hh < 2; ++hh)
+            if (bulk[hh])
+              bulk_g2s(raws + rs * kRawStage + (lane + 32 * hh) * kRawPitch, src[hh] + p0, bytes,
+                       &rfull[rs]);
+        }
+        used[rs] = true;
+        last_phase[rs] = rph;
+        if (++rs == RAW) {
+          rs = 0;
+          rph ^= 1u;
+        }
+      }
+    }
+    if (lane == 0)  // own copies in flight land before the CTA ends
+      for (int i = 0; i < RAW; ++i)
+        if (used[i]) mbar_wait(&rfull[i], last_phase[i], err, 21);
   } else {
-    // ---------------- epilogue: FP64 running sums, FP32 partial per K split ----------------
+    // ------- epilogue: double-float (FP32 hi + lo) running sums, FP32 partial per K split -------
+    // (FP32 TwoSum on the FP32 pipe: FP64 adds would run at 1/64 of its rate)
     const int quarter = warp & 3;        // TMEM lanes 32*quarter .. +31
     const int half = (warp - 6) >> 2;    // accumulator columns 32*half .. +31
     int acc = 0;
@@ -313,9 +414,9 @@ __global__ void __launch_bounds__(kThreads, 1) field_adjoint_tc_kernel(FaTcArgs 
     bool alive = true;
     for (int64_t u = u_begin; u < u_end && alive; ++u) {
       const UnitPos q = unit_pos(a, u);
-      double s[32];
+      float hi[32], lo[32];
 #pragma unroll
-      for (int c = 0; c < 32; ++c) s[c] = 0.0;
+      for (int c = 0; c < 32; ++c) hi[c] = lo[c] = 0.0f;
       for (int g0 = q.t0; g0 < q.t1; g0 += kDrain) {
         int ok = (lane == 0) ? (int)mbar_wait(&tfull[acc], aphase, err, 18) : 1;
         ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -335,13 +436,13 @@ __global__ void __launch_bounds__(kThreads, 1) field_adjoint_tc_kernel(FaTcArgs 
           aphase ^= 1u;
         }
 #pragma unroll
-        for (int c = 0; c < 32; ++c) s[c] += (double)v[c];
+        for (int c = 0; c < 32; ++c) two_sum_acc(hi[c], lo[c], v[c]);
       }
       if (!alive) break;
       const int64_t row = q.mt * 128 + quarter * 32 + lane;
       float* dst = a.part + ((int64_t)q.ks * a.npad + (int64_t)q.kc * 64 + 32 * half) * a.rows_pad + row;
 #pragma unroll
-      for (int c = 0; c < 32; ++c) dst[(int64_t)c * a.rows_pad] = (float)s[c];
+      for (int c = 0; c < 32; ++c) dst[(int64_t)c * a.rows_pad] = hi[c] + lo[c];
     }
   }
 
@@ -358,7 +459,8 @@ __global__ void __launch_bounds__(kThreads, 1) field_adjoint_tc_kernel(FaTcArgs 
 template <int NPIECE>
 size_t smem_bytes() {
   return 1024 + (size_t)Cfg<NPIECE>::NSTAGE * Cfg<NPIECE>::kStage +
-         8 * (4 * Cfg<NPIECE>::NSTAGE + 5) + 16;
+         (size_t)Cfg<NPIECE>::RAW * kRawStage + 8 * (4 * Cfg<NPIECE>::NSTAGE + 5 + 2 * Cfg<NPIECE>::RAW) +
+         16;
 }
 
 // u[b][fn + f N + k] = sum over K splits of the row pair (2i, 2i + 1), i = b F + f
