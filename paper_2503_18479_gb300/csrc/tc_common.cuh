@@ -64,6 +64,24 @@ __device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity, int32_t* err, i
   }
 }
 
+// Bounded wait for waiters off the critical path: polls with a short sleep between tries,
+// so that spinning warps leave issue slots to the warps doing the work.
+__device__ inline bool mbar_wait_sleep(uint64_t* bar, uint32_t parity, int32_t* err, int code) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (true) {
+#pragma unroll 1
+    for (int i = 0; i < 64; ++i) {
+      __nanosleep(100);
+      if (mbar_try_wait(bar, parity)) return true;
+    }
+    if (global_ns() - t0 > kWaitNs) {
+      atomicCAS(err, 0, code);
+      return false;
+    }
+  }
+}
+
 __device__ inline void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
