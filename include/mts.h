@@ -126,6 +126,11 @@ typedef struct mts_problem {
                                   paper's normal field), 1 = Bx, 2 = By; NULL = Bz everywhere.
                                   Another code makes that point's basis rows NaN and
                                   mts_basis_status report MTS_EINVAL. */
+  int32_t keep_factors;        /* nonzero: the tape also holds the LU factors of the systems
+                                  of 33..64 ports (37,120 bytes per configuration and
+                                  frequency, MTS_MIXED / MTS_BF16), written by every solve
+                                  and read by mts_backward's field-cotangent solve instead of
+                                  factoring again. Larger systems always keep theirs. */
 } mts_problem;
 
 /*

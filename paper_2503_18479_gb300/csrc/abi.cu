@@ -136,6 +136,8 @@ TapeLayout tape_layout(const mts_problem* pb, int64_t n_cfg, mts_precision prec)
   t.mu_loss = o; o += align256(16 * nc * ps.sumFN);
   t.fa_part = o; o += align256(fa_part_bytes(pb, n_cfg, prec));
   t.lu_ord = o; o += align256(4 * nc * ps.sumFN);
+  t.fac = o;
+  if (pb->keep_factors && prec != MTS_FP64) o += align256(kFacStride * nc * (size_t)pb->n_freq);
   t.total = o;
   return t;
 }
@@ -260,6 +262,7 @@ static SolveArgs solve_args(const mts_problem* pb, mts_precision prec, const voi
   a.lu_off = reinterpret_cast<const int64_t*>(T + tl.plan + pl.lu_off);
   a.lu = T + tl.lu;
   a.lu_order = reinterpret_cast<int32_t*>(T + tl.lu_ord);
+  a.fac = (pb->keep_factors && prec != MTS_FP64) ? static_cast<void*>(T + tl.fac) : nullptr;
   a.mu_out = reinterpret_cast<double*>(T + tl.mu_loss);
   a.max_loss = max_loss_points(pb);
   a.large_threads = ev->large_threads;

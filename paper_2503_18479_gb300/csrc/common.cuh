@@ -40,6 +40,8 @@
 //              problems; empty otherwise)
 //   lu_ord     int32 [n_cfg][sum F N]: pivot order of each blocked LU (column k's pivot row),
 //              written by the forward, read by a backward call that reuses the factors
+//   fac        [n_cfg][n_freq] blocks of kFacStride bytes, only with keep_factors (MTS_MIXED,
+//              MTS_BF16): the register solve's factors of each 33..64-port system
 #pragma once
 #include <cstddef>
 #include <cstdint>
@@ -117,7 +119,7 @@ struct TableLayout {
 struct TapeLayout {
   size_t I = 0, loss_part = 0, grad_part = 0, dldc = 0, lossv = 0, status = 0, mu = 0,
          gfield = 0, plan = 0, err = 0, Bop = 0, lu = 0, mu_loss = 0, fa_part = 0, lu_ord = 0,
-         total = 0;
+         fac = 0, total = 0;
 };
 
 // Per-call plan tables inside the tape (arrays of n_struct+1 int64).

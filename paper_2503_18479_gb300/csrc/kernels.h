@@ -7,6 +7,13 @@
 
 namespace mts {
 
+// Kept factors of one 33..64-port system of the register solve (keep_factors): row r's 64
+// packed FP32 pairs [q][r] (u64, q < 32 real parts, q >= 32 imaginary parts, blocks rotated
+// as the LU leaves them), each row's pivot step (int32 [64]), then W_b = L_bb^-1 of every
+// panel (FP32 [8][8][8] real, then imaginary).
+constexpr size_t kFacRows = 64 * 64 * 8, kFacPiv = 64 * 4, kFacW = 2 * 8 * 64 * 4;
+constexpr size_t kFacStride = kFacRows + kFacPiv + kFacW;  // 37,120 bytes
+
 // Everything the per-system solve kernels read and write.
 struct SolveArgs {
   int n_struct, n_freq, n_ports;
@@ -43,6 +50,8 @@ struct SolveArgs {
   const int64_t* lu_off;   // per-structure element base of the factor scratch (plan table;
                            // [n_struct] = elements per configuration)
   void* lu;                // factor scratch of the large-system kernel
+  void* fac;               // register-solve factors of 33..64-port systems, kFacStride bytes
+                           // per system (keep_factors), or NULL
   int32_t* lu_order;       // pivot order of each large system (forward writes; a backward
                            // call with rhs_in reuses it and the factors; NULL: refactor)
   double* mu_out;          // adjoint solution mu of the objective (forward with a target)

@@ -223,7 +223,9 @@ __device__ __forceinline__ float2 bdot(const u64* re4, const u64* im4, const flo
   return make_float2((a.x + a.y) - (b.x + b.y), (c.x + c.y) + (d.x + d.y));
 }
 
-template <int NM>
+// KF: the problem keeps its factors (a separate instantiation, so that the common path
+// carries none of the extra registers)
+template <int NM, bool KF>
 __global__ void __launch_bounds__(NM >= 64 ? NM : 128, NM >= 64 ? 6 : (NM == 32 ? 3 : 4))
 solve_mixed_v4(SolveArgs a, int64_t n_sys) {
   constexpr int NB = NM / 8;
@@ -237,6 +239,33 @@ solve_mixed_v4(SolveArgs a, int64_t n_sys) {
   const bool in_range = li < n_sys;
   const int64_t sys = in_range ? launch_sys(a, li) : 0;
   u64 ReP[NB][4], ImP[NB][4];
+  int pivstep = NM;
+  bool need_lu = true;
+  if constexpr (NM == 64 && KF) {
+    // ---- a backward solve of a problem that keeps its factors: load the forward's rows,
+    // pivot steps and W blocks instead of factoring again (a pivot step out of range means
+    // the block was never written: factor) ----
+    if (a.rhs_in != nullptr && a.fac != nullptr) {
+      const char* fb = static_cast<const char*>(a.fac) + (size_t)sys * kFacStride;
+      const u64* fr = reinterpret_cast<const u64*>(fb);
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          ReP[b][m] = fr[(size_t)(b * 4 + m) * NM + r];
+          ImP[b][m] = fr[(size_t)(NB * 4 + b * 4 + m) * NM + r];
+        }
+      pivstep = reinterpret_cast<const int32_t*>(fb + kFacRows)[r];
+      const float* fw = reinterpret_cast<const float*>(fb + kFacRows + kFacPiv);
+      for (int i = r; i < NB * 64; i += NM) {
+        (&sm.wre[0][0][0])[i] = fw[i];
+        (&sm.wim[0][0][0])[i] = fw[NB * 64 + i];
+      }
+      need_lu = __syncthreads_or(!in_range || !((unsigned)pivstep < (unsigned)NM)) != 0;
+    }
+  }
+  if (need_lu) {
+  pivstep = NM;
   {
     // ---- row r of A (FP32), identity rows for padding. The per-system values used here are
     // derived again after the LU, so that none of them stays live across it. ----
@@ -274,7 +303,6 @@ solve_mixed_v4(SolveArgs a, int64_t n_sys) {
   }
 
   // ---- LU with partial pivoting, panels of 8 columns, delayed trailing updates ----
-  int pivstep = NM;
 #pragma unroll 1
   for (int kb = 0; kb < NB; ++kb) {
     const int nact = NB - kb;
@@ -496,6 +524,28 @@ solve_mixed_v4(SolveArgs a, int64_t n_sys) {
       }
     }
   }
+
+  if constexpr (NM == 64 && KF) {
+    // the factors of a problem that keeps them (forward only; rows coalesced per q)
+    if (a.rhs_in == nullptr && a.fac != nullptr && in_range) {
+      char* fb = static_cast<char*>(a.fac) + (size_t)sys * kFacStride;
+      u64* fr = reinterpret_cast<u64*>(fb);
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          fr[(size_t)(b * 4 + m) * NM + r] = ReP[b][m];
+          fr[(size_t)(NB * 4 + b * 4 + m) * NM + r] = ImP[b][m];
+        }
+      reinterpret_cast<int32_t*>(fb + kFacRows)[r] = pivstep;
+      float* fw = reinterpret_cast<float*>(fb + kFacRows + kFacPiv);
+      for (int i = r; i < NB * 64; i += NM) {
+        fw[i] = (&sm.wre[0][0][0])[i];
+        fw[NB * 64 + i] = (&sm.wim[0][0][0])[i];
+      }
+    }
+  }
+  }  // need_lu
 
   const int Mb = pivstep >> 3, ii = pivstep & 7;
 
@@ -813,25 +863,26 @@ solve_mixed_v4(SolveArgs a, int64_t n_sys) {
   if (valid && r == 0 && !bwd) a.status[sys] = (int)fb;
 }
 
-template <int NM>
+template <int NM, bool KF>
 static cudaError_t launch_v4(const SolveArgs& a, int64_t n_sys, cudaStream_t st) {
   constexpr int CT = NM >= 64 ? NM : 128;
   constexpr int G = CT / NM;
   const size_t smem = sizeof(SmemV4<NM>) * G;
-  cudaError_t e = cudaFuncSetAttribute(solve_mixed_v4<NM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(solve_mixed_v4<NM, KF>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const unsigned grid = (unsigned)((n_sys + G - 1) / G);
-  solve_mixed_v4<NM><<<grid, CT, smem, st>>>(a, n_sys);
+  solve_mixed_v4<NM, KF><<<grid, CT, smem, st>>>(a, n_sys);
   note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_solve_mixed(const SolveArgs& a, int64_t n_sys, int max_ports, cudaStream_t st) {
-  if (max_ports <= 8) return launch_v4<8>(a, n_sys, st);
-  if (max_ports <= 16) return launch_v4<16>(a, n_sys, st);
-  if (max_ports <= 32) return launch_v4<32>(a, n_sys, st);
-  if (max_ports <= 64) return launch_v4<64>(a, n_sys, st);
+  if (max_ports <= 8) return launch_v4<8, false>(a, n_sys, st);
+  if (max_ports <= 16) return launch_v4<16, false>(a, n_sys, st);
+  if (max_ports <= 32) return launch_v4<32, false>(a, n_sys, st);
+  if (max_ports <= 64)
+    return a.fac != nullptr ? launch_v4<64, true>(a, n_sys, st) : launch_v4<64, false>(a, n_sys, st);
   return cudaErrorNotSupported;
 }
 

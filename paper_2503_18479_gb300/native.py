@@ -46,7 +46,7 @@ class MtsProblem(ct.Structure):
         ("loop_vtx_off", ct.c_void_p), ("vx", ct.c_void_p), ("vy", ct.c_void_p),
         ("vz", ct.c_void_p), ("px", ct.c_void_p), ("py", ct.c_void_p), ("pz", ct.c_void_p),
         ("loss_idx", ct.c_void_p), ("R", ct.c_void_p), ("L_self", ct.c_void_p),
-        ("pcomp", ct.c_void_p),
+        ("pcomp", ct.c_void_p), ("keep_factors", ct.c_int32),
     ]
 
 
@@ -185,7 +185,7 @@ def _prec(p) -> int:
 class Problem:
     """Device and host copies of a batch of structures (mts_problem)."""
 
-    def __init__(self, flat: dict, wire_radius: float, device="cuda"):
+    def __init__(self, flat: dict, wire_radius: float, device="cuda", keep_factors: bool = False):
         def dev(a, dt):
             return torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).to(device)
         self.h_port_off = np.ascontiguousarray(flat["port_off"], np.int32)
@@ -223,6 +223,7 @@ class Problem:
             setattr(c, k, self.d[k].data_ptr() if self.d[k].numel() else None)
         c.L_self = self.d["L_self"].data_ptr() if "L_self" in self.d else None
         c.pcomp = self.d["pcomp"].data_ptr() if "pcomp" in self.d else None
+        c.keep_factors = 1 if keep_factors else 0
         self.c = c
         self.n_struct = n_struct
 

@@ -19,16 +19,18 @@ from .workloads import Workload
 class Simulator:
     def __init__(self, wl: Workload, precision="mixed", device="cuda", target=None,
                  target_per_cfg: Optional[bool] = None, refine_tol: float = 0.0,
-                 max_refine: int = 0, loss_weight=None, loss_offset=None):
+                 max_refine: int = 0, loss_weight=None, loss_offset=None,
+                 keep_factors: bool = False):
         """loss_weight [FL] real and loss_offset [FL] complex (optional): the objective is
         taken on weight * (B + offset) at the loss points -- the enhancement objective of
-        Sec. IV-B with weight 1/|B_ref| and offset the incident field."""
+        Sec. IV-B with weight 1/|B_ref| and offset the incident field. keep_factors: the tape
+        keeps the register solve's LU factors for a later field-cotangent backward."""
         self.wl = wl
         self.prec = nv._prec(precision)
         self.device = torch.device(device)
         flat = wl.flat()
         self.flat = flat
-        self.pb = nv.Problem(flat, wl.wire_radius, device)
+        self.pb = nv.Problem(flat, wl.wire_radius, device, keep_factors=keep_factors)
         self.basis = nv.alloc_bytes(nv.mts_basis_bytes(self.pb, self.prec), device)
         nv.mts_build_basis(self.pb, self.prec, self.basis)
         code = nv.mts_basis_status(self.pb, self.prec, self.basis)

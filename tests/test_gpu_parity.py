@@ -149,6 +149,37 @@ def test_field_cotangent(name, prec):
     assert cosine(C.grad.cpu().numpy(), want) >= 0.9999
 
 
+@pytest.mark.parametrize("name", ["8x8", "ragged128"])
+@pytest.mark.parametrize("prec", ["mixed", "bf16"])
+def test_field_cotangent_kept_factors(name, prec):
+    """A problem built with keep_factors: the forward stores the register solve's factors of
+    its 33..64-port systems and the field-cotangent backward solves with them instead of
+    factoring again. The factorization is deterministic, so the gradient must equal, bit for
+    bit, the one of a problem that factors again; and it must match the oracle."""
+    from paper_2503_18479_gb300.simulator import Simulator
+    wl, _ = case(name)
+    nc = min(40, wl.n_cfg)
+    sub = W.Workload(wl.name, wl.structures, wl.C[:nc].copy(), wl.wire_radius, target=wl.target)
+    gBs = [W.random_cotangent((nc, st.n_freq, st.n_points), seed=11 + s)
+           for s, st in enumerate(sub.structures)]
+    grads = []
+    for keep in (False, True):
+        sim = Simulator(sub, prec, keep_factors=keep)
+        C = torch.from_numpy(sub.C).cuda().requires_grad_(True)
+        B, loss = sim(C, want_B=True)
+        gflat = np.concatenate([g.reshape(nc, -1) for g in gBs], axis=1)
+        gBt = torch.from_numpy(gflat).to(B.dtype).cuda()
+        torch.autograd.backward([B, loss], [gBt, torch.ones_like(loss)])
+        grads.append(C.grad.cpu().numpy())
+    assert np.array_equal(grads[0], grads[1])
+    if prec == "mixed":
+        bases = [structure_basis(sub, s) for s in range(len(sub.structures))]
+        ref = oracle_reference(sub, want_B=False, gB=gBs, bases=bases)
+        want = np.concatenate([ref[s]["grad_field"] + ref[s]["grad"] for s in range(len(sub.structures))],
+                              axis=1)
+        assert rel(grads[1], want) < 1e-5, rel(grads[1], want)
+
+
 def test_complex_target_mode():
     """|B - t|^2 with complex targets per configuration (loss_mode = 1, target_per_cfg)."""
     wl0 = small_8x8(n_cfg=70)
