@@ -5,7 +5,7 @@
 // x = x0 + x1 + x2 (bf16 pieces, exact for FP32 data) the product keeps the six piece
 // pairs of order >= 2^-16 (x0y0, x0y1, x1y0, x0y2, x1y1, x2y0) accumulated in FP32 in
 // tensor memory: relative error ~2^-24 per product (MTS_MIXED). MTS_BF16 uses x0 y0 only.
-// When K spans more than kSumChunks 64-wide chunks (MTS_MIXED, more than 128 ports), each
+// When K spans more than kSumMaxPlain 64-wide chunks (MTS_MIXED, more than 256 ports), each
 // group of kSumChunks chunks goes to a fresh accumulator and the epilogue adds the group
 // partials into a running double-float sum (hi + lo, Knuth's TwoSum) held in two more TMEM
 // regions: the FP32 accumulator then grows only to the magnitude of one group's partial sum
@@ -39,7 +39,9 @@ constexpr int kThreads = 192;
 constexpr uint32_t kTileBytes = kTileP * kChunkK * 2;  // 16 KB (also kTileN x 64 x 2)
 constexpr uint32_t kTmemCols = 512;  // two 128-column accumulators + running sum hi, lo
 constexpr uint32_t kHiCol = 256, kLoCol = 384;
-constexpr int kSumChunks = 2;  // K chunks per accumulator when the running sum is used
+constexpr int kSumChunks = 2;    // K chunks per accumulator when the running sum is used
+constexpr int kSumMaxPlain = 4;  // up to this many K chunks, one FP32 accumulator (at most
+                                 // 4 x 4 K-steps x 6 piece pairs = 96 FP32 roundings)
 
 struct Unit {
   int s, N, F, nkc;
@@ -190,7 +192,7 @@ __global__ void __launch_bounds__(kThreads, 1) superpose_tc_kernel(SuperposeArgs
       for (int64_t u = u_begin; u < u_end && ok; ++u) {
         Unit x = unit_info(a, u);
         // K chunks per accumulator hand-off: all of them, or kSumChunks with the running sum
-        const int group = (NPIECE == 3 && x.nkc > kSumChunks) ? kSumChunks : x.nkc;
+        const int group = (NPIECE == 3 && x.nkc > kSumMaxPlain) ? kSumChunks : x.nkc;
         for (int k0 = 0; k0 < x.nkc && ok; k0 += group) {
           if (!mbar_wait(&tempty[acc], aphase ^ 1u, err, 2)) {
             ok = false;
@@ -254,7 +256,7 @@ __global__ void __launch_bounds__(kThreads, 1) superpose_tc_kernel(SuperposeArgs
       const int64_t nsys = a.n_cfg * x.F;
       const int64_t sys0 = x.nt * (kTileN / 2);
       const int64_t fpo = a.uni.on ? 0 : a.t.fp_off[x.s];
-      if (NPIECE == 3 && x.nkc > kSumChunks) {
+      if (NPIECE == 3 && x.nkc > kSumMaxPlain) {
         // one partial per group of kSumChunks K chunks, added into the running sum (hi, lo)
         const uint32_t lrow = (uint32_t)(quarter * 32) << 16;
         for (int kc = 0; kc < x.nkc; kc += kSumChunks) {
