@@ -72,9 +72,12 @@ struct LargeCfg<double> {
 };
 
 struct BlockRed {
-  double key[kLargeMaxWarps];
-  float keyf[kLargeMaxWarps];
-  int idx[kLargeMaxWarps];
+  double key[kLargeMaxWarps];  // block_max / block_sum
+  // the pivot search's per-warp candidates, double-buffered by step parity (one barrier
+  // per pivot step)
+  double pkey[2][kLargeMaxWarps];
+  float pkeyf[2][kLargeMaxWarps];
+  int pidx[2][kLargeMaxWarps];
 };
 
 // Shared-memory carve-up for systems of up to n ports (host and device agree on it).
@@ -102,46 +105,34 @@ struct LargeSmem {
   }
 };
 
-// block-wide arg-max of (key, idx) over W warps, ties to the smaller index; every thread
-// gets idx.
-template <int W>
-__device__ inline int block_argmax(double key, int idx, BlockRed* red) {
-  argmax_shfl_d(key, idx, 32);
-  __syncthreads();
+// Pivot search across the CTA with one barrier: the warp winners go to buffer `buf` (step
+// parity), so that a step's writes cannot overtake the previous step's reads; ties go to the
+// smaller row. Every thread gets the row.
+template <int W, typename K>
+__device__ inline int pivot_argmax(K key, int idx, BlockRed* red, int buf) {
+  if constexpr (sizeof(K) == 4) argmax_shfl(key, idx, 32);
+  else argmax_shfl_d(key, idx, 32);
   if ((threadIdx.x & 31) == 0) {
-    red->key[threadIdx.x >> 5] = key;
-    red->idx[threadIdx.x >> 5] = idx;
+    if constexpr (sizeof(K) == 4) red->pkeyf[buf][threadIdx.x >> 5] = key;
+    else red->pkey[buf][threadIdx.x >> 5] = key;
+    red->pidx[buf][threadIdx.x >> 5] = idx;
   }
   __syncthreads();
-  double kb = red->key[0];
-  int ib = red->idx[0];
+  K kb;
+  if constexpr (sizeof(K) == 4) kb = red->pkeyf[buf][0];
+  else kb = red->pkey[buf][0];
+  int ib = red->pidx[buf][0];
 #pragma unroll
-  for (int q = 1; q < W; ++q)
-    if (red->key[q] > kb || (red->key[q] == kb && red->idx[q] < ib)) {
-      kb = red->key[q];
-      ib = red->idx[q];
+  for (int q = 1; q < W; ++q) {
+    K kq;
+    if constexpr (sizeof(K) == 4) kq = red->pkeyf[buf][q];
+    else kq = red->pkey[buf][q];
+    const int iq = red->pidx[buf][q];
+    if (kq > kb || (kq == kb && iq < ib)) {
+      kb = kq;
+      ib = iq;
     }
-  return ib;
-}
-
-// the same over FP32 keys
-template <int W>
-__device__ inline int block_argmax_f(float key, int idx, BlockRed* red) {
-  argmax_shfl(key, idx, 32);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) {
-    red->keyf[threadIdx.x >> 5] = key;
-    red->idx[threadIdx.x >> 5] = idx;
   }
-  __syncthreads();
-  float kb = red->keyf[0];
-  int ib = red->idx[0];
-#pragma unroll
-  for (int q = 1; q < W; ++q)
-    if (red->keyf[q] > kb || (red->keyf[q] == kb && red->idx[q] < ib)) {
-      kb = red->keyf[q];
-      ib = red->idx[q];
-    }
   return ib;
 }
 
@@ -304,6 +295,9 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
         pan[j * NP + r] = v;
       }
       __syncthreads();
+      // pivot steps with one barrier each: a thread reads and writes only its own rows of the
+      // panel and their pivot steps, except the pivot row's entries, which its owner last
+      // wrote before the barrier of this step's search
       for (int kk = 0; kk < nb; ++kk) {
         int p;
         if constexpr (kF) {
@@ -319,7 +313,7 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
                 bi = r;
               }
             }
-          p = block_argmax_f<W>(best, bi, red);
+          p = pivot_argmax<W>(best, bi, red, kk & 1);
         } else {
           double best = -1.0;
           int bi = N;
@@ -333,22 +327,22 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
                 bi = r;
               }
             }
-          p = block_argmax<W>(best, bi, red);
+          p = pivot_argmax<W>(best, bi, red, kk & 1);
         }
         const Cx<R> piv = pan[kk * NP + p];
         for (int r = tid; r < N; r += T)
-          if (pivstep[r] == N && r != p) {
-            const Cx<R> l = cx_div(pan[kk * NP + r], piv);
-            pan[kk * NP + r] = l;
-            for (int j = kk + 1; j < nb; ++j) cx_fnma(pan[j * NP + r], l, pan[j * NP + p]);
+          if (pivstep[r] == N) {
+            if (r == p) {
+              pivstep[r] = c0 + kk;
+            } else {
+              const Cx<R> l = cx_div(pan[kk * NP + r], piv);
+              pan[kk * NP + r] = l;
+              for (int j = kk + 1; j < nb; ++j) cx_fnma(pan[j * NP + r], l, pan[j * NP + p]);
+            }
           }
-        __syncthreads();
-        if (tid == 0) {
-          pivstep[p] = c0 + kk;
-          order[c0 + kk] = p;
-        }
-        __syncthreads();
+        if (tid == 0) order[c0 + kk] = p;
       }
+      __syncthreads();  // every row's panel entries and pivot step in place
       // panel back to the matrix (rows chosen in this panel or later)
       for (int e = tid; e < N * NB; e += T) {
         const int r = e / NB, j = e - r * NB;
@@ -359,19 +353,24 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
       for (int j0 = c0 + nb; j0 < N; j0 += CW) {
         if (tid < CW) {
           const int j = j0 + tid;
-          Cx<R> uu[NB];
+          if (j < N) {  // columns past N skip the unrolled work as a whole
+            Cx<R> uu[NB];
 #pragma unroll
-          for (int i = 0; i < NB; ++i) {
-            Cx<R> v = {0, 0};
-            if (i < nb && j < N) {
-              const int pi = order[c0 + i];
-              v = A[(int64_t)pi * N + j];
+            for (int i = 0; i < NB; ++i) {
+              Cx<R> v = {0, 0};
+              if (i < nb) {
+                const int pi = order[c0 + i];
+                v = A[(int64_t)pi * N + j];
 #pragma unroll
-              for (int m = 0; m < i; ++m) cx_fnma(v, pan[m * NP + pi], uu[m]);
-              A[(int64_t)pi * N + j] = v;
+                for (int m = 0; m < i; ++m) cx_fnma(v, pan[m * NP + pi], uu[m]);
+                A[(int64_t)pi * N + j] = v;
+              }
+              uu[i] = v;
+              u12[i * CW + tid] = v;
             }
-            uu[i] = v;
-            u12[i * CW + tid] = v;
+          } else {
+#pragma unroll
+            for (int i = 0; i < NB; ++i) u12[i * CW + tid] = Cx<R>{0, 0};
           }
         }
         __syncthreads();

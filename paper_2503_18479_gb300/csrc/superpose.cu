@@ -117,9 +117,10 @@ cudaError_t launch_plan(const mts_problem* pb, int64_t n_cfg, int npieces, int64
 }
 
 // SIMT superposition. A unit is 128 points x up to 16 systems of one structure; thread t owns
-// point t of the tile, reads its own row of H straight from global memory (16-byte vector
-// loads when N is a multiple of 4: every structure's block starts on a 128-byte boundary;
-// all of a chunk's loads are in flight together) and accumulates its systems in registers.
+// point t of the tile and accumulates its systems in registers. FP32 with N a multiple of 4
+// (every structure's block starts on a 128-byte boundary): the tile's rows of H arrive in
+// shared memory by coalesced cp.async copies and each (re, im) pair takes one packed FMA;
+// otherwise each thread reads its own row of H straight from global memory.
 // The currents of the unit's systems are staged per K chunk in shared memory (k-major: the
 // systems of one k are contiguous, read as broadcasts). Used for MTS_FP64 (T = double, FP64
 // basis) and, in the other precisions, for structures with at most 16 systems (T = float,
@@ -143,21 +144,49 @@ struct SimtCfg<double> {
 };
 
 template <typename T>
-constexpr size_t simt_smem_bytes() {
+__host__ __device__ constexpr size_t simt_smem_bytes() {
   return sizeof(T) * 2 * (size_t)SimtCfg<T>::KC * kSimtSys;
 }
 
-template <typename T, int SC>
-__device__ inline void simt_accumulate(const T (&h)[SimtCfg<T>::KC], const T* __restrict__ sI,
-                                       int kn, T (&ax)[kSimtSys], T (&ay)[kSimtSys]) {
+template <typename T, int SC, int KR>
+__device__ inline void simt_accumulate(const T (&h)[KR], const T* __restrict__ sI, int kn,
+                                       T (&ax)[kSimtSys], T (&ay)[kSimtSys]) {
 #pragma unroll
-  for (int k = 0; k < SimtCfg<T>::KC; ++k) {
+  for (int k = 0; k < KR; ++k) {
     if (k < kn) {
       const T* ik = sI + 2 * kSimtSys * k;
 #pragma unroll
       for (int i = 0; i < SC; ++i) {
         ax[i] = fma(h[k], ik[2 * i], ax[i]);
         ay[i] = fma(h[k], ik[2 * i + 1], ay[i]);
+      }
+    }
+  }
+}
+
+// FP32 path, N a multiple of 4: (re, im) of a system accumulate as one packed pair, so one
+// fma.rn.f32x2 serves both; h comes from the unit's H tile in shared memory, four k at a time.
+constexpr int kSimtHPitch = SimtCfg<float>::KC + 4;  // floats per staged H row (bank spread)
+
+template <int SC>
+__device__ inline void simt_accumulate_f2(const float* __restrict__ hr, const float* __restrict__ sI,
+                                          int kn, unsigned long long (&acc)[kSimtSys]) {
+#pragma unroll
+  for (int k4 = 0; k4 < SimtCfg<float>::KC; k4 += 4) {
+    if (k4 < kn) {  // kn is a multiple of 4
+      const float4 h4 = *reinterpret_cast<const float4*>(hr + k4);
+      const float hv[4] = {h4.x, h4.y, h4.z, h4.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        unsigned long long hh;
+        asm("mov.b64 %0, {%1,%1};" : "=l"(hh) : "f"(hv[e]));
+        const ulonglong2* ik = reinterpret_cast<const ulonglong2*>(sI + 2 * kSimtSys * (k4 + e));
+#pragma unroll
+        for (int i2 = 0; i2 < SC / 2; ++i2) {
+          const ulonglong2 c = ik[i2];
+          asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc[2 * i2]) : "l"(hh), "l"(c.x));
+          asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc[2 * i2 + 1]) : "l"(hh), "l"(c.y));
+        }
       }
     }
   }
@@ -210,15 +239,75 @@ __global__ void __launch_bounds__(kSimtPts) superpose_simt_kernel(SuperposeArgs 
     s_ooff[t] = oo;
   }
   __syncthreads();
+  if constexpr (sizeof(T) == 4) {
+    if (vec) {
+      // The unit's 128 rows of H are one contiguous block: each K chunk of them is copied
+      // into shared memory with cp.async (consecutive threads, consecutive 16-byte pieces of a
+      // row; rows past P are zero-filled) while the chunk's currents are staged, and each
+      // thread then reads its own padded row.
+      float* sH = reinterpret_cast<float*>(sm_simt + simt_smem_bytes<float>());  // [128][HP]
+      constexpr int HP = kSimtHPitch;
+      unsigned long long acc[kSimtSys];
+#pragma unroll
+      for (int i = 0; i < kSimtSys; ++i) acc[i] = 0ull;
+      const float* hblk = static_cast<const float*>(a.H) + a.t.pn_off[s] + pt * kSimtPts * (int64_t)N;
+      const int rows = (int)min((int64_t)kSimtPts, P - pt * kSimtPts);
+      for (int k0 = 0; k0 < N; k0 += KC) {
+        const int kn = min(KC, N - k0);
+        const int q4 = kn / 4;  // 16-byte pieces per row
+        for (int e = t; e < kSimtPts * q4; e += kSimtPts) {
+          const int r = e / q4, c = e - r * q4;
+          const uint32_t dst = (uint32_t)__cvta_generic_to_shared(sH + r * HP + 4 * c);
+          const float* src = r < rows ? hblk + (int64_t)r * N + k0 + 4 * c : hblk;
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+                       "r"(r < rows ? 16u : 0u)
+                       : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        for (int e = t; e < kn * kSimtSys; e += kSimtPts) {
+          const int k = e / kSimtSys, i = e - k * kSimtSys;
+          float re = 0.0f, im = 0.0f;
+          if (i < nsv) {
+            const double* Ip = a.I + s_ioff[i] + 2 * (k0 + k);
+            re = (float)Ip[0];
+            im = (float)Ip[1];
+          }
+          sI[2 * (k * kSimtSys + i)] = re;
+          sI[2 * (k * kSimtSys + i) + 1] = im;
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncthreads();
+        const float* hr = sH + t * HP;
+        if (nsv <= 4) simt_accumulate_f2<4>(hr, sI, kn, acc);
+        else if (nsv <= 8) simt_accumulate_f2<8>(hr, sI, kn, acc);
+        else simt_accumulate_f2<16>(hr, sI, kn, acc);
+        __syncthreads();
+      }
+      if (live) {
+        float2* out = static_cast<float2*>(a.B_out);
+#pragma unroll
+        for (int i = 0; i < kSimtSys; ++i)
+          if (i < nsv) {
+            float2 v;
+            asm("mov.b64 {%0,%1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(acc[i]));
+            out[s_ooff[i] + p] = v;
+          }
+      }
+      return;
+    }
+  }
+  // FP64, or FP32 with N not a multiple of 4 (a short register chunk: this path is rare in
+  // FP32 and should not set the kernel's register count)
+  constexpr int KR = sizeof(T) == 4 ? 16 : KC;
   T ax[kSimtSys], ay[kSimtSys];
 #pragma unroll
   for (int i = 0; i < kSimtSys; ++i) ax[i] = ay[i] = T(0);
-  for (int k0 = 0; k0 < N; k0 += KC) {
-    const int kn = min(KC, N - k0);
-    T h[KC];
+  for (int k0 = 0; k0 < N; k0 += KR) {
+    const int kn = min(KR, N - k0);
+    T h[KR];
     if (vec) {  // kn is a multiple of VEC here
 #pragma unroll
-      for (int q = 0; q < KC / VEC; ++q) {
+      for (int q = 0; q < KR / VEC; ++q) {
         V v;
         if (live && q * VEC < kn) {
           v = *reinterpret_cast<const V*>(hrow + k0 + q * VEC);
@@ -231,7 +320,7 @@ __global__ void __launch_bounds__(kSimtPts) superpose_simt_kernel(SuperposeArgs 
       }
     } else {
 #pragma unroll
-      for (int k = 0; k < KC; ++k) h[k] = (live && k < kn) ? hrow[k0 + k] : T(0);
+      for (int k = 0; k < KR; ++k) h[k] = (live && k < kn) ? hrow[k0 + k] : T(0);
     }
     __syncthreads();
     for (int e = t; e < kn * kSimtSys; e += kSimtPts) {
@@ -246,9 +335,9 @@ __global__ void __launch_bounds__(kSimtPts) superpose_simt_kernel(SuperposeArgs 
       sI[2 * (k * kSimtSys + i) + 1] = im;
     }
     __syncthreads();
-    if (nsv <= 4) simt_accumulate<T, 4>(h, sI, kn, ax, ay);
-    else if (nsv <= 8) simt_accumulate<T, 8>(h, sI, kn, ax, ay);
-    else simt_accumulate<T, 16>(h, sI, kn, ax, ay);
+    if (nsv <= 4) simt_accumulate<T, 4, KR>(h, sI, kn, ax, ay);
+    else if (nsv <= 8) simt_accumulate<T, 8, KR>(h, sI, kn, ax, ay);
+    else simt_accumulate<T, 16, KR>(h, sI, kn, ax, ay);
   }
   if (live) {
     C2* out = static_cast<C2*>(a.B_out);
@@ -267,7 +356,9 @@ cudaError_t launch_superpose_tc(const SuperposeArgs& a, mts_precision prec, cuda
 
 template <typename T>
 static cudaError_t launch_simt(const SuperposeArgs& a, cudaStream_t st) {
-  constexpr size_t sm = simt_smem_bytes<T>();
+  // FP32: the currents plus the staged H tile of the N % 4 == 0 path
+  constexpr size_t sm = simt_smem_bytes<T>() +
+                        (sizeof(T) == 4 ? sizeof(float) * (size_t)kSimtPts * kSimtHPitch : 0);
   cudaError_t e = cudaFuncSetAttribute(superpose_simt_kernel<T>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
