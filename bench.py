@@ -101,6 +101,11 @@ def parse():
                     help="comma list of extra workloads timed after the headline (loop, line, "
                          "ragged, 32x32, fit, fit8x8, sroute; empty for none); reported under "
                          "other_workloads")
+    ap.add_argument("--x32-configs", type=int, default=256,
+                    help="configurations of the 32x32 entry (256 = the benchmark's; fewer for a "
+                         "profiler capture)")
+    ap.add_argument("--x32-grid", type=int, default=512,
+                    help="grid points per side of each field plane of the 32x32 entry")
     return ap.parse_args()
 
 
@@ -566,7 +571,8 @@ def other_workloads(args, dev, prec, peak, stash):
         "loop": ("single_loop: circular 64-gon, 1 config, 101 freqs, 32x32 grid", lambda: W.single_loop(seed=0)),
         "line": ("line_8x1: 8x1 square loops, 1024 configs, 201 freqs, 64x64 grid", lambda: W.line_8x1(seed=0)),
         "ragged": ("ragged: 10,000 structures of 1..128 ports, 1-16 freqs, 64x64 grid each", lambda: W.ragged(seed=0)),
-        "32x32": ("array_32x32: 1024 ports, 256 configs, 4x512x512 grid", lambda: W.array_32x32(seed=0)),
+        "32x32": (f"array_32x32: 1024 ports, {args.x32_configs} configs, 4x{args.x32_grid}x{args.x32_grid} grid",
+                  lambda: W.array_32x32(seed=0, n_cfg=args.x32_configs, grid=args.x32_grid)),
         "fit": ("loop_sweep: Adam fits (lr 1e-13) of 100 initial C x 100 target fields on the "
                 "single loop at 63.6 MHz, 200 epochs replayed from one CUDA graph", None),
         "fit8x8": ("array_8x8: 4096 independent Adam fits (lr 1e-13) of the 64 capacitances to "
