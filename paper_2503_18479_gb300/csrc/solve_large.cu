@@ -73,6 +73,7 @@ struct LargeCfg<double> {
 
 struct BlockRed {
   double key[kLargeMaxWarps];  // block_max / block_sum
+  int cnt;                     // rows in the active-row list of the trailing update
   // the pivot search's per-warp candidates, double-buffered by step parity (one barrier
   // per pivot step)
   double pkey[2][kLargeMaxWarps];
@@ -349,6 +350,29 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
         if (j < nb && pivstep[r] >= c0) A[(int64_t)r * N + c0 + j] = pan[j * NP + r];
       }
       __syncthreads();
+      // FP32 with up to 256 threads (N <= 256 by default): the rows still to be updated (not
+      // chosen as pivots yet), listed once per panel
+      // in the triangular-solve vector (idle during the LU); warp-aggregated, so the order of
+      // the list varies but every row's update is the same
+      int nact = 0;
+      int* alist = reinterpret_cast<int*>(wv);
+      if constexpr (kF && T <= 256) {
+        if (c0 + nb < N) {
+          if (tid == 0) red->cnt = 0;
+          __syncthreads();
+          for (int rb = warp * 32; rb < N; rb += T) {
+            const int r = rb + lane;
+            const bool act = r < N && pivstep[r] == N;
+            const unsigned bal = __ballot_sync(0xffffffffu, act);
+            int base = 0;
+            if (lane == 0 && bal) base = atomicAdd(&red->cnt, __popc(bal));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (act) alist[base + __popc(bal & ((1u << lane) - 1u))] = r;
+          }
+          __syncthreads();
+          nact = red->cnt;
+        }
+      }
       // trailing columns, CW at a time
       for (int j0 = c0 + nb; j0 < N; j0 += CW) {
         if (tid < CW) {
@@ -374,38 +398,103 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
           }
         }
         __syncthreads();
-        {
-          const int col = tid % CW, rg = tid / CW;
-          const int j = j0 + col;
-          Cx<R> uu[NB];
+        // (512-thread CTAs keep the per-column form below: on 1024-port systems, whose
+        // trailing blocks stream through HBM, the tiles' longer compute between loads was
+        // 2 % slower)
+        if constexpr (kF && T <= 256) {
+          // register-tiled update: a thread takes 4 listed rows x 4 columns (j0 + 4 cg ..),
+          // the (re, im) pairs of a tile in packed registers; per panel column m, with the
+          // multiplier l = (a, b) and the U12 entry u = (c, d):
+          //   v -= l u  <=>  (v.re, v.im) += (b, b) (d, -c) + (-a, -a) (c, d)
+          // two fma.rn.f32x2 per complex multiply-add, 8 shared loads per 16 of them
+          const int cg = lane;  // the warp covers the chunk's 128 columns
+          const int jc = j0 + 4 * cg;
+          const int ntile = (nact + 3) >> 2;
+          for (int t4 = warp; t4 < ntile; t4 += W) {
+            int rw[4];
+            bool okr[4];
 #pragma unroll
-          for (int m = 0; m < NB; ++m) uu[m] = u12[m * CW + col];
-          if (j < N) {
-            constexpr int RF = 8;  // rows in flight: independent loads per thread
-            int r = rg;
-            for (; r + (RF - 1) * RG < N; r += RF * RG) {
-              bool act[RF];
-              Cx<R> v[RF];
+            for (int rr = 0; rr < 4; ++rr) {
+              okr[rr] = 4 * t4 + rr < nact;
+              rw[rr] = alist[okr[rr] ? 4 * t4 + rr : 0];
+            }
+            unsigned long long V[4][4];
 #pragma unroll
-              for (int q = 0; q < RF; ++q) {
-                act[q] = pivstep[r + q * RG] == N;
-                v[q] = act[q] ? A[(int64_t)(r + q * RG) * N + j] : Cx<R>{0, 0};
+            for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+              for (int cc = 0; cc < 4; ++cc) {
+                const int j = jc + cc;
+                V[rr][cc] = (okr[rr] && j < N)
+                                ? *reinterpret_cast<const unsigned long long*>(A + (int64_t)rw[rr] * N + j)
+                                : 0ull;
+              }
+#pragma unroll 2
+            for (int m = 0; m < NB; ++m) {
+              unsigned long long LA[4], LB[4], P1[4], P2[4];
+#pragma unroll
+              for (int rr = 0; rr < 4; ++rr) {
+                const Cx<R> l = pan[m * NP + rw[rr]];
+                asm("mov.b64 %0, {%1,%1};" : "=l"(LA[rr]) : "f"(-l.x));
+                asm("mov.b64 %0, {%1,%1};" : "=l"(LB[rr]) : "f"(l.y));
               }
 #pragma unroll
-              for (int q = 0; q < RF; ++q)
-                if (act[q]) {
+              for (int cc = 0; cc < 4; ++cc) {
+                const Cx<R> u = u12[m * CW + 4 * cg + cc];
+                asm("mov.b64 %0, {%1,%2};" : "=l"(P1[cc]) : "f"(u.x), "f"(u.y));
+                asm("mov.b64 %0, {%1,%2};" : "=l"(P2[cc]) : "f"(u.y), "f"(-u.x));
+              }
 #pragma unroll
-                  for (int m = 0; m < NB; ++m) cx_fnma(v[q], pan[m * NP + r + q * RG], uu[m]);
-                  A[(int64_t)(r + q * RG) * N + j] = v[q];
+              for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) {
+                  // the order of cx_fnma (b d first): the same roundings as the per-column form
+                  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(V[rr][cc]) : "l"(LB[rr]), "l"(P2[cc]));
+                  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(V[rr][cc]) : "l"(LA[rr]), "l"(P1[cc]));
                 }
             }
-            for (; r < N; r += RG)
-              if (pivstep[r] == N) {
-                Cx<R> v = A[(int64_t)r * N + j];
 #pragma unroll
-                for (int m = 0; m < NB; ++m) cx_fnma(v, pan[m * NP + r], uu[m]);
-                A[(int64_t)r * N + j] = v;
+            for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+              for (int cc = 0; cc < 4; ++cc) {
+                const int j = jc + cc;
+                if (okr[rr] && j < N)
+                  *reinterpret_cast<unsigned long long*>(A + (int64_t)rw[rr] * N + j) = V[rr][cc];
               }
+          }
+        } else {
+          {
+            const int col = tid % CW, rg = tid / CW;
+            const int j = j0 + col;
+            Cx<R> uu[NB];
+  #pragma unroll
+            for (int m = 0; m < NB; ++m) uu[m] = u12[m * CW + col];
+            if (j < N) {
+              constexpr int RF = 8;  // rows in flight: independent loads per thread
+              int r = rg;
+              for (; r + (RF - 1) * RG < N; r += RF * RG) {
+                bool act[RF];
+                Cx<R> v[RF];
+  #pragma unroll
+                for (int q = 0; q < RF; ++q) {
+                  act[q] = pivstep[r + q * RG] == N;
+                  v[q] = act[q] ? A[(int64_t)(r + q * RG) * N + j] : Cx<R>{0, 0};
+                }
+  #pragma unroll
+                for (int q = 0; q < RF; ++q)
+                  if (act[q]) {
+  #pragma unroll
+                    for (int m = 0; m < NB; ++m) cx_fnma(v[q], pan[m * NP + r + q * RG], uu[m]);
+                    A[(int64_t)(r + q * RG) * N + j] = v[q];
+                  }
+              }
+              for (; r < N; r += RG)
+                if (pivstep[r] == N) {
+                  Cx<R> v = A[(int64_t)r * N + j];
+  #pragma unroll
+                  for (int m = 0; m < NB; ++m) cx_fnma(v, pan[m * NP + r], uu[m]);
+                  A[(int64_t)r * N + j] = v;
+                }
+            }
           }
         }
         __syncthreads();
