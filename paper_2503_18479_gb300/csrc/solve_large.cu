@@ -500,6 +500,50 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
         __syncthreads();
       }
     }
+    // ---- the diagonal blocks in place by their inverses: W_b = L_bb^-1 (unit lower, below
+    // the diagonal) and V_b = U_bb^-1 (upper, diagonal included), so that the triangular
+    // solves apply each block as one product instead of a 16-step substitution chain. A
+    // warp stages its block (rows in pivot order) in the panel's shared memory, free after
+    // the LU; lane c forms column c of both inverses. ----
+    {
+      Cx<R>* blk = pan + (int64_t)warp * NB * NB;  // [NB][NB], row i = pivot row order[c0 + i]
+      const int wi_n = min(W, NP / NB);             // warps whose slice fits the panel region
+      if (warp < wi_n) {
+        for (int c0 = warp * NB; c0 < N; c0 += wi_n * NB) {
+          const int nb = min(NB, N - c0);
+          for (int e = lane; e < NB * NB; e += 32) {
+            const int i = e / NB, m = e - i * NB;
+            blk[e] = (i < nb && m < nb) ? A[(int64_t)order[c0 + i] * N + c0 + m] : Cx<R>{0, 0};
+          }
+          __syncwarp();
+          if (lane < nb) {
+            const int c = lane;
+            Cx<R> w[NB], v[NB];
+#pragma unroll
+            for (int i = 0; i < NB; ++i) {  // W column c: w_c = 1, w_i = -sum_{m<i} L_im w_m
+              Cx<R> acc = {(R)(i == c ? 1 : 0), (R)0};
+#pragma unroll
+              for (int m = 0; m < i; ++m)
+                if (m >= c) cx_fnma(acc, blk[i * NB + m], w[m]);
+              w[i] = (i >= c && i < nb) ? acc : Cx<R>{0, 0};
+            }
+#pragma unroll
+            for (int i = NB - 1; i >= 0; --i) {  // V column c: U v = e_c, rows c .. 0
+              Cx<R> acc = {(R)(i == c ? 1 : 0), (R)0};
+#pragma unroll
+              for (int m = i + 1; m < NB; ++m)
+                if (m <= c) cx_fnma(acc, blk[i * NB + m], v[m]);
+              v[i] = (i <= c) ? cx_div(acc, blk[i * NB + i]) : Cx<R>{0, 0};
+            }
+#pragma unroll
+            for (int i = 0; i < NB; ++i)
+              if (i < nb) A[(int64_t)order[c0 + i] * N + c0 + c] = (i > c) ? w[i] : v[i];
+          }
+          __syncwarp();
+        }
+      }
+      __syncthreads();
+    }
     if (!bwd && a.lu_order != nullptr)
       for (int k = tid; k < N; k += T) a.lu_order[ioff + k] = order[k];
   }  // need_lu
@@ -521,12 +565,17 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
 #pragma unroll
         for (int m = 0; m < NB; ++m) {
           lr[m] = {0, 0};
-          if (lane < nb && m < lane) lr[m] = A[(int64_t)pi * N + c0 + m];
+          if (lane < nb && m < lane) lr[m] = A[(int64_t)pi * N + c0 + m];  // W_b row
         }
+        // y_b = W_b w_b (unit diagonal): products of the block's original values
+        const Cx<R> w0 = wi;
 #pragma unroll
         for (int m = 0; m < NB; ++m) {
-          const Cx<R> ym = {__shfl_sync(0xffffffffu, wi.x, m), __shfl_sync(0xffffffffu, wi.y, m)};
-          if (lane > m && lane < nb) cx_fnma(wi, lr[m], ym);
+          const Cx<R> wm = {__shfl_sync(0xffffffffu, w0.x, m), __shfl_sync(0xffffffffu, w0.y, m)};
+          if (lane > m && lane < nb) {  // wi += W_im w_m
+            wi.x = fma(lr[m].x, wm.x, fma(-lr[m].y, wm.y, wi.x));
+            wi.y = fma(lr[m].x, wm.y, fma(lr[m].y, wm.x, wi.y));
+          }
         }
         if (lane < NB) pvec[lane] = lane < nb ? wi : Cx<R>{0, 0};
         if (lane < nb) wv[pi] = wi;
@@ -555,13 +604,18 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
 #pragma unroll
         for (int m = 0; m < NB; ++m) {
           ur[m] = {0, 0};
-          if (lane < nb && m >= lane && m < nb) ur[m] = A[(int64_t)pi * N + c0 + m];
+          if (lane < nb && m >= lane && m < nb) ur[m] = A[(int64_t)pi * N + c0 + m];  // V_b row
         }
+        // x_b = V_b y_b: products of the block's values
+        const Cx<R> y0 = wi;
+        wi = {0, 0};
 #pragma unroll
-        for (int m = NB - 1; m >= 0; --m) {
-          if (lane == m && lane < nb) wi = cx_div(wi, ur[m]);
-          const Cx<R> xm = {__shfl_sync(0xffffffffu, wi.x, m), __shfl_sync(0xffffffffu, wi.y, m)};
-          if (lane < m && m < nb) cx_fnma(wi, ur[m], xm);
+        for (int m = 0; m < NB; ++m) {
+          const Cx<R> ym = {__shfl_sync(0xffffffffu, y0.x, m), __shfl_sync(0xffffffffu, y0.y, m)};
+          if (m >= lane && m < nb && lane < nb) {  // wi += V_im y_m
+            wi.x = fma(ur[m].x, ym.x, fma(-ur[m].y, ym.y, wi.x));
+            wi.y = fma(ur[m].x, ym.y, fma(ur[m].y, ym.x, wi.y));
+          }
         }
         if (lane < NB) pvec[lane] = lane < nb ? wi : Cx<R>{0, 0};
         if (lane < nb) wv[pi] = wi;
