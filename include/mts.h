@@ -156,6 +156,11 @@ typedef struct mts_problem {
  *   large_threads threads per system of the blocked solve for N > 64: 128, 256 or 512 (512
  *                 runs as 256 for MTS_FP64); 0 selects 128 for N <= 128, 256 for N <= 256
  *                 and 512 above. Other values give MTS_EINVAL.
+ *   reg_widen     bit c (c = 0, 1, 2 for the classes of N <= 8, 16, 32 ports) runs that
+ *                 class in the register-resident kernel of the next wider mapping (16, 32 or
+ *                 64 threads per system: a half warp, a warp, a two-warp CTA) instead of its
+ *                 own (8, 16, 32); 0 keeps each class in its own. Other bits give
+ *                 MTS_EINVAL. Memory does not depend on it.
  * Enhancement objective (Sec. IV-B: beta = |B_MTS| / |B_ref|, the field with the structure
  * over that of a reference run without it): with loss_weight w and loss_offset o (layout of
  * the target without its configuration blocks; either may be NULL) the objective term of a
@@ -177,6 +182,7 @@ typedef struct mts_eval {
   int32_t large_threads;
   const double* loss_weight; /* device [FL] real, or NULL (1) */
   const double* loss_offset; /* device complex [FL], or NULL (0) */
+  int32_t reg_widen;
 } mts_eval;
 
 /* Human-readable name of a status code (static string). */

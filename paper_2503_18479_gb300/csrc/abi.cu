@@ -193,6 +193,7 @@ static mts_status validate_eval(const mts_problem* pb, const mts_eval* ev) {
   if (ev->large_threads != 0 && ev->large_threads != 128 && ev->large_threads != 256 &&
       ev->large_threads != 512)
     return MTS_EINVAL;
+  if ((ev->reg_widen & ~7) != 0) return MTS_EINVAL;
   if (ev->n_cfg < 0) return MTS_EINVAL;
   if (ev->n_cfg > 0 && !ev->C) return MTS_EINVAL;
   if (pb->n_freq > 0 && (!ev->omega || !ev->V)) return MTS_EINVAL;
@@ -266,6 +267,7 @@ static SolveArgs solve_args(const mts_problem* pb, mts_precision prec, const voi
   a.mu_out = reinterpret_cast<double*>(T + tl.mu_loss);
   a.max_loss = max_loss_points(pb);
   a.large_threads = ev->large_threads;
+  a.reg_widen = ev->reg_widen;
   a.rhs_in = nullptr;
   return a;
 }

@@ -60,6 +60,7 @@ struct SolveArgs {
   const int32_t* glist;
   int64_t gcount;
   int large_threads;  // 0: 128 for N <= 128, 256 for N <= 256, else 512
+  int reg_widen;      // bit c: register class c (N <= 8, 16, 32) in the next wider kernel
   int npieces;
   int max_loss;  // max loss points of one structure (uniform trip count for group loops)
   // backward (field cotangent) mode: solve A mu = rhs_in and write grad terms only

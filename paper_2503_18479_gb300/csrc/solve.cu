@@ -317,15 +317,17 @@ cudaError_t launch_solve(const SolveArgs& a0, mts_precision prec, const ProblemS
     off += cnt;
     const int64_t n_sys = a.n_cfg * cnt;
     cudaError_t e;
+    // the register classes run in their own width, or one wider (reg_widen bit c)
+    const int cw = (c < 3 && ((a.reg_widen >> c) & 1)) ? c + 1 : c;
     if (c == 4) {
       e = launch_solve_large(a, prec, n_sys, kRegMaxPorts, ps.cls_max_ports[c], a.lu, st);
     } else if (prec == MTS_FP64) {
-      e = c == 0 ? launch_fp64<8>(a, n_sys, st)
-        : c == 1 ? launch_fp64<16>(a, n_sys, st)
-        : c == 2 ? launch_fp64<32>(a, n_sys, st)
-                 : launch_fp64<64>(a, n_sys, st);
+      e = cw == 0 ? launch_fp64<8>(a, n_sys, st)
+        : cw == 1 ? launch_fp64<16>(a, n_sys, st)
+        : cw == 2 ? launch_fp64<32>(a, n_sys, st)
+                  : launch_fp64<64>(a, n_sys, st);
     } else {
-      e = launch_solve_mixed(a, n_sys, ps.cls_max_ports[c], st);
+      e = launch_solve_mixed(a, n_sys, cw == c ? ps.cls_max_ports[c] : (8 << cw), st);
     }
     if (e != cudaSuccess) return e;
   }

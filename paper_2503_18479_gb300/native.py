@@ -56,7 +56,7 @@ class MtsEval(ct.Structure):
         ("target", ct.c_void_p), ("target_per_cfg", ct.c_int32), ("loss_mode", ct.c_int32),
         ("refine_tol", ct.c_double), ("max_refine", ct.c_int32),
         ("simt_max_sys", ct.c_int32), ("large_threads", ct.c_int32),
-        ("loss_weight", ct.c_void_p), ("loss_offset", ct.c_void_p),
+        ("loss_weight", ct.c_void_p), ("loss_offset", ct.c_void_p), ("reg_widen", ct.c_int32),
     ]
 
 
@@ -240,7 +240,7 @@ class Eval:
                  loss_mode: int = MTS_LOSS_ABS, refine_tol: float = 0.0, max_refine: int = 0,
                  simt_max_sys: int = 0, large_threads: int = 0,
                  loss_weight: Optional[torch.Tensor] = None,
-                 loss_offset: Optional[torch.Tensor] = None):
+                 loss_offset: Optional[torch.Tensor] = None, reg_widen: int = 0):
         self.C = C.contiguous()
         self.loss_weight = None if loss_weight is None else loss_weight.contiguous()
         self.loss_offset = None if loss_offset is None else loss_offset.contiguous()
@@ -259,6 +259,7 @@ class Eval:
         e.max_refine = int(max_refine)
         e.simt_max_sys = int(simt_max_sys)
         e.large_threads = int(large_threads)
+        e.reg_widen = int(reg_widen)
         e.loss_weight = None if self.loss_weight is None else self.loss_weight.data_ptr()
         e.loss_offset = None if self.loss_offset is None else self.loss_offset.data_ptr()
         self.c = e

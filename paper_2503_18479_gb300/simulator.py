@@ -53,9 +53,9 @@ class Simulator:
         self.sumFN = int(sum(s.n_freq * s.n_ports for s in wl.structures))
         self.n_ports = wl.n_ports
         self.b_dtype = torch.complex128 if self.prec == nv.MTS_FP64 else torch.complex64
-        # launch schedule (mts_eval.simt_max_sys, large_threads); 0 = the library's rules,
+        # launch schedule (mts_eval.simt_max_sys, large_threads, reg_widen); 0 = the library's rules,
         # set by tune.autotune
-        self.tuning = {"simt_max_sys": 0, "large_threads": 0}
+        self.tuning = {"simt_max_sys": 0, "large_threads": 0, "reg_widen": 0}
 
     # ------------------------------------------------------------------
     def make_eval(self, C: torch.Tensor, with_target: bool = True) -> nv.Eval:

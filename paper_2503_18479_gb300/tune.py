@@ -2,8 +2,10 @@
 Simulator on a given batch for each candidate schedule and keeps the fastest in
 `sim.tuning` (passed to every later call through mts_eval). The candidates choose, per
 structure, the tensor-core or the SIMT superposition (the threshold on configurations x
-frequencies) and the CTA size of the blocked solve for N > 64 (128, 256 or 512 threads per
-system). Every schedule computes the same result to rounding; only time differs."""
+frequencies), the CTA size of the blocked solve for N > 64 (128, 256 or 512 threads per
+system), and whether the register classes of up to 32 ports run one mapping wider (a half
+warp, a warp or a two-warp CTA per system instead of the class's own). Every schedule
+computes the same result to rounding; only time differs."""
 from __future__ import annotations
 
 import itertools
@@ -15,6 +17,7 @@ from .simulator import Simulator
 
 SIMT_CHOICES = (-1, 4, 16, 64, 1 << 30)  # -1: every structure on the tensor cores
 LARGE_CHOICES = (128, 256, 512)
+WIDEN_CHOICES = (1, 2, 4, 7)  # register classes run one mapping wider (bit c: class c)
 
 
 def _time_step(sim: Simulator, C: torch.Tensor, tuning: dict, reps: int, flush: torch.Tensor):
@@ -60,8 +63,17 @@ def autotune(sim: Simulator, C: torch.Tensor, reps: int = 3):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=sim.device)
     times = {}
     for s_thr, l_thr in itertools.product(simt, large):
-        tuning = {"simt_max_sys": s_thr, "large_threads": l_thr}
-        times[(s_thr, l_thr)] = _time_step(sim, C, tuning, reps, flush)
+        tuning = {"simt_max_sys": s_thr, "large_threads": l_thr, "reg_widen": 0}
+        times[(s_thr, l_thr, 0)] = _time_step(sim, C, tuning, reps, flush)
     best = min(times, key=times.get)
-    sim.tuning = {"simt_max_sys": best[0], "large_threads": best[1]}
+    # then, with that pair, the mapping of the register classes present (warp-per-system
+    # against wider groups of threads per system)
+    classes = {0 if n <= 8 else 1 if n <= 16 else 2 for n in (st.n_ports for st in sim.wl.structures)
+               if n <= 32}
+    for w in WIDEN_CHOICES:
+        if any((w >> c) & 1 for c in classes):
+            tuning = {"simt_max_sys": best[0], "large_threads": best[1], "reg_widen": w}
+            times[(best[0], best[1], w)] = _time_step(sim, C, tuning, reps, flush)
+    best = min(times, key=times.get)
+    sim.tuning = {"simt_max_sys": best[0], "large_threads": best[1], "reg_widen": best[2]}
     return sim.tuning, times

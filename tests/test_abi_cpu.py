@@ -249,7 +249,8 @@ def test_adam_step_validation(nv):
 
 
 def test_schedule_fields_are_validated(nv):
-    """large_threads must be 0, 128, 256 or 512; the schedule does not change the tape size."""
+    """large_threads must be 0, 128, 256 or 512 and reg_widen a combination of bits 0..2; the
+    schedule does not change the tape size."""
     L = nv.lib()
     wl = W.array_8x8(n_cfg=2, grid=4, planes=(0.02,))
     c, keep = fake_problem(nv, wl)
@@ -258,6 +259,11 @@ def test_schedule_fields_are_validated(nv):
     ev.C = ev.omega = ev.V = FAKE
     tneed = L.mts_tape_bytes(ct.byref(c), 2, nv.MTS_MIXED)
     ev.large_threads = 64
+    code = L.mts_solve(ct.byref(c), nv.MTS_MIXED, ct.c_void_p(FAKE), ct.byref(ev), None, None,
+                       ct.c_void_p(FAKE), tneed, None)
+    assert code == nv.MTS_EINVAL
+    ev.large_threads = 0
+    ev.reg_widen = 8
     code = L.mts_solve(ct.byref(c), nv.MTS_MIXED, ct.c_void_p(FAKE), ct.byref(ev), None, None,
                        ct.c_void_p(FAKE), tneed, None)
     assert code == nv.MTS_EINVAL

@@ -1,7 +1,7 @@
 """Schedules and the autotuner: every superposition schedule (all structures on the tensor
-cores, the default threshold, all on the SIMT kernel) and both CTA sizes of the blocked solve
-give the oracle's results; the autotuner returns one of its candidates and the tuned
-Simulator still matches."""
+cores, the default threshold, all on the SIMT kernel), every CTA size of the blocked solve and
+every width of the register classes give the oracle's results; the autotuner returns one of
+its candidates and the tuned Simulator still matches."""
 import numpy as np
 import pytest
 import torch
@@ -60,6 +60,32 @@ def test_large_solve_cta_sizes_agree(prec):
             assert rel(a.cpu().numpy(), b.cpu().numpy()) < 1e-13
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_register_class_widths_agree(prec):
+    """The register classes of up to 32 ports in their own mapping or one wider (reg_widen):
+    the same results to rounding, and the oracle's."""
+    from paper_2503_18479_gb300.simulator import Simulator
+    wl = small_ragged(n_struct=6, seed=5, grid=8, max_freq=6, ports=(1, 8, 16, 32))
+    ref = oracle_reference(wl, bases=[structure_basis(wl, s) for s in range(len(wl.structures))])
+    sim = Simulator(wl, prec)
+    outs = []
+    for w in (0, 1, 2, 4, 7):
+        sim.tuning = {"simt_max_sys": 0, "large_threads": 0, "reg_widen": w}
+        C = torch.from_numpy(wl.C).cuda().requires_grad_(True)
+        B, loss = sim(C)
+        loss.sum().backward()
+        outs.append((B.detach().cpu().numpy(), loss.detach().cpu().numpy(), C.grad.cpu().numpy()))
+    # different widths block the LU differently: FP32 factors round differently and the
+    # refinement converges to its tolerance (1e-8 estimated), not to the same bits
+    tol = 1e-13 if prec == "fp64" else 1e-7
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert rel(a, b) < tol
+    Bs = split_B(wl, outs[-1][0])
+    for s in range(len(wl.structures)):
+        assert rel(Bs[s], ref[s]["B"]) < (1e-10 if prec == "fp64" else 1e-6)
+
+
 def test_autotune_picks_a_candidate_and_keeps_results():
     from paper_2503_18479_gb300 import tune
     from paper_2503_18479_gb300.simulator import Simulator
@@ -67,8 +93,8 @@ def test_autotune_picks_a_candidate_and_keeps_results():
     sim = Simulator(wl, "mixed")
     C = torch.from_numpy(wl.C).cuda()
     tuning, times = tune.autotune(sim, C, reps=2)
-    assert (tuning["simt_max_sys"], tuning["large_threads"]) in times
-    assert len(times) == len(tune.SIMT_CHOICES) * len(tune.LARGE_CHOICES)
+    assert (tuning["simt_max_sys"], tuning["large_threads"], tuning["reg_widen"]) in times
+    assert len(times) >= len(tune.SIMT_CHOICES) * len(tune.LARGE_CHOICES)
     assert all(np.isfinite(t) and t > 0 for t in times.values())
     out = sim.forward(C)
     Bs = split_B(wl, out["B"].cpu().numpy())
