@@ -43,6 +43,10 @@ _CASES = {
     "32x32few": lambda: W.array_32x32(seed=3, n_cfg=3, grid=12, planes=(0.02,), seg_per_side=2),
     # 80 ports: the large-system kernel at 128 threads in both precisions
     "10x8": lambda: small_rect(10, 8, n_cfg=20, n_freq=2, grid=10, seed=4),
+    # odd point counts with two frequencies: rows of grad_B that start on an odd point (the
+    # tensor-core field adjoint's 8-byte copies) and a ragged last K step
+    "8x8odd": lambda: small_rect(8, 8, n_cfg=12, n_freq=2, grid=9, seed=13),
+    "10x8odd": lambda: small_rect(10, 8, n_cfg=12, n_freq=2, grid=9, seed=14),
     # circular loops: mutual inductances from oblique segment pairs (quadrature)
     "circles": lambda: W.circle_array(3, 3, seed=6, n_cfg=40, n_freq=3, grid=12),
     # circular loops whose self inductances come from their own segments: the polygon
@@ -122,7 +126,7 @@ def test_gradient(name, prec):
         assert cosine(g[s], ref[s]["grad"]) >= 0.9999
 
 
-@pytest.mark.parametrize("name", ["8x8", "ragged128", "32x32", "32x32few"])
+@pytest.mark.parametrize("name", ["8x8", "ragged128", "32x32", "32x32few", "8x8odd", "10x8odd"])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_field_cotangent(name, prec):
     """Backward with a field cotangent dL/dRe B + j dL/dIm B (and a loss cotangent)."""
@@ -172,12 +176,13 @@ def test_field_cotangent_kept_factors(name, prec):
         torch.autograd.backward([B, loss], [gBt, torch.ones_like(loss)])
         grads.append(C.grad.cpu().numpy())
     assert np.array_equal(grads[0], grads[1])
-    if prec == "mixed":
-        bases = [structure_basis(sub, s) for s in range(len(sub.structures))]
-        ref = oracle_reference(sub, want_B=False, gB=gBs, bases=bases)
-        want = np.concatenate([ref[s]["grad_field"] + ref[s]["grad"] for s in range(len(sub.structures))],
-                              axis=1)
-        assert rel(grads[1], want) < 1e-5, rel(grads[1], want)
+    bases = [structure_basis(sub, s) for s in range(len(sub.structures))]
+    ref = oracle_reference(sub, want_B=False, gB=gBs, bases=bases)
+    want = np.concatenate([ref[s]["grad_field"] + ref[s]["grad"] for s in range(len(sub.structures))],
+                          axis=1)
+    # MTS_BF16: one bf16 pair in the superposition and the field adjoint (2^-8 per operand)
+    tol = 1e-5 if prec == "mixed" else 5e-2
+    assert rel(grads[1], want) < tol, rel(grads[1], want)
 
 
 def test_complex_target_mode():
