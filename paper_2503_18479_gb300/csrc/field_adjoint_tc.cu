@@ -3,9 +3,9 @@
 //   u[b][f][k] = sum_p H[p][k] conj(grad_B[b][f][p])
 // for a problem with one structure on the tensor path (MTS_MIXED, MTS_BF16).
 //
-// Real GEMM: per tile of 64 systems i = b F + f, rows il (Re grad_B) and 64 + il (-Im grad_B),
+// Real GEMM: per tile of 64 systems i = b F + f, rows il (Re grad_B) and 64 + il (Im grad_B),
 // K = field points, columns = ports: D[c 64 + il][k] = sum_p G_c[i][p] H[p][k], so that
-// u = D[il][k] + j D[64 + il][k]. The H operand is the basis image the superposition already
+// u = D[il][k] - j D[64 + il][k]. The H operand is the basis image the superposition already
 // keeps (bf16 pieces of H, [piece][point tile][port chunk][128 points x 64 ports] in the
 // 128-byte-swizzled layout): read with points as K and ports as the contiguous dimension it
 // is the MN-major B operand of this GEMM, so nothing is repacked. grad_B (complex64, the
@@ -27,8 +27,9 @@
 //                warp instruction reads 512 contiguous bytes of one row; row pitch 528 bytes
 //                in shared memory so that the 16-byte reads below hit distinct banks), RAW - 1
 //                K steps ahead; then thread = one A row (TMEM lane 32 (warp % 4) + lane: Re
-//                of system lane quarters 0-1, -Im quarters 2-3), 32 of the step's 64 points
-//                (warps 2..5 the first half, 6..9 the second): conj, bf16 pieces, tcgen05.st
+//                of system lane quarters 0-1, Im quarters 2-3), 32 of the step's 64 points
+//                (warps 2..5 the first half, 6..9 the second): bf16 pieces, tcgen05.st (the
+//                conj's sign is applied in the K-split reduction)
 //   warps 10..17 epilogue: tcgen05.ld of the accumulator into double-float (FP32 hi + lo)
 //                running sums (one TMEM lane = one row, 32 of the 64 columns per thread: two
 //                warps per lane quarter), at the unit's end the FP32 partial of its K split
@@ -301,40 +302,48 @@ __global__ void __launch_bounds__(kThreads, 1) field_adjoint_tc_kernel(FaTcArgs 
     const int quarter = warp & 3;          // TMEM lane quarter this warp may access
     const int R = quarter * 32 + lane;     // A row = TMEM lane
     const int il = R & 63;                 // system of the tile
-    const bool imag = R >= 64;             // rows 64.. hold -Im grad_B (warp-uniform)
+    const bool imag = R >= 64;             // rows 64.. hold Im grad_B (warp-uniform; the
+                                           // reduce applies the conj's sign)
     const int hp = (warp - 2) >> 2;        // half of the step's 64 points
     const uint32_t trow = tmem_base + ((uint32_t)(quarter * 32) << 16) + kAColBase + 16u * hp;
     // prefetch cursor: (unit, step) RAW - 1 steps ahead, with the first copied row's (b, f)
     int64_t pu = u_begin;
     int pt = 0, pt1 = 0;
-    int64_t pb0 = 0;
-    int pf0 = 0;
-    int64_t psys0 = 0;
+    const float2* rsrc[8];  // the warp's 8 rows of the cursor's unit (NULL past nsys)
+    unsigned ralign = 0;    // bit j: row j starts on a 16-byte boundary
     auto cur_unit = [&]() {
       if (pu < u_end) {
         const UnitPos q = unit_pos(a, pu);
         pt = q.t0;
         pt1 = q.t1;
-        psys0 = q.mt * 64 + 8 * cw;
-        pb0 = psys0 / a.F;
-        pf0 = (int)(psys0 - pb0 * a.F);
+        const int64_t psys0 = q.mt * 64 + 8 * cw;
+        int64_t bb = psys0 / a.F;
+        int ff = (int)(psys0 - bb * a.F);
+        ralign = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float2* src = a.gB + bb * a.sumFP + a.fpo + (int64_t)ff * a.P;
+          rsrc[j] = psys0 + j < a.nsys ? src : nullptr;
+          if ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) ralign |= 1u << j;
+          if (++ff == a.F) {
+            ff = 0;
+            ++bb;
+          }
+        }
       }
     };
     auto issue = [&](int slot) {  // copies of the cursor's step into raw slot `slot`, one group
       if (pu < u_end) {
         const int64_t p0 = (int64_t)pt * kStepPts + 2 * lane;  // this lane's first point
         const int nvalid = (int)max((int64_t)0, min((int64_t)2, a.P - p0));
-        int64_t bb = pb0;
-        int ff = pf0;
+        const uint32_t dst0 = smem_u32(raws + slot * kRawStage + 8 * cw * kRawPitch + 16 * lane);
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          const int row = 8 * cw + j;
-          const bool vs = psys0 + j < a.nsys;
-          const float2* src = a.gB + bb * a.sumFP + a.fpo + (int64_t)ff * a.P;
-          const uint32_t dst = smem_u32(raws + slot * kRawStage + row * kRawPitch + 16 * lane);
-          const int n = vs ? nvalid : 0;
+          const float2* src = rsrc[j];
+          const uint32_t dst = dst0 + (uint32_t)(j * kRawPitch);
+          const int n = src ? nvalid : 0;
           const float2* sp = n > 0 ? src + p0 : a.gB;
-          if ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
+          if ((ralign >> j) & 1u) {
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(sp),
                          "r"((uint32_t)(8 * n))
                          : "memory");
@@ -345,10 +354,6 @@ __global__ void __launch_bounds__(kThreads, 1) field_adjoint_tc_kernel(FaTcArgs 
             asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst + 8u),
                          "l"(n >= 2 ? sp + 1 : a.gB), "r"(n >= 2 ? 8u : 0u)
                          : "memory");
-          }
-          if (++ff == a.F) {
-            ff = 0;
-            ++bb;
           }
         }
         if (++pt == pt1) {
@@ -399,8 +404,8 @@ __global__ void __launch_bounds__(kThreads, 1) field_adjoint_tc_kernel(FaTcArgs 
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
             const float4 v = s4[i];
-            x[2 * i] = -v.y;
-            x[2 * i + 1] = -v.w;
+            x[2 * i] = v.y;
+            x[2 * i + 1] = v.w;
           }
         } else {
 #pragma unroll
@@ -506,7 +511,7 @@ __global__ void fa_reduce_kernel(FaTcArgs a, double* __restrict__ u, int64_t sum
   for (int ks = 0; ks < a.nsplit; ++ks) {
     const float* p = a.part + ((int64_t)ks * a.npad + k) * a.rows_pad + row;
     sr += (double)p[0];
-    si += (double)p[64];
+    si -= (double)p[64];  // rows 64.. hold Im grad_B: conj
   }
   const int64_t b = i / a.F, f = i - b * a.F;
   double* d = u + 2 * (b * sumFN + fno + f * a.N + k);
