@@ -102,6 +102,31 @@ __device__ inline void tmem_ld16(uint32_t taddr, float* v) {
       : "memory");
 }
 
+// TwoSum on two columns at once: (hi, lo) += v per lane of the packed FP32 pairs (the same
+// roundings as the scalar form; add/sub.rn.f32x2 round each lane as add/sub.rn.f32)
+__device__ inline void two_sum_acc2(unsigned long long& hi, unsigned long long& lo,
+                                    unsigned long long v) {
+  unsigned long long sm, bp, t1, t2, e;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(sm) : "l"(hi), "l"(v));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(bp) : "l"(sm), "l"(hi));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(t1) : "l"(sm), "l"(bp));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(t1) : "l"(hi), "l"(t1));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(t2) : "l"(v), "l"(bp));
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(e) : "l"(t1), "l"(t2));
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(lo) : "l"(lo), "l"(e));
+  hi = sm;
+}
+
+// 2 n values -> n packed bf16 pairs (round to nearest), no remainder (the last piece)
+template <int n>
+__device__ inline void bf16_pack(const float* x, uint32_t* pk) {
+#pragma unroll
+  for (int i = 0; i < n; ++i) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(x[2 * i], x[2 * i + 1]);
+    pk[i] = *reinterpret_cast<const uint32_t*>(&h);
+  }
+}
+
 template <int NPIECE>
 struct Cfg {
   static constexpr int NSTAGE = NPIECE == 3 ? 3 : 4;  // operand stages (A in TMEM, B in smem)
@@ -417,13 +442,16 @@ __global__ void __launch_bounds__(kThreads, 1) field_adjoint_tc_kernel(FaTcArgs 
         }
         const uint32_t ta = trow + (uint32_t)(stage * NPIECE) * kAPieceCols;
         uint32_t pk[16];
-        bf16_split<16>(x, pk);
-        tmem_st16(ta, pk);
         if (NPIECE == 3) {
           bf16_split<16>(x, pk);
-          tmem_st16(ta + kAPieceCols, pk);
+          tmem_st16(ta, pk);
           bf16_split<16>(x, pk);
+          tmem_st16(ta + kAPieceCols, pk);
+          bf16_pack<16>(x, pk);
           tmem_st16(ta + 2 * kAPieceCols, pk);
+        } else {
+          bf16_pack<16>(x, pk);
+          tmem_st16(ta, pk);
         }
         tmem_wait_st();
         tc_fence_before();
@@ -446,9 +474,9 @@ __global__ void __launch_bounds__(kThreads, 1) field_adjoint_tc_kernel(FaTcArgs 
     bool alive = true;
     for (int64_t u = u_begin; u < u_end && alive; ++u) {
       const UnitPos q = unit_pos(a, u);
-      float hi[32], lo[32];
+      unsigned long long hi[16], lo[16];  // columns (2c, 2c + 1) as packed pairs
 #pragma unroll
-      for (int c = 0; c < 32; ++c) hi[c] = lo[c] = 0.0f;
+      for (int c = 0; c < 16; ++c) hi[c] = lo[c] = 0ull;
       for (int g0 = q.t0; g0 < q.t1; g0 += kDrain) {
         int ok = (lane == 0) ? (int)mbar_wait_sleep(&tfull[acc], aphase, err, 18) : 1;
         ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -465,7 +493,11 @@ __global__ void __launch_bounds__(kThreads, 1) field_adjoint_tc_kernel(FaTcArgs 
           tmem_ld16(tcol + 16u * hh, v);
           tmem_wait_ld();
 #pragma unroll
-          for (int c = 0; c < 16; ++c) two_sum_acc(hi[16 * hh + c], lo[16 * hh + c], v[c]);
+          for (int c = 0; c < 8; ++c) {
+            unsigned long long vv;
+            asm("mov.b64 %0, {%1,%2};" : "=l"(vv) : "f"(v[2 * c]), "f"(v[2 * c + 1]));
+            two_sum_acc2(hi[8 * hh + c], lo[8 * hh + c], vv);
+          }
         }
         tc_fence_before();
         mbar_arrive(&tempty[acc]);
@@ -478,7 +510,13 @@ __global__ void __launch_bounds__(kThreads, 1) field_adjoint_tc_kernel(FaTcArgs 
       const int64_t row = q.mt * 128 + quarter * 32 + lane;
       float* dst = a.part + ((int64_t)q.ks * a.npad + (int64_t)q.kc * 64 + 32 * half) * a.rows_pad + row;
 #pragma unroll
-      for (int c = 0; c < 32; ++c) dst[(int64_t)c * a.rows_pad] = hi[c] + lo[c];
+      for (int c = 0; c < 16; ++c) {
+        float h0, h1, l0, l1;
+        asm("mov.b64 {%0,%1}, %2;" : "=f"(h0), "=f"(h1) : "l"(hi[c]));
+        asm("mov.b64 {%0,%1}, %2;" : "=f"(l0), "=f"(l1) : "l"(lo[c]));
+        dst[(int64_t)(2 * c) * a.rows_pad] = h0 + l0;
+        dst[(int64_t)(2 * c + 1) * a.rows_pad] = h1 + l1;
+      }
     }
   }
 
