@@ -154,8 +154,11 @@ typedef struct mts_problem {
  *                 MTS_BF16); 0 selects 16, a negative value puts every structure on the
  *                 tensor cores. Memory does not depend on it.
  *   large_threads threads per system of the blocked solve for N > 64: 128, 256 or 512 (512
- *                 runs as 256 for MTS_FP64); 0 selects 128 for N <= 128, 256 for N <= 256
- *                 and 512 above. Other values give MTS_EINVAL.
+ *                 runs as 256 for MTS_FP64). With MTS_MIXED / MTS_BF16 and at most 128
+ *                 ports in the class, 256 and 512 keep the matrix in shared memory (one
+ *                 system per SM: faster per system, slower for a full machine) and 128
+ *                 keeps it in the factor scratch of the tape. 0 selects 128 for N <= 128,
+ *                 256 for N <= 256 and 512 above. Other values give MTS_EINVAL.
  *   reg_widen     bit c (c = 0, 1, 2 for the classes of N <= 8, 16, 32 ports) runs that
  *                 class in the register-resident kernel of the next wider mapping (16, 32 or
  *                 64 threads per system: a half warp, a warp, a two-warp CTA) instead of its

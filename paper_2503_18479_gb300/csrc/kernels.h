@@ -59,7 +59,7 @@ struct SolveArgs {
   // configurations x the gcount frequencies glist[0 .. gcount-1] of one port class
   const int32_t* glist;
   int64_t gcount;
-  int large_threads;  // 0: 128 for N <= 128, 256 for N <= 256, else 512
+  int large_threads;  // 0: the library's rule (solve_large.cu: large_threads)
   int reg_widen;      // bit c: register class c (N <= 8, 16, 32) in the next wider kernel
   int npieces;
   int max_loss;  // max loss points of one structure (uniform trip count for group loops)

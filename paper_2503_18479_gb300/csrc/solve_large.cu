@@ -35,6 +35,13 @@
 namespace mts {
 
 constexpr int kLargeMaxWarps = 16;  // CTAs of 128, 256 or 512 threads
+// FP32 classes of up to this many ports keep the matrix in shared memory with CTAs of 256 or
+// 512 threads (128 x 128 complex = 128 KB beside the 44 KB of panels and vectors): one CTA
+// per SM, every access of the LU and the solves at shared-memory latency. With one system
+// per SM instead of five, 14,206 systems of 128 ports took 32 ms against 17.5 ms in the
+// scratch form, so the scratch form with 128 threads stays the default and the
+// shared-resident one is a schedule choice that the autotuner times.
+constexpr int kLargeSmemPorts = 128;
 
 template <typename R>
 struct Cx {
@@ -85,8 +92,8 @@ struct BlockRed {
 template <typename R>
 struct LargeSmem {
   static constexpr int NB = LargeCfg<R>::NB, CW = LargeCfg<R>::CW;
-  size_t pan, u12, wv, piv, ord, rhs, sv, xk, xc, red, pvec, bytes;
-  __host__ __device__ explicit LargeSmem(int n) {
+  size_t pan, u12, wv, piv, ord, rhs, sv, xk, xc, red, pvec, amat, bytes;
+  __host__ __device__ explicit LargeSmem(int n, bool sa = false) {
     const size_t cx = sizeof(Cx<R>);
     size_t o = 0;
     pan = o; o += cx * (size_t)NB * (n + 1);  // panel, column-major, pitch n + 1
@@ -102,6 +109,9 @@ struct LargeSmem {
     red = o; o += sizeof(BlockRed);
     o = (o + 15) / 16 * 16;
     pvec = o; o += cx * NB;                   // panel part of y or x
+    o = (o + 15) / 16 * 16;
+    amat = o;                                 // the matrix itself (shared-resident form)
+    if (sa) o += cx * (size_t)n * n;
     bytes = o;
   }
 };
@@ -173,8 +183,20 @@ __device__ inline double block_sum(double v, BlockRed* red) {
 }
 
 // T threads per CTA (one system): 128 for N <= 128, so that more systems share an SM, else 256.
-template <typename R, int T>
-__global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_sys,
+// asynchronous copy of one matrix entry (8 or 16 bytes) from global to shared memory
+template <typename R>
+__device__ __forceinline__ void cp_async_elem(Cx<R>* dst, const Cx<R>* src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(Cx<R>) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+
+// SA: the matrix lives in shared memory (FP32, up to kLargeSmemPorts ports) and goes to the
+// factor scratch only as a copy for the backward; otherwise it stays in the scratch (L2).
+template <typename R, int T, bool SA>
+__global__ void __launch_bounds__(T, T == 128 ? 5 : (T == 256 ? 2 : 1)) solve_large_kernel(SolveArgs a, int64_t n_sys,
                                                                      int min_ports, int smem_n,
                                                                      Cx<R>* __restrict__ scratch) {
   constexpr int NB = LargeCfg<R>::NB, CW = LargeCfg<R>::CW;
@@ -187,7 +209,7 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
   if (N <= min_ports) return;  // a register-resident kernel owns this system (CTA-uniform)
 
   extern __shared__ __align__(16) unsigned char dsm[];
-  const LargeSmem<R> L(smem_n);
+  const LargeSmem<R> L(smem_n, SA);
   Cx<R>* pan = reinterpret_cast<Cx<R>*>(dsm + L.pan);
   Cx<R>* u12 = reinterpret_cast<Cx<R>*>(dsm + L.u12);
   Cx<R>* wv = reinterpret_cast<Cx<R>*>(dsm + L.wv);
@@ -214,7 +236,8 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
   const double* __restrict__ Cb = a.C + si.b * a.n_ports + si.k0;
   const double* __restrict__ Rk = a.R + si.k0;
   const int F = a.freq_off[si.s + 1] - a.freq_off[si.s];
-  Cx<R>* A = scratch + si.b * a.lu_off[a.n_struct] + a.lu_off[si.s] + (int64_t)si.f * N * N;
+  Cx<R>* const Ag = scratch + si.b * a.lu_off[a.n_struct] + a.lu_off[si.s] + (int64_t)si.f * N * N;
+  Cx<R>* const A = SA ? reinterpret_cast<Cx<R>*>(dsm + L.amat) : Ag;
 
   const int64_t ioff = si.b * a.sumFN + a.t.fn_off[si.s] + (int64_t)si.f * N;
   // A backward call reuses the factors and the pivot order the forward left in the tape
@@ -289,11 +312,22 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
     // ---- blocked LU with partial pivoting ----
     for (int c0 = 0; c0 < N; c0 += NB) {
       const int nb = min(NB, N - c0);
-      for (int e = tid; e < N * NB; e += T) {
-        const int r = e / NB, j = e - r * NB;
-        Cx<R> v = {0, 0};
-        if (j < nb && pivstep[r] == N) v = A[(int64_t)r * N + c0 + j];
-        pan[j * NP + r] = v;
+      // eight independent loads in flight per thread (the matrix may be in the scratch)
+      for (int e0 = 0; e0 < N * NB; e0 += 8 * T) {
+        Cx<R> v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int e = e0 + q * T + tid;
+          const int r = e / NB, j = e - r * NB;
+          v[q] = {0, 0};
+          if (e < N * NB && j < nb && pivstep[r] == N) v[q] = A[(int64_t)r * N + c0 + j];
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int e = e0 + q * T + tid;
+          const int r = e / NB, j = e - r * NB;
+          if (e < N * NB) pan[j * NP + r] = v[q];
+        }
       }
       __syncthreads();
       // pivot steps with one barrier each: a thread reads and writes only its own rows of the
@@ -356,7 +390,7 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
       // the list varies but every row's update is the same
       int nact = 0;
       int* alist = reinterpret_cast<int*>(wv);
-      if constexpr (kF && T <= 256) {
+      if constexpr (kF && (T <= 256 || SA)) {
         if (c0 + nb < N) {
           if (tid == 0) red->cnt = 0;
           __syncthreads();
@@ -378,19 +412,23 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
         if (tid < CW) {
           const int j = j0 + tid;
           if (j < N) {  // columns past N skip the unrolled work as a whole
+            // the nb entries of the pivot rows first (independent loads), then the unit
+            // lower solve L_bb u = a in place
             Cx<R> uu[NB];
 #pragma unroll
             for (int i = 0; i < NB; ++i) {
-              Cx<R> v = {0, 0};
+              uu[i] = {0, 0};
+              if (i < nb) uu[i] = A[(int64_t)order[c0 + i] * N + j];
+            }
+#pragma unroll
+            for (int i = 0; i < NB; ++i) {
               if (i < nb) {
                 const int pi = order[c0 + i];
-                v = A[(int64_t)pi * N + j];
 #pragma unroll
-                for (int m = 0; m < i; ++m) cx_fnma(v, pan[m * NP + pi], uu[m]);
-                A[(int64_t)pi * N + j] = v;
+                for (int m = 0; m < i; ++m) cx_fnma(uu[i], pan[m * NP + pi], uu[m]);
+                A[(int64_t)pi * N + j] = uu[i];
               }
-              uu[i] = v;
-              u12[i * CW + tid] = v;
+              u12[i * CW + tid] = uu[i];
             }
           } else {
 #pragma unroll
@@ -401,14 +439,15 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
         // (512-thread CTAs keep the per-column form below: on 1024-port systems, whose
         // trailing blocks stream through HBM, the tiles' longer compute between loads was
         // 2 % slower)
-        if constexpr (kF && T <= 256) {
-          // register-tiled update: a thread takes 4 listed rows x 4 columns (j0 + 4 cg ..),
+        if constexpr (kF && (T <= 256 || SA)) {
+          // register-tiled update: a thread takes 4 listed rows x 4 columns (j0 + lane + 32 cc,
+          // so that a warp's loads of one (row, cc) are 256 contiguous bytes: conflict-free in
+          // shared memory, coalesced in the scratch),
           // the (re, im) pairs of a tile in packed registers; per panel column m, with the
           // multiplier l = (a, b) and the U12 entry u = (c, d):
           //   v -= l u  <=>  (v.re, v.im) += (b, b) (d, -c) + (-a, -a) (c, d)
           // two fma.rn.f32x2 per complex multiply-add, 8 shared loads per 16 of them
-          const int cg = lane;  // the warp covers the chunk's 128 columns
-          const int jc = j0 + 4 * cg;
+          const int jc = j0 + lane;  // the warp covers the chunk's 128 columns
           const int ntile = (nact + 3) >> 2;
           for (int t4 = warp; t4 < ntile; t4 += W) {
             int rw[4];
@@ -423,7 +462,7 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
             for (int rr = 0; rr < 4; ++rr)
 #pragma unroll
               for (int cc = 0; cc < 4; ++cc) {
-                const int j = jc + cc;
+                const int j = jc + 32 * cc;
                 V[rr][cc] = (okr[rr] && j < N)
                                 ? *reinterpret_cast<const unsigned long long*>(A + (int64_t)rw[rr] * N + j)
                                 : 0ull;
@@ -439,7 +478,7 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
               }
 #pragma unroll
               for (int cc = 0; cc < 4; ++cc) {
-                const Cx<R> u = u12[m * CW + 4 * cg + cc];
+                const Cx<R> u = u12[m * CW + lane + 32 * cc];
                 asm("mov.b64 %0, {%1,%2};" : "=l"(P1[cc]) : "f"(u.x), "f"(u.y));
                 asm("mov.b64 %0, {%1,%2};" : "=l"(P2[cc]) : "f"(u.y), "f"(-u.x));
               }
@@ -456,7 +495,7 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
             for (int rr = 0; rr < 4; ++rr)
 #pragma unroll
               for (int cc = 0; cc < 4; ++cc) {
-                const int j = jc + cc;
+                const int j = jc + 32 * cc;
                 if (okr[rr] && j < N)
                   *reinterpret_cast<unsigned long long*>(A + (int64_t)rw[rr] * N + j) = V[rr][cc];
               }
@@ -547,41 +586,110 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
     if (!bwd && a.lu_order != nullptr)
       for (int k = tid; k < N; k += T) a.lu_order[ioff + k] = order[k];
   }  // need_lu
+  if constexpr (SA) {
+    // the factors between the forward and a backward that reuses them: 8-byte units (the
+    // scratch base of a system is 8-byte aligned), eight loads in flight per thread
+    using U8 = unsigned long long;
+    const int NN = N * N;
+    U8* sA = reinterpret_cast<U8*>(A);
+    U8* gA = reinterpret_cast<U8*>(Ag);
+    if (!need_lu || (!bwd && a.lu_order != nullptr)) {
+      U8* dst = need_lu ? gA : sA;
+      const U8* src = need_lu ? sA : gA;
+      for (int e0 = 0; e0 < NN; e0 += 8 * T) {
+        U8 v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int e = e0 + q * T + tid;
+          v[q] = e < NN ? src[e] : 0ull;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int e = e0 + q * T + tid;
+          if (e < NN) dst[e] = v[q];
+        }
+      }
+      __syncthreads();
+    }
+  }
 
   // ---- solve A x = rhs (FP64 rhs in shared memory) into wv (by row) with the factors;
-  // the unknown of column k ends in wv[order[k]] ----
+  // the unknown of column k ends in wv[order[k]]. With the factors in the scratch, each
+  // step's entries are copied one step ahead (cp.async) into shared memory that is idle
+  // during the solves: the block of row tid that the row update needs (in the panel region,
+  // element m of row t at m N + t; rows past T, N > T, load theirs in the step) and warp 0's
+  // rows of the diagonal block (in the U12 region), so that their latency overlaps the
+  // barrier and the diagonal block's products. A thread reads only what it copied. ----
+  Cx<R>* const stg = pan;  // [NB][N]
+  Cx<R>* const dstg = u12;  // [NB][32]
   auto lu_solve = [&]() {
     for (int r = tid; r < N; r += T) wv[r] = {(R)rhs[r].x, (R)rhs[r].y};
+    const int last = (N - 1) / NB * NB;
+    // step (c0, forward or back): rows that take the step's update, and the diagonal rows
+    auto fetch = [&](int c0, bool fwd) {
+      if constexpr (!SA) {
+        const int nb = min(NB, N - c0);
+        if (tid < N && (fwd ? pivstep[tid] >= c0 + nb : pivstep[tid] < c0)) {
+#pragma unroll
+          for (int m = 0; m < NB; ++m)
+            if (m < nb) cp_async_elem(stg + m * N + tid, A + (int64_t)tid * N + c0 + m);
+        }
+        if (warp == 0 && lane < nb) {
+          const int pi = order[c0 + lane];
+#pragma unroll
+          for (int m = 0; m < NB; ++m)  // W_b row (forward), V_b row (back)
+            if (fwd ? m < lane : (m >= lane && m < nb))
+              cp_async_elem(dstg + m * 32 + lane, A + (int64_t)pi * N + c0 + m);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+      }
+    };
+    // entry m of this thread's staged row block / diagonal row (the matrix itself when it
+    // is in shared memory)
+    auto row_elem = [&](int c0, int m) -> Cx<R> {
+      if constexpr (SA) return A[(int64_t)tid * N + c0 + m];
+      else return stg[m * N + tid];
+    };
+    auto diag_elem = [&](int c0, int pi, int m) -> Cx<R> {
+      if constexpr (SA) return A[(int64_t)pi * N + c0 + m];
+      else return dstg[m * 32 + lane];
+    };
+    fetch(0, true);
     __syncthreads();
     for (int c0 = 0; c0 < N; c0 += NB) {  // forward: L y = P rhs
       const int nb = min(NB, N - c0);
       if (warp == 0) {
-        Cx<R> wi = {0, 0}, lr[NB];
+        Cx<R> wi = {0, 0};
         int pi = 0;
         if (lane < nb) {
           pi = order[c0 + lane];
           wi = wv[pi];
         }
-#pragma unroll
-        for (int m = 0; m < NB; ++m) {
-          lr[m] = {0, 0};
-          if (lane < nb && m < lane) lr[m] = A[(int64_t)pi * N + c0 + m];  // W_b row
-        }
+        if constexpr (!SA) asm volatile("cp.async.wait_all;" ::: "memory");
         // y_b = W_b w_b (unit diagonal): products of the block's original values
         const Cx<R> w0 = wi;
 #pragma unroll
         for (int m = 0; m < NB; ++m) {
           const Cx<R> wm = {__shfl_sync(0xffffffffu, w0.x, m), __shfl_sync(0xffffffffu, w0.y, m)};
           if (lane > m && lane < nb) {  // wi += W_im w_m
-            wi.x = fma(lr[m].x, wm.x, fma(-lr[m].y, wm.y, wi.x));
-            wi.y = fma(lr[m].x, wm.y, fma(lr[m].y, wm.x, wi.y));
+            const Cx<R> l = diag_elem(c0, pi, m);
+            wi.x = fma(l.x, wm.x, fma(-l.y, wm.y, wi.x));
+            wi.y = fma(l.x, wm.y, fma(l.y, wm.x, wi.y));
           }
         }
         if (lane < NB) pvec[lane] = lane < nb ? wi : Cx<R>{0, 0};
         if (lane < nb) wv[pi] = wi;
       }
       __syncthreads();
-      for (int r = tid; r < N; r += T)
+      if constexpr (!SA) asm volatile("cp.async.wait_all;" ::: "memory");
+      if (tid < N && pivstep[tid] >= c0 + nb) {
+        Cx<R> v = wv[tid];
+#pragma unroll
+        for (int m = 0; m < NB; ++m)
+          if (m < nb) cx_fnma(v, row_elem(c0, m), pvec[m]);
+        wv[tid] = v;
+      }
+      for (int r = tid + T; r < N; r += T)
         if (pivstep[r] >= c0 + nb) {
           Cx<R> v = wv[r];
 #pragma unroll
@@ -589,23 +697,20 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
             if (m < nb) cx_fnma(v, A[(int64_t)r * N + c0 + m], pvec[m]);
           wv[r] = v;
         }
+      if (c0 + NB < N) fetch(c0 + NB, true);
+      else fetch(last, false);
       __syncthreads();
     }
-    const int last = (N - 1) / NB * NB;
     for (int c0 = last; c0 >= 0; c0 -= NB) {  // back: U x = y
       const int nb = min(NB, N - c0);
       if (warp == 0) {
-        Cx<R> wi = {0, 0}, ur[NB];
+        Cx<R> wi = {0, 0};
         int pi = 0;
         if (lane < nb) {
           pi = order[c0 + lane];
           wi = wv[pi];
         }
-#pragma unroll
-        for (int m = 0; m < NB; ++m) {
-          ur[m] = {0, 0};
-          if (lane < nb && m >= lane && m < nb) ur[m] = A[(int64_t)pi * N + c0 + m];  // V_b row
-        }
+        if constexpr (!SA) asm volatile("cp.async.wait_all;" ::: "memory");
         // x_b = V_b y_b: products of the block's values
         const Cx<R> y0 = wi;
         wi = {0, 0};
@@ -613,15 +718,24 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
         for (int m = 0; m < NB; ++m) {
           const Cx<R> ym = {__shfl_sync(0xffffffffu, y0.x, m), __shfl_sync(0xffffffffu, y0.y, m)};
           if (m >= lane && m < nb && lane < nb) {  // wi += V_im y_m
-            wi.x = fma(ur[m].x, ym.x, fma(-ur[m].y, ym.y, wi.x));
-            wi.y = fma(ur[m].x, ym.y, fma(ur[m].y, ym.x, wi.y));
+            const Cx<R> u = diag_elem(c0, pi, m);
+            wi.x = fma(u.x, ym.x, fma(-u.y, ym.y, wi.x));
+            wi.y = fma(u.x, ym.y, fma(u.y, ym.x, wi.y));
           }
         }
         if (lane < NB) pvec[lane] = lane < nb ? wi : Cx<R>{0, 0};
         if (lane < nb) wv[pi] = wi;
       }
       __syncthreads();
-      for (int r = tid; r < N; r += T)
+      if constexpr (!SA) asm volatile("cp.async.wait_all;" ::: "memory");
+      if (tid < N && pivstep[tid] < c0) {
+        Cx<R> v = wv[tid];
+#pragma unroll
+        for (int m = 0; m < NB; ++m)
+          if (m < nb) cx_fnma(v, row_elem(c0, m), pvec[m]);
+        wv[tid] = v;
+      }
+      for (int r = tid + T; r < N; r += T)
         if (pivstep[r] < c0) {
           Cx<R> v = wv[r];
 #pragma unroll
@@ -629,6 +743,7 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
             if (m < nb) cx_fnma(v, A[(int64_t)r * N + c0 + m], pvec[m]);
           wv[r] = v;
         }
+      if (c0 > 0) fetch(c0 - NB, false);
       __syncthreads();
     }
   };
@@ -873,19 +988,25 @@ __global__ void __launch_bounds__(T) solve_large_kernel(SolveArgs a, int64_t n_s
 // CTA size for a class whose largest system has max_ports ports
 static int large_threads(int max_ports) { return max_ports <= 128 ? 128 : (max_ports <= 256 ? 256 : 512); }
 
-size_t large_solve_smem(mts_precision prec, int max_ports) {
-  return prec == MTS_FP64 ? LargeSmem<double>(max_ports).bytes : LargeSmem<float>(max_ports).bytes;
+// the shared-resident form: FP32, a class of up to kLargeSmemPorts ports, 256 or 512 threads
+static bool large_in_smem(mts_precision prec, int T, int max_ports) {
+  return prec != MTS_FP64 && T >= 256 && max_ports <= kLargeSmemPorts;
 }
 
-template <typename R, int T>
+size_t large_solve_smem(mts_precision prec, int max_ports) {
+  if (prec == MTS_FP64) return LargeSmem<double>(max_ports).bytes;
+  return LargeSmem<float>(max_ports, large_in_smem(prec, large_threads(max_ports), max_ports)).bytes;
+}
+
+template <typename R, int T, bool SA>
 static cudaError_t launch_large(const SolveArgs& a, int64_t n_sys, int min_ports, int max_ports,
                                 void* scratch, cudaStream_t st) {
-  const size_t sm = LargeSmem<R>(max_ports).bytes;
-  cudaError_t e = cudaFuncSetAttribute(solve_large_kernel<R, T>,
+  const size_t sm = LargeSmem<R>(max_ports, SA).bytes;
+  cudaError_t e = cudaFuncSetAttribute(solve_large_kernel<R, T, SA>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  solve_large_kernel<R, T><<<(unsigned)n_sys, T, sm, st>>>(a, n_sys, min_ports, max_ports,
-                                                           static_cast<Cx<R>*>(scratch));
+  solve_large_kernel<R, T, SA><<<(unsigned)n_sys, T, sm, st>>>(a, n_sys, min_ports, max_ports,
+                                                               static_cast<Cx<R>*>(scratch));
   note_launch();
   return cudaGetLastError();
 }
@@ -895,11 +1016,15 @@ cudaError_t launch_solve_large(const SolveArgs& a, mts_precision prec, int64_t n
   if (n_sys == 0) return cudaSuccess;
   const int T = a.large_threads ? a.large_threads : large_threads(max_ports);
   if (prec == MTS_FP64)  // FP64 factors: at most 256 threads (the register budget of 512 is too small)
-    return T == 128 ? launch_large<double, 128>(a, n_sys, min_ports, max_ports, scratch, st)
-                    : launch_large<double, 256>(a, n_sys, min_ports, max_ports, scratch, st);
-  if (T == 128) return launch_large<float, 128>(a, n_sys, min_ports, max_ports, scratch, st);
-  if (T == 256) return launch_large<float, 256>(a, n_sys, min_ports, max_ports, scratch, st);
-  return launch_large<float, 512>(a, n_sys, min_ports, max_ports, scratch, st);
+    return T == 128 ? launch_large<double, 128, false>(a, n_sys, min_ports, max_ports, scratch, st)
+                    : launch_large<double, 256, false>(a, n_sys, min_ports, max_ports, scratch, st);
+  const bool sa = large_in_smem(prec, T, max_ports);
+  if (T == 128) return launch_large<float, 128, false>(a, n_sys, min_ports, max_ports, scratch, st);
+  if (T == 256)
+    return sa ? launch_large<float, 256, true>(a, n_sys, min_ports, max_ports, scratch, st)
+              : launch_large<float, 256, false>(a, n_sys, min_ports, max_ports, scratch, st);
+  return sa ? launch_large<float, 512, true>(a, n_sys, min_ports, max_ports, scratch, st)
+            : launch_large<float, 512, false>(a, n_sys, min_ports, max_ports, scratch, st);
 }
 
 }  // namespace mts

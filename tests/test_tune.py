@@ -45,6 +45,9 @@ def test_superposition_schedules_agree(simt_max_sys, prec):
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_large_solve_cta_sizes_agree(prec):
+    """The blocked solve of 80-port systems with 128, 256 and 512 threads: with MTS_MIXED the
+    first keeps the matrix in the factor scratch and the others in shared memory (the
+    backward reloads the forward's factors into it); the same results to rounding."""
     from paper_2503_18479_gb300.simulator import Simulator
     wl = small_rect(10, 8, n_cfg=6, n_freq=2, grid=8, seed=9)
     sim = Simulator(wl, prec)
