@@ -384,13 +384,12 @@ __global__ void __launch_bounds__(T, T == 128 ? 5 : (T == 256 ? 2 : 1)) solve_la
         if (j < nb && pivstep[r] >= c0) A[(int64_t)r * N + c0 + j] = pan[j * NP + r];
       }
       __syncthreads();
-      // FP32 with up to 256 threads (N <= 256 by default): the rows still to be updated (not
-      // chosen as pivots yet), listed once per panel
+      // FP32: the rows still to be updated (not chosen as pivots yet), listed once per panel
       // in the triangular-solve vector (idle during the LU); warp-aggregated, so the order of
       // the list varies but every row's update is the same
       int nact = 0;
       int* alist = reinterpret_cast<int*>(wv);
-      if constexpr (kF && (T <= 256 || SA)) {
+      if constexpr (kF) {
         if (c0 + nb < N) {
           if (tid == 0) red->cnt = 0;
           __syncthreads();
@@ -436,10 +435,7 @@ __global__ void __launch_bounds__(T, T == 128 ? 5 : (T == 256 ? 2 : 1)) solve_la
           }
         }
         __syncthreads();
-        // (512-thread CTAs keep the per-column form below: on 1024-port systems, whose
-        // trailing blocks stream through HBM, the tiles' longer compute between loads was
-        // 2 % slower)
-        if constexpr (kF && (T <= 256 || SA)) {
+        if constexpr (kF) {
           // register-tiled update: a thread takes 4 listed rows x 4 columns (j0 + lane + 32 cc,
           // so that a warp's loads of one (row, cc) are 256 contiguous bytes: conflict-free in
           // shared memory, coalesced in the scratch),
@@ -616,10 +612,10 @@ __global__ void __launch_bounds__(T, T == 128 ? 5 : (T == 256 ? 2 : 1)) solve_la
   // ---- solve A x = rhs (FP64 rhs in shared memory) into wv (by row) with the factors;
   // the unknown of column k ends in wv[order[k]]. With the factors in the scratch, each
   // step's entries are copied one step ahead (cp.async) into shared memory that is idle
-  // during the solves: the block of row tid that the row update needs (in the panel region,
-  // element m of row t at m N + t; rows past T, N > T, load theirs in the step) and warp 0's
-  // rows of the diagonal block (in the U12 region), so that their latency overlaps the
-  // barrier and the diagonal block's products. A thread reads only what it copied. ----
+  // during the solves: the blocks of the thread's rows that the row update needs (in the
+  // panel region, element m of row r at m N + r) and warp 0's rows of the diagonal block (in
+  // the U12 region), so that their latency overlaps the barrier and the diagonal block's
+  // products. A thread reads only what it copied. ----
   Cx<R>* const stg = pan;  // [NB][N]
   Cx<R>* const dstg = u12;  // [NB][32]
   auto lu_solve = [&]() {
@@ -629,11 +625,12 @@ __global__ void __launch_bounds__(T, T == 128 ? 5 : (T == 256 ? 2 : 1)) solve_la
     auto fetch = [&](int c0, bool fwd) {
       if constexpr (!SA) {
         const int nb = min(NB, N - c0);
-        if (tid < N && (fwd ? pivstep[tid] >= c0 + nb : pivstep[tid] < c0)) {
+        for (int r = tid; r < N; r += T)
+          if (fwd ? pivstep[r] >= c0 + nb : pivstep[r] < c0) {
 #pragma unroll
-          for (int m = 0; m < NB; ++m)
-            if (m < nb) cp_async_elem(stg + m * N + tid, A + (int64_t)tid * N + c0 + m);
-        }
+            for (int m = 0; m < NB; ++m)
+              if (m < nb) cp_async_elem(stg + m * N + r, A + (int64_t)r * N + c0 + m);
+          }
         if (warp == 0 && lane < nb) {
           const int pi = order[c0 + lane];
 #pragma unroll
@@ -644,11 +641,11 @@ __global__ void __launch_bounds__(T, T == 128 ? 5 : (T == 256 ? 2 : 1)) solve_la
         asm volatile("cp.async.commit_group;" ::: "memory");
       }
     };
-    // entry m of this thread's staged row block / diagonal row (the matrix itself when it
-    // is in shared memory)
-    auto row_elem = [&](int c0, int m) -> Cx<R> {
-      if constexpr (SA) return A[(int64_t)tid * N + c0 + m];
-      else return stg[m * N + tid];
+    // entry m of the staged block of row r / of this lane's diagonal row (the matrix itself
+    // when it is in shared memory)
+    auto row_elem = [&](int r, int c0, int m) -> Cx<R> {
+      if constexpr (SA) return A[(int64_t)r * N + c0 + m];
+      else return stg[m * N + r];
     };
     auto diag_elem = [&](int c0, int pi, int m) -> Cx<R> {
       if constexpr (SA) return A[(int64_t)pi * N + c0 + m];
@@ -682,19 +679,12 @@ __global__ void __launch_bounds__(T, T == 128 ? 5 : (T == 256 ? 2 : 1)) solve_la
       }
       __syncthreads();
       if constexpr (!SA) asm volatile("cp.async.wait_all;" ::: "memory");
-      if (tid < N && pivstep[tid] >= c0 + nb) {
-        Cx<R> v = wv[tid];
-#pragma unroll
-        for (int m = 0; m < NB; ++m)
-          if (m < nb) cx_fnma(v, row_elem(c0, m), pvec[m]);
-        wv[tid] = v;
-      }
-      for (int r = tid + T; r < N; r += T)
+      for (int r = tid; r < N; r += T)
         if (pivstep[r] >= c0 + nb) {
           Cx<R> v = wv[r];
 #pragma unroll
           for (int m = 0; m < NB; ++m)
-            if (m < nb) cx_fnma(v, A[(int64_t)r * N + c0 + m], pvec[m]);
+            if (m < nb) cx_fnma(v, row_elem(r, c0, m), pvec[m]);
           wv[r] = v;
         }
       if (c0 + NB < N) fetch(c0 + NB, true);
@@ -728,19 +718,12 @@ __global__ void __launch_bounds__(T, T == 128 ? 5 : (T == 256 ? 2 : 1)) solve_la
       }
       __syncthreads();
       if constexpr (!SA) asm volatile("cp.async.wait_all;" ::: "memory");
-      if (tid < N && pivstep[tid] < c0) {
-        Cx<R> v = wv[tid];
-#pragma unroll
-        for (int m = 0; m < NB; ++m)
-          if (m < nb) cx_fnma(v, row_elem(c0, m), pvec[m]);
-        wv[tid] = v;
-      }
-      for (int r = tid + T; r < N; r += T)
+      for (int r = tid; r < N; r += T)
         if (pivstep[r] < c0) {
           Cx<R> v = wv[r];
 #pragma unroll
           for (int m = 0; m < NB; ++m)
-            if (m < nb) cx_fnma(v, A[(int64_t)r * N + c0 + m], pvec[m]);
+            if (m < nb) cx_fnma(v, row_elem(r, c0, m), pvec[m]);
           wv[r] = v;
         }
       if (c0 > 0) fetch(c0 - NB, false);
