@@ -105,7 +105,7 @@ int64_t bop_elems(const mts_problem* pb, int64_t n_cfg, int npieces, int64_t* un
     if (use_tensor_path(npieces, n_cfg, F, simt_max_sys)) {
       u += (P + kTileP - 1) / kTileP * nn;
     } else {
-      const int64_t vs = (P + kSimtPts - 1) / kSimtPts * ((n_cfg * F + kSimtSys - 1) / kSimtSys);
+      const int64_t vs = simt_point_groups(P) * ((n_cfg * F + kSimtSys - 1) / kSimtSys);
       v += vs;
       if (vs > vmax) vmax = vs;
     }

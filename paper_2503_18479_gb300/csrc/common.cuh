@@ -78,6 +78,17 @@ inline bool use_tensor_path(int npieces, int64_t n_cfg, int64_t F, int64_t simt_
   return npieces > 0 && (simt_max_sys < 0 || n_cfg * F > simt_max_sys);
 }
 
+// A SIMT unit is up to kSimtTiles consecutive tiles of kSimtPts points x kSimtSys systems
+// of one structure, taken in turn by one CTA (the systems' offsets and, for N <= one K
+// chunk, their staged currents serve every tile).
+constexpr int kSimtTiles = 4;
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline int64_t simt_point_groups(int64_t P) {
+  return ((P + kSimtPts - 1) / kSimtPts + kSimtTiles - 1) / kSimtTiles;
+}
+
 // Each structure's H block starts at a multiple of 32 elements (128 bytes), so that its rows
 // are 16-byte aligned whenever N_s is a multiple of 4 (vector loads in the SIMT kernel).
 constexpr int64_t kHAlign = 32;

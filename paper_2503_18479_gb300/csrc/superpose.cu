@@ -33,7 +33,7 @@ __device__ inline PlanWork plan_work(int s, int64_t n_cfg, const int32_t* __rest
   if (use_tensor_path(npieces, n_cfg, F, simt_max_sys))
     w.u = (P + kTileP - 1) / kTileP * nn;
   else
-    w.v = (P + kSimtPts - 1) / kSimtPts * ((n_cfg * F + kSimtSys - 1) / kSimtSys);
+    w.v = simt_point_groups(P) * ((n_cfg * F + kSimtSys - 1) / kSimtSys);
   if (N > kRegMaxPorts) w.f = F * N * N;
   return w;
 }
@@ -215,13 +215,11 @@ __global__ void __launch_bounds__(kSimtPts) superpose_simt_kernel(SuperposeArgs 
   const int F = a.freq_off[s + 1] - a.freq_off[s];
   const int64_t nsys = a.n_cfg * F;
   const int64_t np = (P + kSimtPts - 1) / kSimtPts;
+  const int64_t npg = simt_point_groups(P);
   const int64_t lu = unit - a.simt_off[s];
-  const int64_t pt = lu % np, sys0 = (lu / np) * kSimtSys;
+  const int64_t pt0 = (lu % npg) * kSimtTiles, sys0 = (lu / npg) * kSimtSys;
   const int nsv = (int)min((int64_t)kSimtSys, nsys - sys0);
   const int t = threadIdx.x;
-  const int64_t p = pt * kSimtPts + t;
-  const bool live = p < P;
-  const T* hrow = static_cast<const T*>(a.H) + a.t.pn_off[s] + (live ? p : 0) * N;
   const bool vec = (N % VEC) == 0;
   // offsets of the unit's systems in I and in B, one 64-bit division per system (not one per
   // staged current and per stored value)
@@ -239,116 +237,126 @@ __global__ void __launch_bounds__(kSimtPts) superpose_simt_kernel(SuperposeArgs 
     s_ooff[t] = oo;
   }
   __syncthreads();
-  if constexpr (sizeof(T) == 4) {
-    if (vec) {
-      // The unit's 128 rows of H are one contiguous block: each K chunk of them is copied
-      // into shared memory with cp.async (consecutive threads, consecutive 16-byte pieces of a
-      // row; rows past P are zero-filled) while the chunk's currents are staged, and each
-      // thread then reads its own padded row.
-      float* sH = reinterpret_cast<float*>(sm_simt + simt_smem_bytes<float>());  // [128][HP]
-      constexpr int HP = kSimtHPitch;
-      unsigned long long acc[kSimtSys];
+  // the unit's point tiles in turn (CTA-uniform bounds)
+  for (int64_t pt = pt0; pt < min(np, pt0 + kSimtTiles); ++pt) {
+    const int64_t p = pt * kSimtPts + t;
+    const bool live = p < P;
+    const T* hrow = static_cast<const T*>(a.H) + a.t.pn_off[s] + (live ? p : 0) * N;
+    // the currents of a single K chunk are staged once, for the unit's first tile
+    const bool stage_I = pt == pt0 || N > KC;
+    if constexpr (sizeof(T) == 4) {
+      if (vec) {
+        // The tile's 128 rows of H are one contiguous block: each K chunk of them is copied
+        // into shared memory with cp.async (consecutive threads, consecutive 16-byte pieces
+        // of a row; rows past P are zero-filled) while the chunk's currents are staged, and
+        // each thread then reads its own padded row.
+        float* sH = reinterpret_cast<float*>(sm_simt + simt_smem_bytes<float>());  // [128][HP]
+        constexpr int HP = kSimtHPitch;
+        unsigned long long acc[kSimtSys];
 #pragma unroll
-      for (int i = 0; i < kSimtSys; ++i) acc[i] = 0ull;
-      const float* hblk = static_cast<const float*>(a.H) + a.t.pn_off[s] + pt * kSimtPts * (int64_t)N;
-      const int rows = (int)min((int64_t)kSimtPts, P - pt * kSimtPts);
-      for (int k0 = 0; k0 < N; k0 += KC) {
-        const int kn = min(KC, N - k0);
-        const int q4 = kn / 4;  // 16-byte pieces per row
-        for (int e = t; e < kSimtPts * q4; e += kSimtPts) {
-          const int r = e / q4, c = e - r * q4;
-          const uint32_t dst = (uint32_t)__cvta_generic_to_shared(sH + r * HP + 4 * c);
-          const float* src = r < rows ? hblk + (int64_t)r * N + k0 + 4 * c : hblk;
-          asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
-                       "r"(r < rows ? 16u : 0u)
-                       : "memory");
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-        for (int e = t; e < kn * kSimtSys; e += kSimtPts) {
-          const int k = e / kSimtSys, i = e - k * kSimtSys;
-          float re = 0.0f, im = 0.0f;
-          if (i < nsv) {
-            const double* Ip = a.I + s_ioff[i] + 2 * (k0 + k);
-            re = (float)Ip[0];
-            im = (float)Ip[1];
+        for (int i = 0; i < kSimtSys; ++i) acc[i] = 0ull;
+        const float* hblk = static_cast<const float*>(a.H) + a.t.pn_off[s] + pt * kSimtPts * (int64_t)N;
+        const int rows = (int)min((int64_t)kSimtPts, P - pt * kSimtPts);
+        for (int k0 = 0; k0 < N; k0 += KC) {
+          const int kn = min(KC, N - k0);
+          const int q4 = kn / 4;  // 16-byte pieces per row
+          for (int e = t; e < kSimtPts * q4; e += kSimtPts) {
+            const int r = e / q4, c = e - r * q4;
+            const uint32_t dst = (uint32_t)__cvta_generic_to_shared(sH + r * HP + 4 * c);
+            const float* src = r < rows ? hblk + (int64_t)r * N + k0 + 4 * c : hblk;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+                         "r"(r < rows ? 16u : 0u)
+                         : "memory");
           }
-          sI[2 * (k * kSimtSys + i)] = re;
-          sI[2 * (k * kSimtSys + i) + 1] = im;
-        }
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        __syncthreads();
-        const float* hr = sH + t * HP;
-        if (nsv <= 4) simt_accumulate_f2<4>(hr, sI, kn, acc);
-        else if (nsv <= 8) simt_accumulate_f2<8>(hr, sI, kn, acc);
-        else simt_accumulate_f2<16>(hr, sI, kn, acc);
-        __syncthreads();
-      }
-      if (live) {
-        float2* out = static_cast<float2*>(a.B_out);
-#pragma unroll
-        for (int i = 0; i < kSimtSys; ++i)
-          if (i < nsv) {
-            float2 v;
-            asm("mov.b64 {%0,%1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(acc[i]));
-            out[s_ooff[i] + p] = v;
+          asm volatile("cp.async.commit_group;" ::: "memory");
+          if (stage_I) {
+            for (int e = t; e < kn * kSimtSys; e += kSimtPts) {
+              const int k = e / kSimtSys, i = e - k * kSimtSys;
+              float re = 0.0f, im = 0.0f;
+              if (i < nsv) {
+                const double* Ip = a.I + s_ioff[i] + 2 * (k0 + k);
+                re = (float)Ip[0];
+                im = (float)Ip[1];
+              }
+              sI[2 * (k * kSimtSys + i)] = re;
+              sI[2 * (k * kSimtSys + i) + 1] = im;
+            }
           }
-      }
-      return;
-    }
-  }
-  // FP64, or FP32 with N not a multiple of 4 (a short register chunk: this path is rare in
-  // FP32 and should not set the kernel's register count)
-  constexpr int KR = sizeof(T) == 4 ? 16 : KC;
-  T ax[kSimtSys], ay[kSimtSys];
-#pragma unroll
-  for (int i = 0; i < kSimtSys; ++i) ax[i] = ay[i] = T(0);
-  for (int k0 = 0; k0 < N; k0 += KR) {
-    const int kn = min(KR, N - k0);
-    T h[KR];
-    if (vec) {  // kn is a multiple of VEC here
-#pragma unroll
-      for (int q = 0; q < KR / VEC; ++q) {
-        V v;
-        if (live && q * VEC < kn) {
-          v = *reinterpret_cast<const V*>(hrow + k0 + q * VEC);
-        } else {
-          v = V{};
+          asm volatile("cp.async.wait_all;" ::: "memory");
+          __syncthreads();
+          const float* hr = sH + t * HP;
+          if (nsv <= 4) simt_accumulate_f2<4>(hr, sI, kn, acc);
+          else if (nsv <= 8) simt_accumulate_f2<8>(hr, sI, kn, acc);
+          else simt_accumulate_f2<16>(hr, sI, kn, acc);
+          __syncthreads();
         }
-        const T* pv = reinterpret_cast<const T*>(&v);
+        if (live) {
+          float2* out = static_cast<float2*>(a.B_out);
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) h[q * VEC + e] = pv[e];
+          for (int i = 0; i < kSimtSys; ++i)
+            if (i < nsv) {
+              float2 v;
+              asm("mov.b64 {%0,%1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(acc[i]));
+              out[s_ooff[i] + p] = v;
+            }
+        }
+        continue;
       }
-    } else {
-#pragma unroll
-      for (int k = 0; k < KR; ++k) h[k] = (live && k < kn) ? hrow[k0 + k] : T(0);
     }
-    __syncthreads();
-    for (int e = t; e < kn * kSimtSys; e += kSimtPts) {
-      const int k = e / kSimtSys, i = e - k * kSimtSys;
-      T re = T(0), im = T(0);
-      if (i < nsv) {
-        const double* Ip = a.I + s_ioff[i] + 2 * (k0 + k);
-        re = (T)Ip[0];
-        im = (T)Ip[1];
-      }
-      sI[2 * (k * kSimtSys + i)] = re;
-      sI[2 * (k * kSimtSys + i) + 1] = im;
-    }
-    __syncthreads();
-    if (nsv <= 4) simt_accumulate<T, 4, KR>(h, sI, kn, ax, ay);
-    else if (nsv <= 8) simt_accumulate<T, 8, KR>(h, sI, kn, ax, ay);
-    else simt_accumulate<T, 16, KR>(h, sI, kn, ax, ay);
-  }
-  if (live) {
-    C2* out = static_cast<C2*>(a.B_out);
+    // FP64, or FP32 with N not a multiple of 4 (a short register chunk: this path is rare in
+    // FP32 and should not set the kernel's register count)
+    constexpr int KR = sizeof(T) == 4 ? 16 : KC;
+    T ax[kSimtSys], ay[kSimtSys];
 #pragma unroll
-    for (int i = 0; i < kSimtSys; ++i)
-      if (i < nsv) {
-        C2 v;
-        v.x = ax[i];
-        v.y = ay[i];
-        out[s_ooff[i] + p] = v;
+    for (int i = 0; i < kSimtSys; ++i) ax[i] = ay[i] = T(0);
+    for (int k0 = 0; k0 < N; k0 += KR) {
+      const int kn = min(KR, N - k0);
+      T h[KR];
+      if (vec) {  // kn is a multiple of VEC here
+#pragma unroll
+        for (int q = 0; q < KR / VEC; ++q) {
+          V v;
+          if (live && q * VEC < kn) {
+            v = *reinterpret_cast<const V*>(hrow + k0 + q * VEC);
+          } else {
+            v = V{};
+          }
+          const T* pv = reinterpret_cast<const T*>(&v);
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) h[q * VEC + e] = pv[e];
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < KR; ++k) h[k] = (live && k < kn) ? hrow[k0 + k] : T(0);
       }
+      __syncthreads();
+      for (int e = t; e < kn * kSimtSys; e += kSimtPts) {
+        const int k = e / kSimtSys, i = e - k * kSimtSys;
+        T re = T(0), im = T(0);
+        if (i < nsv) {
+          const double* Ip = a.I + s_ioff[i] + 2 * (k0 + k);
+          re = (T)Ip[0];
+          im = (T)Ip[1];
+        }
+        sI[2 * (k * kSimtSys + i)] = re;
+        sI[2 * (k * kSimtSys + i) + 1] = im;
+      }
+      __syncthreads();
+      if (nsv <= 4) simt_accumulate<T, 4, KR>(h, sI, kn, ax, ay);
+      else if (nsv <= 8) simt_accumulate<T, 8, KR>(h, sI, kn, ax, ay);
+      else simt_accumulate<T, 16, KR>(h, sI, kn, ax, ay);
+    }
+    if (live) {
+      C2* out = static_cast<C2*>(a.B_out);
+#pragma unroll
+      for (int i = 0; i < kSimtSys; ++i)
+        if (i < nsv) {
+          C2 v;
+          v.x = ax[i];
+          v.y = ay[i];
+          out[s_ooff[i] + p] = v;
+        }
+    }
   }
 }
 
