@@ -1,20 +1,24 @@
 // solve_large.cu -- (b) port solve, (d) objective and (adj) adjoint for structures with more
 // ports than the register-resident kernels hold (64 < N <= 1024).
 //
-// One system (configuration b, frequency g) per CTA of 128 (N <= 128) or 256 threads. The
-// matrix A = diag(R) + j w M + diag(1/(j w C)) (paper Eq. 2, 11) is assembled into the tape's
-// factor scratch (global memory, L2-resident while in use) and factorised there by a blocked
-// right-looking LU with
-// partial pivoting, without moving rows (the pivot of column k is the largest |a_rk| among
-// rows not chosen yet; chosen rows keep U in place, the others keep their multipliers):
+// One system (configuration b, frequency g) per CTA of 128 (N <= 128), 256 (N <= 256) or 512
+// threads. The matrix A = diag(R) + j w M + diag(1/(j w C)) (paper Eq. 2, 11) is assembled
+// into the tape's factor scratch (global memory, L2-resident while in use; or shared memory,
+// a schedule choice for FP32 classes of up to 128 ports) and factorised there by a blocked
+// right-looking LU with partial pivoting, without moving rows (the pivot of column k is the
+// largest |a_rk| among rows not chosen yet; chosen rows keep U in place, the others keep
+// their multipliers):
 //   panel   the NB columns [c0, c0+NB) of every row, staged column-major in shared memory,
-//           factorised step by step (block arg-max per step);
+//           factorised step by step (block arg-max per step, one barrier);
 //   U12     the NB pivot rows of the panel over the trailing columns: a unit-lower
-//           triangular solve against the panel's multipliers;
-//   update  every row not chosen yet: A[r][j] -= sum_m L[r][m] U12[m][j], thread per
-//           column j of a CW-column chunk with U12[.][j] in registers (coalesced rows).
-// Triangular solves run panel by panel: a warp solves the panel's NB x NB triangle, then
-// the other rows take the panel's contribution (thread per row).
+//           triangular solve against the panel's multipliers, a CW-column chunk at a time;
+//   update  every row not chosen yet: A[r][j] -= sum_m L[r][m] U12[m][j]; FP32 register-
+//           tiled (4 listed rows x 4 columns per thread), FP64 thread per column j with
+//           U12[.][j] in registers.
+// After the LU the NB x NB diagonal blocks are replaced by their inverses, and the
+// triangular solves run block by block: warp 0 applies the block's inverse, then the other
+// rows take the block's contribution (thread per row), with each step's entries copied a
+// step ahead.
 //
 //   R = double: FP64 factors and one solve (MTS_FP64, NB = 8).
 //   R = float : FP32 factors (NB = 16) and iterative refinement on residuals rhs - A x
