@@ -3,7 +3,8 @@ Simulator on a given batch for each candidate schedule and keeps the fastest in
 `sim.tuning` (passed to every later call through mts_eval). The candidates choose, per
 structure, the tensor-core or the SIMT superposition (the threshold on configurations x
 frequencies), the CTA size of the blocked solve for N > 64 (128, 256 or 512 threads per
-system), and whether the register classes of up to 32 ports run one mapping wider (a half
+system; with MTS_MIXED / MTS_BF16 and at most 128 ports, 256 and 512 also keep the matrix in
+shared memory, one system per SM), and whether the register classes of up to 32 ports run one mapping wider (a half
 warp, a warp or a two-warp CTA per system instead of the class's own). Every schedule
 computes the same result to rounding; only time differs."""
 from __future__ import annotations
