@@ -46,18 +46,28 @@ def test_superposition_schedules_agree(simt_max_sys, prec):
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_large_solve_cta_sizes_agree(prec):
     """The blocked solve of 80-port systems with 128, 256 and 512 threads: with MTS_MIXED the
-    first keeps the matrix in the factor scratch and the others in shared memory (the
-    backward reloads the forward's factors into it); the same results to rounding."""
+    first keeps the matrix in the factor scratch and the others in shared memory (a backward
+    with a field cotangent reloads the forward's factors into it); the same results to
+    rounding, for the loss cotangent alone and with a field cotangent."""
     from paper_2503_18479_gb300.simulator import Simulator
     wl = small_rect(10, 8, n_cfg=6, n_freq=2, grid=8, seed=9)
     sim = Simulator(wl, prec)
     outs = []
+    gB = None
     for lt in (128, 256, 512):
         sim.tuning = {"simt_max_sys": 0, "large_threads": lt}
         C = torch.from_numpy(wl.C).cuda().requires_grad_(True)
         B, loss = sim(C)
         loss.sum().backward()
-        outs.append((B.detach(), loss.detach(), C.grad.clone()))
+        C2 = torch.from_numpy(wl.C).cuda().requires_grad_(True)
+        B2, loss2 = sim(C2)
+        if gB is None:
+            g = torch.Generator().manual_seed(3)
+            gB = torch.complex(torch.randn(B2.shape, generator=g, dtype=torch.float64),
+                               torch.randn(B2.shape, generator=g, dtype=torch.float64))
+            gB = gB.to(B2.dtype).cuda()
+        torch.autograd.backward([B2, loss2], [gB, torch.ones_like(loss2)])
+        outs.append((B.detach(), loss.detach(), C.grad.clone(), C2.grad.clone()))
     for o in outs[1:]:
         for a, b in zip(outs[0], o):
             assert rel(a.cpu().numpy(), b.cpu().numpy()) < 1e-13
